@@ -1,0 +1,136 @@
+"""CPU oracle for the sync step (element writes -> canonical CSC).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package.  The product path
+(``paper_1805_03380_gb300``) never imports it, and this package never imports
+the product.  The C++ source ``spm_oracle.cpp`` is a plain std::map (red-black
+tree) build followed by an in-order walk into CSC, following Sections 3.1 and
+3.3 of the paper; the functions here only marshal numpy arrays into it.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "spm_oracle.cpp")
+_LIB = os.path.join(_HERE, "libspm_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with the host compiler (g++, -O2, no -march flags)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", _SRC, "-o", tmp])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB)
+            p = ctypes.c_void_p
+            i64 = ctypes.c_int64
+            lib.oracle_assemble_csc.argtypes = [i64, i64, i64, p, p, p, p, ctypes.c_int, ctypes.c_int,
+                                                p, p, p, p, p]
+            lib.oracle_assemble_csc.restype = ctypes.c_int
+            lib.oracle_csc_mm.argtypes = [i64, i64, p, p, p, ctypes.c_int, i64, p, i64, p, i64]
+            lib.oracle_csc_mm.restype = ctypes.c_int
+            lib.oracle_dvals.argtypes = [i64, p, p, p, i64, p, i64, p, i64, p]
+            lib.oracle_dvals.restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+class OracleError(RuntimeError):
+    pass
+
+
+def assemble_csc(rows, cols, vals, shape, mode="set", seq=None, out_f32=None, with_map=False):
+    """Canonical CSC of the matrix produced by the element writes.
+
+    rows, cols : integer arrays of length m
+    vals       : float32 or float64 array; float32 input means float32 output
+                 (the accumulation is double either way) unless ``out_f32`` says
+                 otherwise
+    shape      : (n_rows, n_cols)
+    mode       : "set" (X(r,c) = v, last write wins) or "sum" (X(r,c) += v)
+    seq        : optional uint64 order of the writes (ties keep stream order)
+
+    Returns (col_ptr int64[n_cols+1], row_idx int64[nnz], values float64[nnz])
+    and, with ``with_map``, the int64 map (slot, -1 overwritten, -2 removed).
+    """
+    n_rows, n_cols = int(shape[0]), int(shape[1])
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    cols = np.ascontiguousarray(cols, dtype=np.int64)
+    vals_in = np.asarray(vals)
+    if out_f32 is None:
+        out_f32 = vals_in.dtype == np.float32
+    v64 = np.ascontiguousarray(vals_in, dtype=np.float64)
+    m = rows.shape[0]
+    if cols.shape[0] != m or v64.shape[0] != m:
+        raise ValueError("rows, cols and vals must have the same length")
+    s = None if seq is None else np.ascontiguousarray(seq, dtype=np.uint64)
+    col_ptr = np.zeros(n_cols + 1, dtype=np.int64)
+    row_idx = np.empty(max(m, 1), dtype=np.int64)
+    out = np.empty(max(m, 1), dtype=np.float64)
+    nnz = np.zeros(1, dtype=np.int64)
+    mp = np.empty(max(m, 1), dtype=np.int64) if with_map else None
+    rc = _load().oracle_assemble_csc(n_rows, n_cols, m, _ptr(rows), _ptr(cols), _ptr(v64), _ptr(s),
+                                     1 if mode == "sum" else 0, 1 if out_f32 else 0,
+                                     _ptr(col_ptr), _ptr(row_idx), _ptr(out), _ptr(nnz), _ptr(mp))
+    if rc == 2:
+        raise OracleError("index out of range")
+    if rc != 0:
+        raise OracleError(f"oracle_assemble_csc failed: {rc}")
+    n = int(nnz[0])
+    res = (col_ptr, row_idx[:n].copy(), out[:n].copy())
+    if with_map:
+        return res + (mp[:m].copy(),)
+    return res
+
+
+def csc_mm(shape, col_ptr, row_idx, vals, X, transpose=False):
+    """Y = A X or A^T X in double precision, A in CSC."""
+    n_rows, n_cols = int(shape[0]), int(shape[1])
+    col_ptr = np.ascontiguousarray(col_ptr, dtype=np.int64)
+    row_idx = np.ascontiguousarray(row_idx, dtype=np.int64)
+    vals = np.ascontiguousarray(vals, dtype=np.float64)
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    k = X.shape[1]
+    out_rows = n_cols if transpose else n_rows
+    Y = np.empty((out_rows, k), dtype=np.float64)
+    rc = _load().oracle_csc_mm(n_rows, n_cols, _ptr(col_ptr), _ptr(row_idx), _ptr(vals),
+                               1 if transpose else 0, k, _ptr(X), k, _ptr(Y), k)
+    if rc != 0:
+        raise OracleError(f"oracle_csc_mm failed: {rc}")
+    return Y
+
+
+def dvals(rows, cols, dY, X, map=None):
+    """d<dY, A X>/d vals[t] (zero for overwritten writes when a map is given)."""
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    cols = np.ascontiguousarray(cols, dtype=np.int64)
+    dY = np.ascontiguousarray(dY, dtype=np.float64)
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    mp = None if map is None else np.ascontiguousarray(map, dtype=np.int64)
+    m = rows.shape[0]
+    out = np.empty(max(m, 1), dtype=np.float64)
+    rc = _load().oracle_dvals(m, _ptr(rows), _ptr(cols), _ptr(mp), X.shape[1], _ptr(dY), dY.shape[1],
+                              _ptr(X), X.shape[1], _ptr(out))
+    if rc != 0:
+        raise OracleError(f"oracle_dvals failed: {rc}")
+    return out[:m].copy()
