@@ -1,0 +1,385 @@
+#!/usr/bin/env python
+"""Benchmark of the sync step: unordered element writes -> canonical CSC.
+
+Default workload (N=1): 100,000 x 100,000 matrix, 10^8 writes, column index
+bounded Zipf(s=1.1), row uniform, values U(-1,1) in float64, add semantics
+(duplicates summed) -- the 10^8-write assembly the headline metric is quoted
+on.  One step = one spm_assemble_csc call (every kernel of the path) over the
+whole stream, inputs resident in HBM (1.6 GB, larger than the 129 MB L2, so
+no flush is needed between steps).
+
+Prints ONE JSON line (rank 0).  Multi-GPU (torchrun, one rank per GPU): every
+rank assembles its own replica of the workload (different seed), there is no
+data-path collective; value = writes of all ranks / max over ranks of the
+timed region (weak scaling).
+
+--impl reference runs the CPU oracle (std::map build + in-order walk) on the
+host cores instead, each step a bounded prefix of the same stream.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "assembled triplets/sec and achieved HBM GB/s (% of roofline) vs CPU oracle"
+UNIT = "triplets/s"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def workload_spec(name):
+    import numpy as np
+    specs = {
+        "n8": dict(desc="100,000 x 100,000, 10^8 writes, Zipf(1.1) columns, uniform rows, U(-1,1) float64, sum mode",
+                   m=100_000_000, n=100_000, dtype=np.float64, mode="sum", kind="zipf"),
+        "zipf1e7": dict(desc="100,000 x 100,000, 10^7 writes, Zipf(1.1) columns, U(-1,1) float64, sum mode",
+                        m=10_000_000, n=100_000, dtype=np.float64, mode="sum", kind="zipf"),
+        "zipf1e7_f32": dict(desc="100,000 x 100,000, 10^7 writes, Zipf(1.1) columns, U(-1,1) float32 values, "
+                                 "float64 accumulation, sum mode",
+                            m=10_000_000, n=100_000, dtype=np.float32, mode="sum", kind="zipf"),
+        "fem2048": dict(desc="Q1 FEM 2048 x 2048 elements (4,198,401 nodes), 67,108,864 writes, float64, sum mode",
+                        n_el=2048, dtype=np.float64, mode="sum", kind="fem"),
+    }
+    return specs[name]
+
+
+def make_workload(name, rank=0):
+    import workloads
+    s = workload_spec(name)
+    if s["kind"] == "zipf":
+        d = workloads.zipf_batch(m=s["m"], n=s["n"], dtype=s["dtype"], seed=workloads.SEED_BASE + 2 + 1000 * rank)
+    else:
+        d = workloads.fem_q1(n_el=s["n_el"], dtype=s["dtype"], seed=workloads.SEED_BASE + 3 + 1000 * rank)
+    return d, s
+
+
+def measured_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            j = json.load(f)
+        return float(j["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1805_03380_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        if fn.endswith((".cu", ".cuh")):
+            with open(os.path.join(csrc, fn), "rb") as f:
+                h.update(fn.encode() + f.read())
+    with open(os.path.join(ROOT, "include", "spm.h"), "rb") as f:
+        h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(workload):
+    """DRAM bytes per call from the committed ncu summary, if it was taken on
+    the current sources (otherwise None)."""
+    p = os.path.join(ROOT, "profiles", f"traffic_{workload}.md")
+    if not os.path.exists(p):
+        return None
+    vals = {}
+    with open(p) as f:
+        for line in f:
+            if ":" in line and line.startswith("- "):
+                k, v = line[2:].split(":", 1)
+                vals[k.strip()] = v.strip()
+    if vals.get("source_hash") != source_hash():
+        return None
+    try:
+        return int(vals["dram_bytes_per_call"])
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "50", "-i", str(self.gpu)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def aggregate(elapsed_s, units, world, device):
+    """Max of the timed region and sum of the units over ranks."""
+    if world == 1:
+        return elapsed_s, units
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([elapsed_s], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
+def oracle_rate(d, mode, sample):
+    """CPU oracle (single thread) on the first `sample` writes: writes/s."""
+    import oracle
+    r, c, v = d["rows"][:sample], d["cols"][:sample], d["vals"][:sample]
+    t0 = time.perf_counter()
+    oracle.assemble_csc(r, c, v, d["shape"], mode=mode)
+    dt = time.perf_counter() - t0
+    return sample / dt, dt
+
+
+def run_reference(args, world, rank):
+    import numpy as np  # noqa: F401
+    import workloads
+    if rank != 0:
+        return
+    spec = workload_spec(args.workload)
+    sample = args.ref_sample
+    # the prefix of the same stream (the generator draws in fixed chunks of 2^24)
+    if spec["kind"] == "zipf":
+        d = workloads.zipf_batch(m=max(sample, min(spec["m"], 1 << 24)), n=spec["n"], dtype=spec["dtype"],
+                                 seed=workloads.SEED_BASE + 2)
+    else:
+        d = workloads.fem_q1(n_el=spec["n_el"], dtype=spec["dtype"], seed=workloads.SEED_BASE + 3)
+    for _ in range(args.warmup):
+        oracle_rate(d, spec["mode"], sample)
+    times = []
+    for _ in range(args.steps):
+        _, dt = oracle_rate(d, spec["mode"], sample)
+        times.append(dt)
+    tot = sum(times)
+    value = sample * args.steps / tot
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1000 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if spec["dtype"].__name__ == "float64" else "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "description": spec["desc"],
+                   "sample": f"first {sample} writes of the same stream per step"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"first {sample} writes of the workload's stream, std::map build + walk, 1 thread"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="n8", choices=["n8", "zipf1e7", "zipf1e7_f32", "fem2048"])
+    ap.add_argument("--cpu-sample", type=int, default=10_000_000, help="writes the CPU oracle baseline times")
+    ap.add_argument("--ref-sample", type=int, default=1_000_000, help="writes per step of --impl reference")
+    ap.add_argument("--e2e-steps", type=int, default=None)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+
+    import numpy as np
+    import torch
+
+    import paper_1805_03380_gb300 as spm
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    d, spec = make_workload(args.workload, rank)
+    m = len(d["rows"])
+    n_rows, n_cols = d["shape"]
+    sv = np.dtype(spec["dtype"]).itemsize
+    rows = torch.from_numpy(d["rows"]).to(dev)
+    cols = torch.from_numpy(d["cols"]).to(dev)
+    vals = torch.from_numpy(d["vals"]).to(dev)
+    asm = spm.Assembler(d["shape"], m, vals.dtype, spec["mode"], device=dev)
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        asm.run(rows, cols, vals)
+    A = asm.result()  # synchronises and checks the device status
+    nnz = A.nnz
+
+    # ---- timed region: K steps, inputs resident in HBM ----
+    spm.spm_debug_stage_timing(True)
+    sampler = ClockSampler(local_rank if "CUDA_VISIBLE_DEVICES" not in os.environ else 0)
+    sampler.start()
+    time.sleep(0.2)
+    launches0 = spm.spm_debug_launch_count()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for k in range(args.steps):
+        starts[k].record(stream)
+        asm.run(rows, cols, vals)
+        ends[k].record(stream)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    launches = spm.spm_debug_launch_count() - launches0
+    elapsed_s = t_start.elapsed_time(t_end) / 1000.0
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    stages = {}
+    nback = min(args.steps, 64)
+    for back in range(nback):
+        for kname, v in spm.spm_debug_stage_times(back).items():
+            stages.setdefault(kname, []).append(v)
+    # keep the GPU under the same load for a moment so the clock sampler sees it
+    t_extra = time.perf_counter()
+    while time.perf_counter() - t_extra < 1.0:
+        asm.run(rows, cols, vals)
+        torch.cuda.synchronize()
+    sampler.stop()
+    spm.spm_debug_stage_timing(False)
+    A = asm.result()
+    assert A.nnz == nnz
+
+    tot_s, tot_units = aggregate(elapsed_s, m * args.steps, world, dev)
+    value = tot_units / tot_s
+    ms_per_step = 1000.0 * tot_s / args.steps
+
+    # ---- roofline of the whole call (the sync step's algorithmic bytes) ----
+    alg_bytes = m * (4 + 4 + sv) + nnz * (4 + sv) + (n_cols + 1) * 8
+    mean_call_s = statistics.mean(step_ms) / 1000.0
+    achieved = alg_bytes / mean_call_s / 1e9
+    peak, peak_kind = measured_peak()
+    stage_ms = {k: statistics.mean(v) for k, v in stages.items()}
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": profiled_traffic(args.workload), "peak_kind": peak_kind,
+                "kernel": "spm_assemble_csc: the whole sync step (12 kernels), CUDA events around each call",
+                "algorithmic_bytes_per_call": alg_bytes,
+                "bytes_formula": "m*(4+4+sv) + nnz*(4+sv) + (n_cols+1)*8",
+                "call_ms_mean": 1000 * mean_call_s, "stage_ms_mean": stage_ms}
+
+    # ---- end to end through the public API: pinned host buffers, copies inside ----
+    e2e_steps = args.e2e_steps or min(args.steps, 10)
+    h_rows = torch.from_numpy(d["rows"]).pin_memory()
+    h_cols = torch.from_numpy(d["cols"]).pin_memory()
+    h_vals = torch.from_numpy(d["vals"]).pin_memory()
+    o_cp = torch.empty(n_cols + 1, dtype=torch.int64).pin_memory()
+    o_ri = torch.empty(m, dtype=torch.int32).pin_memory()
+    o_v = torch.empty(m, dtype=vals.dtype).pin_memory()
+    d_rows, d_cols, d_vals = torch.empty_like(rows), torch.empty_like(cols), torch.empty_like(vals)
+    d2h = 0
+
+    def e2e_step():
+        d_rows.copy_(h_rows, non_blocking=True)
+        d_cols.copy_(h_cols, non_blocking=True)
+        d_vals.copy_(h_vals, non_blocking=True)
+        asm.run(d_rows, d_cols, d_vals)
+        k = int(asm.d_nnz.item())
+        o_cp.copy_(asm.col_ptr, non_blocking=True)
+        o_ri[:k].copy_(asm.row_idx[:k], non_blocking=True)
+        o_v[:k].copy_(asm.out_vals[:k], non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+        return 8 + (n_cols + 1) * 8 + k * (4 + sv)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        d2h = e2e_step()
+    e2e_s = time.perf_counter() - t0
+    e2e_tot_s, e2e_units = aggregate(e2e_s, m * e2e_steps, world, dev)
+    if int(asm.d_status.item()) != 0:
+        raise RuntimeError("device status not OK after the e2e steps")
+
+    # ---- CPU oracle baseline (rank 0, N = 1 only) ----
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        sample = min(args.cpu_sample, m)
+        rate, dt = oracle_rate(d, spec["mode"], sample)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"first {sample} of the {m} writes of this stream, std::map build + in-order walk, "
+                         f"1 thread, {dt:.1f} s"}
+
+    clocks = sampler.summary()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if sv == 8 else "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "description": spec["desc"], "m": m, "n_rows": n_rows,
+                       "n_cols": n_cols, "nnz": nnz, "mode": spec["mode"],
+                       "l2": "inputs larger than the 129 MB L2 (no flush between steps)",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_units / e2e_tot_s, "unit": UNIT, "h2d_bytes_per_step": m * (8 + sv),
+                    "d2h_bytes_per_step": d2h, "steps": e2e_steps},
+            "clocks": clocks,
+            "gpu_launches": launches,
+            "gpu": torch.cuda.get_device_name(dev),
+            "source_hash": source_hash(),
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,255 @@
+/*
+ * spm.h -- C ABI of the GB300 (sm_103a) sync-step library.
+ *
+ * The operation is the "sync" of the hybrid sparse matrix class described by
+ * Sanderson & Curtin, "A User-Friendly Hybrid Sparse Matrix Class in C++"
+ * (LNCS 10931, 2018): element writes collected outside the compressed format
+ * (the red-black-tree / coordinate-list side, Sections 3.2-3.4) are turned into
+ * canonical Compressed Sparse Column storage (Section 3.1).  Here the writes
+ * arrive as an unordered stream of (row, col, value[, seq]) and the library
+ * performs, on the GPU, what the paper's in-order tree traversal performs on
+ * the CPU: order the elements by the linear index row + col*n_rows (Section
+ * 3.3), resolve repeated writes to one element (element setting "X(r,c) = v"
+ * or batch insertion with accumulation "X(r,c) += v", Table 1 and Fig. 2),
+ * drop elements that are zero (CSC stores non-zero elements only, Section
+ * 3.1) and emit values, row indices and column offsets (c[0] = 0,
+ * c[n_cols] = N).
+ *
+ * Conventions for every call:
+ *   - All pointers are DEVICE pointers unless the parameter name starts with
+ *     h_ (host memory).  The caller allocates and owns every buffer, including
+ *     the workspace; the library never allocates, frees or synchronises.
+ *   - Work is enqueued on `stream` (a cudaStream_t; NULL = legacy default
+ *     stream) and returns immediately.  A call can be captured in a CUDA graph
+ *     once its first call on the device has returned (that first call reads
+ *     device attributes).
+ *   - Host-detectable errors (NULL pointers, negative sizes, index spaces that
+ *     are too large, a workspace that is too small) return an error status and
+ *     launch nothing.  Errors found by the kernels (an index outside the
+ *     matrix, a bounded wait that expired) are written to the device int32
+ *     *d_status (0 = SPM_OK) and the call itself returns SPM_OK ("launched");
+ *     read *d_status after the stream has completed.  When *d_status is not
+ *     SPM_OK the CSC output is unspecified, but no memory outside the given
+ *     buffers is touched.
+ *   - Sizes: n_rows, n_cols < 2^31 (int32 indices), n_rows * n_cols <= 2^52,
+ *     total writes per call m < 2^32 - 64.
+ */
+#ifndef SPM_H_
+#define SPM_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SPM_OK = 0,
+  SPM_ERR_INVALID_ARG = 1,
+  SPM_ERR_INDEX_OUT_OF_RANGE = 2,
+  SPM_ERR_WORKSPACE_TOO_SMALL = 3,
+  SPM_ERR_UNSUPPORTED = 4,
+  SPM_ERR_CUDA = 5,
+  SPM_ERR_TIMEOUT = 6
+} spm_status;
+
+/* Duplicate resolution.  LAST_WRITE: element setting, X(r,c) = v (Table 1);
+ * the write with the largest (seq, position) wins and its value is copied
+ * bit for bit.  SUM: batch insertion with accumulation, X(r,c) += v (Fig. 2);
+ * the writes to one element are added in (seq, position) order in double
+ * precision and rounded once to the output type. */
+typedef enum { SPM_MODE_LAST_WRITE = 0, SPM_MODE_SUM = 1 } spm_mode;
+
+/* Value type of the writes and of the CSC values.  SPM_F32 values are
+ * accumulated in double precision in SUM mode; indices are never affected. */
+typedef enum { SPM_F32 = 0, SPM_F64 = 1 } spm_dtype;
+
+/* flags */
+enum {
+  SPM_KEEP_MAP = 1,      /* write map[t] for every write t (see below)               */
+  SPM_CHECK_BOUNDS = 2,  /* accepted for compatibility: bounds are always checked    */
+  SPM_SEQ_EXPLICIT = 4   /* seq != NULL; must be set when sizing the workspace too   */
+};
+
+/* Human-readable name of a status code (static string). */
+const char* spm_status_string(spm_status s);
+
+/* Version of this library as major*10000 + minor*100 + patch. */
+int32_t spm_version(void);
+
+/*
+ * spm_assemble_csc_workspace -- bytes of device workspace that
+ * spm_assemble_csc needs for these sizes, dtype, mode and flags.
+ * Returns SPM_ERR_INVALID_ARG / SPM_ERR_UNSUPPORTED for sizes the call would
+ * reject.  The workspace needs no initialisation and may be reused by
+ * successive calls on the same stream.
+ */
+spm_status spm_assemble_csc_workspace(int64_t n_rows, int64_t n_cols, int64_t m, spm_dtype dtype,
+                                      spm_mode mode, uint32_t flags, size_t* bytes);
+
+/*
+ * spm_assemble_csc -- canonical CSC of the n_rows x n_cols matrix that the m
+ * element writes (rows[t], cols[t], vals[t]) produce, Section 3.1 / 3.3.
+ *
+ *   rows, cols  int32[m]                zero-based indices; any index outside
+ *                                       [0,n_rows) x [0,n_cols) sets
+ *                                       *d_status = SPM_ERR_INDEX_OUT_OF_RANGE
+ *   vals        float[m] or double[m]   per dtype
+ *   seq         NULL, or uint64[m]      order of the writes (larger = later;
+ *                                       equal seq keeps stream order); requires
+ *                                       SPM_SEQ_EXPLICIT in flags
+ *   col_ptr     int64[n_cols+1]         output column offsets, col_ptr[0] = 0,
+ *                                       col_ptr[n_cols] = nnz
+ *   row_idx     int32[m]                output row indices (first nnz used)
+ *   out_vals    float[m] or double[m]   output values (first nnz used)
+ *   d_nnz       int64[1]                output number of stored elements
+ *   map         NULL, or int32[m]       with SPM_KEEP_MAP: the CSC slot that
+ *                                       write t feeds; -1 if the write was
+ *                                       overwritten (LAST_WRITE mode); -2 if its
+ *                                       element is not stored because its value
+ *                                       is zero
+ *   d_status    int32[1]                device status, see conventions
+ *   workspace   ws_bytes bytes          at least spm_assemble_csc_workspace()
+ *
+ * Output is canonical: rows strictly increase inside each column and no stored
+ * value compares equal to zero (so -0.0 is dropped, NaN is kept).  With m = 0
+ * the result is an all-zero col_ptr.
+ */
+spm_status spm_assemble_csc(int64_t n_rows, int64_t n_cols, int64_t m, const int32_t* rows,
+                            const int32_t* cols, const void* vals, const uint64_t* seq, spm_dtype dtype,
+                            spm_mode mode, uint32_t flags, int64_t* col_ptr, int32_t* row_idx,
+                            void* out_vals, int64_t* d_nnz, int32_t* map, int32_t* d_status,
+                            void* workspace, size_t ws_bytes, void* stream);
+
+/*
+ * spm_assemble_csc_batched_workspace / spm_assemble_csc_batched -- the same
+ * sync step for `batch` independent matrices in one call (one sequence of
+ * kernels for the whole batch; no host synchronisation, so the call can be
+ * captured in a CUDA graph and replayed).
+ *
+ *   h_n_rows, h_n_cols  host int64[batch]     matrix sizes
+ *   h_trip_ptr          host int64[batch+1]   writes of matrix i are
+ *                                             [h_trip_ptr[i], h_trip_ptr[i+1])
+ *                                             of the concatenated streams;
+ *                                             h_trip_ptr[0] = 0
+ *   d_n_rows, d_n_cols, d_trip_ptr            device copies of the same arrays
+ *                                             (read by the kernels; a mismatch
+ *                                             with the host copies is reported
+ *                                             as SPM_ERR_INVALID_ARG in *d_status)
+ *   rows, cols, vals, seq                     concatenated as for one matrix
+ *   col_ptr   int64[sum_i (n_cols_i + 1)]     matrix i's offsets start at
+ *                                             sum_{j<i} (n_cols_j + 1); each
+ *                                             matrix's offsets start at 0
+ *   row_idx, out_vals  [total writes]         matrix i's elements start at
+ *                                             h_trip_ptr[i] (capacity m_i)
+ *   d_nnz     int64[batch]                    stored elements per matrix
+ *   map       NULL or int32[total writes]     as for one matrix (slots are
+ *                                             relative to matrix i's start)
+ */
+spm_status spm_assemble_csc_batched_workspace(int64_t batch, const int64_t* h_n_rows,
+                                              const int64_t* h_n_cols, const int64_t* h_trip_ptr,
+                                              spm_dtype dtype, spm_mode mode, uint32_t flags,
+                                              size_t* bytes);
+
+spm_status spm_assemble_csc_batched(int64_t batch, const int64_t* h_n_rows, const int64_t* h_n_cols,
+                                    const int64_t* h_trip_ptr, const int64_t* d_n_rows,
+                                    const int64_t* d_n_cols, const int64_t* d_trip_ptr,
+                                    const int32_t* rows, const int32_t* cols, const void* vals,
+                                    const uint64_t* seq, spm_dtype dtype, spm_mode mode, uint32_t flags,
+                                    int64_t* col_ptr, int32_t* row_idx, void* out_vals, int64_t* d_nnz,
+                                    int32_t* map, int32_t* d_status, void* workspace, size_t ws_bytes,
+                                    void* stream);
+
+/*
+ * spm_csc_mm -- Y = A X (transpose = 0) or Y = A^T X (transpose = 1) for A in
+ * CSC (Section 3.1; the paper's use cases (iv) "multiplication of dense
+ * vectors with sparse matrices", Fig. 2 "W = V * X").
+ *
+ *   col_ptr int64[n_cols+1], row_idx int32[nnz], vals (dtype)[nnz]   A
+ *   X   (dtype) row-major, (transpose ? n_rows : n_cols) x k, leading dim ldx
+ *   Y   (dtype) row-major, (transpose ? n_cols : n_rows) x k, leading dim ldy;
+ *       overwritten.  ldx, ldy >= k.  X and Y must not overlap.
+ * Accumulation is in the value type.  Y = A X adds the contributions of each
+ * column with atomic adds (order not fixed); Y = A^T X gathers each output row
+ * in storage order.
+ */
+spm_status spm_csc_mm(int64_t n_rows, int64_t n_cols, const int64_t* col_ptr, const int32_t* row_idx,
+                      const void* vals, spm_dtype dtype, int32_t transpose, int64_t k, const void* X,
+                      int64_t ldx, void* Y, int64_t ldy, void* stream);
+
+/*
+ * spm_triplet_dvals -- gradient of a scalar loss L with respect to the value
+ * of every write, given dL/dY for Y = A X with A assembled from the writes:
+ *     dvals[t] = sum_j dY[rows[t], j] * X[cols[t], j]
+ * except dvals[t] = 0 when map != NULL and map[t] == -1 (a write that was
+ * overwritten does not influence A).  A coordinate dropped because its value
+ * is zero still passes its gradient (A is continuous there).
+ *
+ *   rows, cols int32[m]; map NULL or int32[m] (from spm_assemble_csc)
+ *   dY  (dtype) row-major n_rows x k, leading dim lddy
+ *   X   (dtype) row-major n_cols x k, leading dim ldx
+ *   dvals (dtype)[m]  output
+ */
+spm_status spm_triplet_dvals(int64_t m, const int32_t* rows, const int32_t* cols, const int32_t* map,
+                             spm_dtype dtype, int64_t k, const void* dY, int64_t lddy, const void* X,
+                             int64_t ldx, void* dvals, void* stream);
+
+/*
+ * Tuning parameters of the assembly kernels (process-wide; the autotuner
+ * sets them).  A call with NULL restores the defaults.  Changing them changes
+ * the workspace size, so query the workspace after setting them.
+ *   bucket_target      expected writes per bucket the planner aims for
+ *                      (256 .. 8192)
+ *   sub_bits           log2 of the counting-sort digit used inside a bucket
+ *                      (8 .. 12)
+ *   partition_threads  threads per block of the histogram/scatter kernels
+ *                      (256, 512 or 1024)
+ *   resolve_threads    threads per block of the per-bucket kernel (256 or 512)
+ */
+typedef struct {
+  int32_t bucket_target;
+  int32_t sub_bits;
+  int32_t partition_threads;
+  int32_t resolve_threads;
+} spm_tuning;
+
+spm_status spm_set_tuning(const spm_tuning* t);
+spm_status spm_get_tuning(spm_tuning* t);
+
+/*
+ * spm_debug_withhold_publication -- fault injection for tests of the failure
+ * path (the paper has no counterpart).  While set to b >= 0, the block that
+ * resolves bucket b of an assembly call publishes no look-back state, so the
+ * blocks of the following buckets of the same matrix wait until their bounded
+ * wait (about 2 s) expires, record SPM_ERR_TIMEOUT in *d_status and stop.
+ * Nothing traps or hangs.  -1 (the default) switches it off.  Process-wide.
+ */
+spm_status spm_debug_withhold_publication(int64_t bucket);
+
+/*
+ * Measurement hooks for benchmarks (the paper has no counterpart).
+ *
+ * spm_debug_stage_timing(1) makes every later assembly call on the current
+ * device record CUDA events, on the call's stream, at the boundaries of its
+ * five stages: 0 planning (sampling, lookup tables, bucket descriptors),
+ * 1 histogram pass, 2 bucket offsets, 3 scatter pass, 4 per-bucket resolve.
+ * Events of the last 64 calls are kept.  spm_debug_stage_timing(0) stops
+ * recording.  Not capturable in a CUDA graph while enabled.
+ *
+ * spm_debug_stage_times(back, ms, n): after the stream has completed, writes
+ * the durations in milliseconds of the first n (<= 5) stages of the call made
+ * `back` calls ago (0 = the latest).
+ *
+ * spm_debug_launch_count(): number of kernels this library has launched so
+ * far in the process (all entry points).
+ */
+spm_status spm_debug_stage_timing(int32_t enable);
+spm_status spm_debug_stage_times(int32_t back, float* ms, int32_t n);
+int64_t spm_debug_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPM_H_ */

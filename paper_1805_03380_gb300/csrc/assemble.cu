@@ -1,0 +1,1708 @@
+// libspm: the sync step of the hybrid sparse matrix class on GB300 (sm_103a).
+//
+// The paper (Sanderson & Curtin, Section 3.3) converts its red-black tree to
+// CSC by an in-order traversal: the tree is keyed by index = row + col*n_rows,
+// so the traversal visits elements in column-major order and each index is
+// decoded with a division and a modulo.  On the GPU the same result is built
+// from an unordered write stream by a bucketed sort over that key:
+//
+//   sample   -> a few hundred thousand keys drawn at fixed pseudo-random
+//               positions give the key distribution (hot columns included)
+//   plan     -> per matrix, a two-level lookup table maps a key in O(1) to a
+//               bucket: an aligned power-of-two key range expected to hold
+//               ~bucket_target writes; hot level-1 cells are refined into 256
+//               level-2 cells so that skewed (Zipf) columns still split evenly
+//   hist     -> one pass over (row, col) counts writes per (block, bucket)
+//   scan     -> per-bucket and per-(block, bucket) offsets
+//   scatter  -> one pass over (row, col, value[, seq]) writes a record
+//               (key-within-bucket << 32 | stream position, value) into the
+//               bucket's contiguous range
+//   resolve  -> a persistent kernel takes buckets in order; each bucket is
+//               sorted in shared memory (counting sort on the top key bits,
+//               then a short insertion sort per sub-range by (key, seq,
+//               position)), duplicate writes are resolved (last write wins,
+//               or a float64 sum in write order), zeros are dropped, and the
+//               bucket's output offset comes from a decoupled look-back over
+//               the preceding buckets of the same matrix; the CSC arrays and
+//               the column offsets of every column that starts inside the
+//               bucket are written directly.
+//
+// No kernel ever traps or spins without a bound: out-of-range indices and
+// expired waits are reported in the device status word.
+
+#include <algorithm>
+#include <cstdint>
+#include <cstring>
+#include <atomic>
+#include <mutex>
+#include <vector>
+
+#include "spm_common.cuh"
+
+namespace spm {
+
+// ===========================================================================
+// Small device helpers
+// ===========================================================================
+__device__ __forceinline__ void record_error(const Ctx& c, int code) { atomicCAS(c.status, 0, code); }
+
+__device__ __forceinline__ void record_fatal(const Ctx& c, int code) {
+  atomicCAS(c.status, 0, code);
+  atomicExch(&c.scal->abort, 1u);
+}
+
+__device__ __forceinline__ bool is_aborted(const Ctx& c) {
+  return *reinterpret_cast<volatile uint32_t*>(&c.scal->abort) != 0u;
+}
+
+__device__ __forceinline__ uint64_t global_timer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ uint64_t ld_acquire_u64(const uint64_t* p) {
+  uint64_t v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release_u64(uint64_t* p, uint64_t v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ uint32_t mix32(uint64_t x) {
+  x ^= x >> 33;
+  x *= 0xff51afd7ed558ccdull;
+  x ^= x >> 33;
+  x *= 0xc4ceb9fe1a85ec53ull;
+  x ^= x >> 33;
+  return (uint32_t)x;
+}
+
+// Exclusive scan of one value per thread over the block (blockDim a multiple
+// of 32, at most 1024).  buf needs 32 entries.  Returns the prefix; *total
+// receives the block total.  Contains __syncthreads.
+template <typename T>
+__device__ T block_scan_excl(T v, T* total, T* buf) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  T x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    T y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) buf[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    T w = lane < nw ? buf[lane] : T(0);
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      T y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    buf[lane] = w;
+  }
+  __syncthreads();
+  T res = (warp ? buf[warp - 1] : T(0)) + x - v;
+  if (total) *total = buf[nw - 1];
+  __syncthreads();
+  return res;
+}
+
+// Largest i in [lo, hi] with key(i) <= x (requires key(lo) <= x).
+template <typename F>
+__device__ __forceinline__ int64_t upper_index(int64_t lo, int64_t hi, int64_t x, F key) {
+  while (lo < hi) {
+    int64_t mid = lo + (hi - lo + 1) / 2;
+    if (key(mid) <= x) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ uint32_t isqrt_u32(uint32_t x) {
+  uint32_t r = (uint32_t)sqrtf((float)x);
+  while ((uint64_t)r * r > x) --r;
+  while ((uint64_t)(r + 1) * (r + 1) <= x) ++r;
+  return r;
+}
+
+// ===========================================================================
+// Setup: per-matrix metadata
+// ===========================================================================
+__global__ void k_setup_single(Ctx c, MatMeta mm) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) c.meta[0] = mm;
+}
+
+__global__ void k_setup_batched(Ctx c, const int64_t* __restrict__ d_n_rows, const int64_t* __restrict__ d_n_cols,
+                                const int64_t* __restrict__ d_trip, int64_t exp_S, int64_t exp_lut, int64_t exp_l2,
+                                int64_t exp_nbcap, int64_t exp_cols, unsigned long long exp_hash) {
+  __shared__ unsigned long long buf[32];
+  __shared__ unsigned long long tot;
+  __shared__ unsigned long long hsum;
+  __shared__ int bad;
+  if (threadIdx.x == 0) {
+    bad = 0;
+    hsum = 0;
+  }
+  unsigned long long carry[5] = {0, 0, 0, 0, 0};
+  __syncthreads();
+  for (int64_t base = 0; base < c.B; base += blockDim.x) {
+    const int64_t i = base + threadIdx.x;
+    const bool ok = i < c.B;
+    MatMeta mm;
+    memset(&mm, 0, sizeof(mm));
+    unsigned long long q[5] = {0, 0, 0, 0, 0};
+    if (ok) {
+      mm.n_rows = d_n_rows[i];
+      mm.n_cols = d_n_cols[i];
+      mm.t0 = d_trip[i];
+      const int64_t t1 = d_trip[i + 1];
+      mm.m = t1 - mm.t0;
+      atomicAdd(&hsum, (unsigned long long)meta_term(i, mm.n_rows, mm.n_cols, t1));
+      if (i == 0 && mm.t0 != 0) atomicExch(&bad, 1);
+      bool invalid = mm.n_rows < 0 || mm.n_cols < 0 || mm.n_rows > 0x7fffffffLL || mm.n_cols > 0x7fffffffLL ||
+                     mm.m < 0 || mm.t0 < 0 || t1 > c.m_total;
+      if (!invalid) {
+        Derived d = derive(mm.n_rows, mm.n_cols, mm.m, c.m_total, c.tgt);
+        if (d.bbits > kMaxKeyBits) invalid = true;
+        mm.K = d.K;
+        mm.bbits = d.bbits;
+        mm.L1 = d.L1;
+        mm.s1 = d.s1;
+        mm.H2 = d.H2;
+        mm.ns = d.ns;
+        mm.lut_len = d.lut_len;
+        mm.nbcap = d.nbcap;
+        q[0] = (unsigned long long)d.ns;
+        q[1] = (unsigned long long)d.lut_len;
+        q[2] = (unsigned long long)d.H2;
+        q[3] = (unsigned long long)d.nbcap;
+        q[4] = (unsigned long long)(mm.n_cols + 1);
+      }
+      if (invalid) atomicExch(&bad, 1);
+    }
+    unsigned long long off[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      off[k] = block_scan_excl<unsigned long long>(q[k], &tot, buf) + carry[k];
+      carry[k] += tot;
+    }
+    if (ok) {
+      mm.samp_off = (int64_t)off[0];
+      mm.lut_off = (int64_t)off[1];
+      mm.l2_off = (int64_t)off[2];
+      mm.nbcap_off = (int64_t)off[3];
+      mm.col_base = (int64_t)off[4];
+      c.meta[i] = mm;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (bad || hsum != exp_hash || (int64_t)carry[0] != exp_S || (int64_t)carry[1] != exp_lut || (int64_t)carry[2] != exp_l2 ||
+        (int64_t)carry[3] != exp_nbcap || (int64_t)carry[4] != exp_cols)
+      record_fatal(c, SPM_ERR_INVALID_ARG);
+  }
+}
+
+// ===========================================================================
+// Sampling
+// ===========================================================================
+__global__ void k_sample(Ctx c) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= c.S_total || is_aborted(c)) return;
+  const MatMeta* meta = c.meta;
+  const int64_t i = upper_index(0, c.B - 1, g, [&](int64_t j) { return meta[j].samp_off; });
+  const MatMeta& mm = meta[i];
+  const uint64_t k = (uint64_t)(g - mm.samp_off);
+  const uint64_t m = (uint64_t)mm.m, ns = (uint64_t)mm.ns;
+  uint64_t p;
+  if (ns >= m) {
+    p = k;
+  } else {
+    const uint64_t a = k * m / ns, b = (k + 1) * m / ns;
+    p = a + (b > a ? mix32((uint64_t)g * 0x9e3779b97f4a7c15ull + 17) % (b - a) : 0);
+  }
+  const int64_t t = mm.t0 + (int64_t)p;
+  const int32_t r = c.rows[t], col = c.cols[t];
+  uint64_t key = kBadKey;
+  if (r >= 0 && (int64_t)r < mm.n_rows && col >= 0 && (int64_t)col < mm.n_cols)
+    key = (uint64_t)col * (uint64_t)mm.n_rows + (uint64_t)r;
+  c.samp[g] = key;
+}
+
+// ===========================================================================
+// Planning: one block per matrix
+// ===========================================================================
+struct Split {
+  int j;
+  uint32_t count;
+};
+
+__device__ __forceinline__ Split leaf_split(uint64_t lo, int shift, uint64_t est, uint64_t tgt, uint64_t K) {
+  Split s{0, 0};
+  if (lo >= K) return s;
+  int j = 0;
+  if (est > tgt) j = ceil_log2_u64((est + tgt - 1) / tgt);
+  if (j > shift) j = shift;
+  if (j > 31) j = 31;
+  if (j < shift - 32) j = shift - 32;
+  const int w = shift - j;
+  const uint64_t n = ((K - lo) + ((uint64_t{1} << w) - 1)) >> w;
+  const uint64_t full = uint64_t{1} << j;
+  s.j = j;
+  s.count = (uint32_t)(n < full ? n : full);
+  return s;
+}
+
+__device__ __forceinline__ uint64_t estimate(uint32_t cnt, const MatMeta& mm) {
+  if (mm.ns <= 0) return 0;
+  if (mm.ns >= mm.m) return cnt;
+  const uint64_t x = (uint64_t)cnt + 2ull * isqrt_u32(cnt) + 1ull;  // upper confidence margin
+  return x * (uint64_t)mm.m / (uint64_t)mm.ns;
+}
+
+__global__ void __launch_bounds__(512) k_plan(Ctx c) {
+  __shared__ MatMeta mm;
+  __shared__ uint32_t buf[32];
+  __shared__ uint32_t s_tot;
+  __shared__ uint32_t s_red;
+  const int64_t i = blockIdx.x;
+  if (threadIdx.x == 0) mm = c.meta[i];
+  __syncthreads();
+  if (is_aborted(c)) return;
+  uint32_t* cnt = c.cellcnt + mm.lut_off;
+  uint32_t* lut = c.lut + mm.lut_off;
+  int32_t* l2cell = c.l2cell + mm.l2_off;
+  const int64_t L1size = int64_t{1} << mm.L1;
+  if (mm.K == 0) {
+    if (threadIdx.x == 0) {
+      lut[0] = 0;
+      c.meta[i].nb = 1;
+      c.meta[i].h2used = 0;
+    }
+    return;
+  }
+  const uint64_t* samp = c.samp + mm.samp_off;
+  // level-1 counts
+  for (int64_t k = threadIdx.x; k < mm.ns; k += blockDim.x) {
+    const uint64_t key = samp[k];
+    if (key != kBadKey) atomicAdd(&cnt[key >> mm.s1], 1u);
+  }
+  __syncthreads();
+  // choose the cells refined by a level-2 table: the heaviest cells whose
+  // estimate exceeds 8 buckets' worth, at most H2 of them
+  uint32_t h = 0;
+  const uint64_t tgt = (uint64_t)c.tgt;
+  if (mm.H2 > 0) {
+    const uint64_t thr = 8ull * tgt;
+    uint32_t mx = 0;
+    for (int64_t cell = threadIdx.x; cell < L1size; cell += blockDim.x) mx = max(mx, cnt[cell]);
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (threadIdx.x == 0) s_red = 0;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) atomicMax(&s_red, mx);
+    __syncthreads();
+    mx = s_red;
+    __syncthreads();
+    uint32_t lo = 1, hi = mx + 1;  // smallest tau with at most H2 candidates
+    while (lo < hi) {
+      const uint32_t mid = lo + (hi - lo) / 2;
+      uint32_t n = 0;
+      for (int64_t cell = threadIdx.x; cell < L1size; cell += blockDim.x)
+        n += (cnt[cell] >= mid && estimate(cnt[cell], mm) > thr) ? 1u : 0u;
+      for (int o = 16; o > 0; o >>= 1) n += __shfl_xor_sync(0xffffffffu, n, o);
+      if (threadIdx.x == 0) s_red = 0;
+      __syncthreads();
+      if ((threadIdx.x & 31) == 0) atomicAdd(&s_red, n);
+      __syncthreads();
+      n = s_red;
+      __syncthreads();
+      if (n <= (uint32_t)mm.H2) hi = mid; else lo = mid + 1;
+    }
+    const uint32_t tau = lo;
+    uint32_t carry = 0;
+    for (int64_t base = 0; base < L1size; base += blockDim.x) {
+      const int64_t cell = base + threadIdx.x;
+      uint32_t f = 0;
+      if (cell < L1size) f = (cnt[cell] >= tau && estimate(cnt[cell], mm) > thr) ? 1u : 0u;
+      const uint32_t off = block_scan_excl<uint32_t>(f, &s_tot, buf) + carry;
+      if (cell < L1size) {
+        lut[cell] = f ? (kPtrFlag | off) : 0u;
+        if (f) l2cell[off] = (int32_t)cell;
+      }
+      carry += s_tot;
+    }
+    h = carry;
+  } else {
+    for (int64_t cell = threadIdx.x; cell < L1size; cell += blockDim.x) lut[cell] = 0u;
+  }
+  __syncthreads();
+  // level-2 counts
+  if (h > 0) {
+    const int s2 = mm.s1 - kL2Bits;
+    for (int64_t k = threadIdx.x; k < mm.ns; k += blockDim.x) {
+      const uint64_t key = samp[k];
+      if (key == kBadKey) continue;
+      const uint32_t e = lut[key >> mm.s1];
+      if (e & kPtrFlag)
+        atomicAdd(&cnt[L1size + (int64_t)(e & ~kPtrFlag) * kL2Size + ((key >> s2) & (kL2Size - 1))], 1u);
+    }
+  }
+  __syncthreads();
+  // number of buckets per leaf; retry with a larger target if over the cap
+  uint64_t tg = tgt;
+  uint32_t nb_total = 0;
+  for (int attempt = 0;; ++attempt) {
+    uint32_t carry = 0;
+    for (int64_t base = 0; base < L1size; base += blockDim.x) {
+      const int64_t cell = base + threadIdx.x;
+      uint32_t nbc = 0;
+      if (cell < L1size) {
+        const uint32_t e = lut[cell];
+        const uint64_t clo = (uint64_t)cell << mm.s1;
+        if (e & kPtrFlag) {
+          const uint32_t* c2 = cnt + L1size + (int64_t)(e & ~kPtrFlag) * kL2Size;
+          const int s2 = mm.s1 - kL2Bits;
+          for (int u = 0; u < kL2Size; ++u)
+            nbc += leaf_split(clo + ((uint64_t)u << s2), s2, estimate(c2[u], mm), tg, mm.K).count;
+        } else {
+          nbc = leaf_split(clo, mm.s1, estimate(cnt[cell], mm), tg, mm.K).count;
+        }
+      }
+      block_scan_excl<uint32_t>(nbc, &s_tot, buf);
+      carry += s_tot;
+    }
+    nb_total = carry;
+    if ((int64_t)nb_total <= mm.nbcap || attempt >= 48) break;
+    tg *= 2;
+  }
+  if ((int64_t)nb_total > mm.nbcap) {
+    if (threadIdx.x == 0) record_fatal(c, SPM_ERR_UNSUPPORTED);
+    return;
+  }
+  // write the leaf entries: j in bits 26..30, first local bucket in bits 0..25
+  uint32_t carry = 0;
+  for (int64_t base = 0; base < L1size; base += blockDim.x) {
+    const int64_t cell = base + threadIdx.x;
+    uint32_t nbc = 0;
+    uint32_t e = 0;
+    Split s1v{0, 0};
+    const uint64_t clo = (uint64_t)cell << mm.s1;
+    if (cell < L1size) {
+      e = lut[cell];
+      if (e & kPtrFlag) {
+        const uint32_t* c2 = cnt + L1size + (int64_t)(e & ~kPtrFlag) * kL2Size;
+        const int s2 = mm.s1 - kL2Bits;
+        for (int u = 0; u < kL2Size; ++u)
+          nbc += leaf_split(clo + ((uint64_t)u << s2), s2, estimate(c2[u], mm), tg, mm.K).count;
+      } else {
+        s1v = leaf_split(clo, mm.s1, estimate(cnt[cell], mm), tg, mm.K);
+        nbc = s1v.count;
+      }
+    }
+    const uint32_t off = block_scan_excl<uint32_t>(nbc, &s_tot, buf) + carry;
+    if (cell < L1size) {
+      if (e & kPtrFlag) {
+        const int64_t tb = (int64_t)(e & ~kPtrFlag);
+        const uint32_t* c2 = cnt + L1size + tb * kL2Size;
+        uint32_t* l2 = lut + L1size + tb * kL2Size;
+        const int s2 = mm.s1 - kL2Bits;
+        uint32_t run = off;
+        for (int u = 0; u < kL2Size; ++u) {
+          const Split sp = leaf_split(clo + ((uint64_t)u << s2), s2, estimate(c2[u], mm), tg, mm.K);
+          l2[u] = ((uint32_t)sp.j << kBaseBits) | run;
+          run += sp.count;
+        }
+      } else {
+        lut[cell] = ((uint32_t)s1v.j << kBaseBits) | off;
+      }
+    }
+    carry += s_tot;
+  }
+  if (threadIdx.x == 0) {
+    c.meta[i].nb = nb_total;
+    c.meta[i].h2used = (int32_t)h;
+  }
+}
+
+// Bucket offsets of the matrices and the ranges of the partition blocks.
+__global__ void k_bucket_scan(Ctx c) {
+  __shared__ unsigned long long buf[32];
+  __shared__ unsigned long long tot;
+  if (is_aborted(c)) return;
+  unsigned long long carry = 0, lcarry = 0;
+  for (int64_t base = 0; base < c.B; base += blockDim.x) {
+    const int64_t i = base + threadIdx.x;
+    const unsigned long long nb = i < c.B ? (unsigned long long)c.meta[i].nb : 0ull;
+    const unsigned long long off = block_scan_excl<unsigned long long>(nb, &tot, buf) + carry;
+    if (i < c.B) c.meta[i].bucket_off = (int64_t)off;
+    carry += tot;
+    const unsigned long long used =
+        i < c.B ? (unsigned long long)((int64_t{1} << c.meta[i].L1) + (int64_t)c.meta[i].h2used * kL2Size) : 0ull;
+    const unsigned long long loff = block_scan_excl<unsigned long long>(used, &tot, buf) + lcarry;
+    if (i < c.B) c.meta[i].lut_used_off = (int64_t)loff;
+    lcarry += tot;
+  }
+  if (threadIdx.x == 0) {
+    if (carry > (unsigned long long)c.nbcap_total) record_fatal(c, SPM_ERR_UNSUPPORTED);
+    c.scal->NB = (uint32_t)carry;
+  }
+  __syncthreads();
+  const MatMeta* meta = c.meta;
+  unsigned long long hcarry = 0;
+  for (int64_t base = 0; base < c.C; base += blockDim.x) {
+    const int64_t cc = base + threadIdx.x;
+    CtaInfo ci;
+    memset(&ci, 0, sizeof(ci));
+    unsigned long long range = 0;
+    if (cc < c.C) {
+      ci.e0 = chunk_begin(c.m_total, cc, c.C);
+      ci.e1 = chunk_begin(c.m_total, cc + 1, c.C);
+      ci.i0 = 0;
+      ci.i1 = -1;
+      if (ci.e0 < ci.e1) {
+        const int64_t i0 = upper_index(0, c.B - 1, ci.e0, [&](int64_t j) { return meta[j].t0; });
+        const int64_t i1 = upper_index(0, c.B - 1, ci.e1 - 1, [&](int64_t j) { return meta[j].t0; });
+        ci.i0 = (int32_t)i0;
+        ci.i1 = (int32_t)i1;
+        ci.cb0 = (uint32_t)meta[i0].bucket_off;
+        ci.cb1 = (uint32_t)(meta[i1].bucket_off + meta[i1].nb);
+        ci.l0 = meta[i0].lut_used_off;
+        ci.l1 = meta[i1].lut_used_off + (int64_t{1} << meta[i1].L1) + (int64_t)meta[i1].h2used * kL2Size;
+        range = ci.cb1 - ci.cb0;
+      }
+    }
+    const unsigned long long off = block_scan_excl<unsigned long long>(range, &tot, buf) + hcarry;
+    if (cc < c.C) {
+      ci.hoff = (int64_t)off;
+      c.cta[cc] = ci;
+    }
+    hcarry += tot;
+  }
+  if (threadIdx.x == 0 && hcarry > (unsigned long long)c.hist_bound) record_fatal(c, SPM_ERR_UNSUPPORTED);
+}
+
+// Bucket descriptors (first key and width) from the leaf entries: one warp per
+// LUT entry.
+__global__ void k_bucket_fill(Ctx c) {
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (gw >= c.lut_total || is_aborted(c)) return;
+  const MatMeta* meta = c.meta;
+  const int64_t i = upper_index(0, c.B - 1, gw, [&](int64_t j) { return meta[j].lut_off; });
+  const MatMeta& mm = meta[i];
+  const int64_t e = gw - mm.lut_off;
+  if (e >= mm.lut_len) return;
+  if (mm.K == 0) {
+    if (e == 0 && lane == 0) {
+      c.bk_lo[mm.bucket_off] = 0;
+      c.bk_info[mm.bucket_off] = ((uint32_t)i << 6) | 0u;
+    }
+    return;
+  }
+  const int64_t L1size = int64_t{1} << mm.L1;
+  uint64_t lo;
+  int shift;
+  const uint32_t ent = c.lut[gw];
+  if (e < L1size) {
+    if (ent & kPtrFlag) return;
+    lo = (uint64_t)e << mm.s1;
+    shift = mm.s1;
+  } else {
+    const int64_t tb = (e - L1size) >> kL2Bits;
+    const int64_t u = (e - L1size) & (kL2Size - 1);
+    if (tb >= mm.h2used) return;
+    const int64_t cell = c.l2cell[mm.l2_off + tb];
+    shift = mm.s1 - kL2Bits;
+    lo = ((uint64_t)cell << mm.s1) + ((uint64_t)u << shift);
+  }
+  if (lo >= mm.K) return;
+  const int j = (ent >> kBaseBits) & 31;
+  const uint32_t base = ent & kBaseMask;
+  const int w = shift - j;
+  const uint64_t n = ((mm.K - lo) + ((uint64_t{1} << w) - 1)) >> w;
+  const uint64_t full = uint64_t{1} << j;
+  const uint64_t count = n < full ? n : full;
+  for (uint64_t q = lane; q < count; q += 32) {
+    const int64_t b = mm.bucket_off + base + (int64_t)q;
+    c.bk_lo[b] = lo + (q << w);
+    c.bk_info[b] = ((uint32_t)i << 6) | (uint32_t)w;
+  }
+}
+
+// ===========================================================================
+// Partition: histogram and scatter
+// ===========================================================================
+// Current matrix of a thread while it walks its writes in increasing order.
+struct MatView {
+  int64_t idx, t_end;
+  uint64_t n_rows, n_cols;
+  int s1;
+  int64_t L1size;
+  const uint32_t* lut;      // this matrix's LUT (shared or global memory)
+  int64_t bucket_rel;       // bucket_off - cb0
+};
+
+__device__ __forceinline__ void load_view(const Ctx& c, const CtaInfo& ci, const uint32_t* lut_base, bool lut_smem,
+                                          int64_t i, MatView& v) {
+  const MatMeta& mm = c.meta[i];
+  v.idx = i;
+  v.t_end = mm.t0 + mm.m;
+  v.n_rows = (uint64_t)mm.n_rows;
+  v.n_cols = (uint64_t)mm.n_cols;
+  v.s1 = mm.s1;
+  v.L1size = int64_t{1} << mm.L1;
+  v.lut = lut_smem ? (lut_base + (mm.lut_used_off - ci.l0)) : (c.lut + mm.lut_off);
+  v.bucket_rel = mm.bucket_off - (int64_t)ci.cb0;
+}
+
+// Classify one write: bucket (relative to the block's range) and key within
+// the bucket.  Returns false for an index outside the matrix.
+__device__ __forceinline__ bool classify(const MatView& v, int32_t r, int32_t col, uint32_t& brel, uint32_t& lkey) {
+  if (r < 0 || col < 0 || (uint64_t)r >= v.n_rows || (uint64_t)col >= v.n_cols) return false;
+  const uint64_t key = (uint64_t)col * v.n_rows + (uint64_t)r;
+  uint32_t e = v.lut[key >> v.s1];
+  int sh = v.s1;
+  if (e & kPtrFlag) {
+    sh = v.s1 - kL2Bits;
+    e = v.lut[v.L1size + (int64_t)(e & ~kPtrFlag) * kL2Size + ((key >> sh) & (kL2Size - 1))];
+  }
+  const int j = (e >> kBaseBits) & 31;
+  const int w = sh - j;
+  const uint32_t sub = (uint32_t)((key >> w) & ((uint64_t{1} << j) - 1));
+  brel = (uint32_t)(v.bucket_rel + (int64_t)(e & kBaseMask) + sub);
+  lkey = (uint32_t)(key & ((uint64_t{1} << w) - 1));
+  return true;
+}
+
+template <bool BATCHED>
+__device__ __forceinline__ void advance_view(const Ctx& c, const CtaInfo& ci, const uint32_t* lut_base, bool lut_smem,
+                                             int64_t t, MatView& v) {
+  if (BATCHED && t >= v.t_end) {
+    const MatMeta* meta = c.meta;
+    const int64_t i = upper_index(v.idx + 1, ci.i1, t, [&](int64_t j) { return meta[j].t0; });
+    load_view(c, ci, lut_base, lut_smem, i, v);
+  }
+}
+
+// Shared-memory layout of the partition kernels: [counters | LUT slice].
+__device__ __forceinline__ void partition_prologue(const Ctx& c, const CtaInfo& ci, uint32_t* sm, bool& hist_smem,
+                                                   bool& lut_smem, uint32_t*& lut_base) {
+  const int64_t range = (int64_t)ci.cb1 - (int64_t)ci.cb0;
+  const int64_t lutn = ci.l1 - ci.l0;
+  hist_smem = range <= kHistCapSmem;
+  lut_smem = lutn <= kLutCapSmem;
+  const int64_t hwords = hist_smem ? ((range + 3) & ~3ll) : 0;
+  lut_base = sm + hwords;
+  if (lut_smem) {
+    // per matrix: its level-1 table and the level-2 tables it uses, packed
+    for (int64_t i = ci.i0; i <= ci.i1; ++i) {
+      const MatMeta& mm = c.meta[i];
+      const int64_t len = (int64_t{1} << mm.L1) + (int64_t)mm.h2used * kL2Size;
+      uint32_t* dst = lut_base + (mm.lut_used_off - ci.l0);
+      const uint32_t* src = c.lut + mm.lut_off;
+      for (int64_t k = threadIdx.x; k < len; k += blockDim.x) dst[k] = src[k];
+    }
+  }
+}
+
+template <bool BATCHED, bool VEC>
+__global__ void __launch_bounds__(1024) k_hist(Ctx c) {
+  extern __shared__ __align__(16) uint32_t sm[];
+  const CtaInfo ci = c.cta[blockIdx.x];
+  if (is_aborted(c) || ci.e0 >= ci.e1) return;
+  bool hist_smem, lut_smem;
+  uint32_t* lut_base;
+  partition_prologue(c, ci, sm, hist_smem, lut_smem, lut_base);
+  const int64_t range = (int64_t)ci.cb1 - (int64_t)ci.cb0;
+  uint32_t* hist = hist_smem ? sm : (c.hist + ci.hoff);
+  for (int64_t k = threadIdx.x; k < range; k += blockDim.x) hist[k] = 0u;
+  __syncthreads();
+  MatView v;
+  load_view(c, ci, lut_base, lut_smem, ci.i0, v);
+  bool bad = false;
+  auto body = [&](int64_t t, int32_t r, int32_t col) {
+    advance_view<BATCHED>(c, ci, lut_base, lut_smem, t, v);
+    uint32_t b, lk;
+    if (classify(v, r, col, b, lk)) atomicAdd(&hist[b], 1u); else bad = true;
+  };
+  if (VEC) {
+    const int64_t nvec = (ci.e1 - ci.e0) >> 2;
+    const int4* r4p = reinterpret_cast<const int4*>(c.rows + ci.e0);
+    const int4* c4p = reinterpret_cast<const int4*>(c.cols + ci.e0);
+    for (int64_t q = threadIdx.x; q < nvec; q += blockDim.x) {
+      const int4 r4 = __ldcs(r4p + q), c4 = __ldcs(c4p + q);
+      const int64_t t = ci.e0 + 4 * q;
+      body(t, r4.x, c4.x);
+      body(t + 1, r4.y, c4.y);
+      body(t + 2, r4.z, c4.z);
+      body(t + 3, r4.w, c4.w);
+    }
+    for (int64_t t = ci.e0 + 4 * nvec + threadIdx.x; t < ci.e1; t += blockDim.x) body(t, c.rows[t], c.cols[t]);
+  } else {
+    for (int64_t t = ci.e0 + threadIdx.x; t < ci.e1; t += blockDim.x) body(t, c.rows[t], c.cols[t]);
+  }
+  if (bad) record_error(c, SPM_ERR_INDEX_OUT_OF_RANGE);
+  __syncthreads();
+  if (hist_smem)
+    for (int64_t k = threadIdx.x; k < range; k += blockDim.x) c.hist[ci.hoff + k] = hist[k];
+}
+
+// Per bucket: exclusive prefix over the partition blocks (in place) and total.
+__global__ void k_colscan(Ctx c) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= c.nbcap_total) return;
+  if (is_aborted(c)) return;
+  const int64_t NB = c.scal->NB;
+  if (b >= NB) {
+    c.bk_count[b] = 0u;
+    return;
+  }
+  uint32_t running = 0;
+  for (int64_t cc = 0; cc < c.C; ++cc) {
+    const uint32_t cb0 = c.cta[cc].cb0, cb1 = c.cta[cc].cb1;
+    if ((uint32_t)b >= cb0 && (uint32_t)b < cb1 && c.cta[cc].e0 < c.cta[cc].e1) {
+      uint32_t* p = c.hist + c.cta[cc].hoff + (b - cb0);
+      const uint32_t v = *p;
+      *p = running;
+      running += v;
+    }
+  }
+  c.bk_count[b] = running;
+}
+
+// Device-wide exclusive scan of bk_count into bk_start (three kernels).
+__global__ void k_scan_reduce(Ctx c) {
+  __shared__ uint32_t buf[32];
+  __shared__ uint32_t tot;
+  const int64_t i = (int64_t)blockIdx.x * kScanBlock + threadIdx.x;
+  const uint32_t v = i < c.nbcap_total ? c.bk_count[i] : 0u;
+  block_scan_excl<uint32_t>(v, &tot, buf);
+  if (threadIdx.x == 0) c.scanpart[blockIdx.x] = tot;
+}
+
+__global__ void k_scan_top(Ctx c, int64_t nblk) {
+  __shared__ uint32_t buf[32];
+  __shared__ uint32_t tot;
+  uint32_t carry = 0;
+  for (int64_t base = 0; base < nblk; base += blockDim.x) {
+    const int64_t i = base + threadIdx.x;
+    const uint32_t v = i < nblk ? c.scanpart[i] : 0u;
+    const uint32_t off = block_scan_excl<uint32_t>(v, &tot, buf) + carry;
+    if (i < nblk) c.scanpart[i] = off;
+    carry += tot;
+  }
+}
+
+__global__ void k_scan_down(Ctx c) {
+  __shared__ uint32_t buf[32];
+  __shared__ uint32_t tot;
+  const int64_t i = (int64_t)blockIdx.x * kScanBlock + threadIdx.x;
+  const uint32_t v = i < c.nbcap_total ? c.bk_count[i] : 0u;
+  const uint32_t off = block_scan_excl<uint32_t>(v, &tot, buf) + c.scanpart[blockIdx.x];
+  if (i < c.nbcap_total) c.bk_start[i] = off;
+}
+
+template <bool BATCHED, bool VEC, bool F64, bool SEQ>
+__global__ void __launch_bounds__(1024) k_scatter(Ctx c) {
+  extern __shared__ __align__(16) uint32_t sm[];
+  const CtaInfo ci = c.cta[blockIdx.x];
+  if (is_aborted(c) || ci.e0 >= ci.e1) return;
+  bool hist_smem, lut_smem;
+  uint32_t* lut_base;
+  partition_prologue(c, ci, sm, hist_smem, lut_smem, lut_base);
+  const int64_t range = (int64_t)ci.cb1 - (int64_t)ci.cb0;
+  uint32_t* cur = hist_smem ? sm : (c.hist + ci.hoff);
+  for (int64_t k = threadIdx.x; k < range; k += blockDim.x)
+    cur[k] = c.bk_start[ci.cb0 + k] + c.hist[ci.hoff + k];
+  __syncthreads();
+  MatView v;
+  load_view(c, ci, lut_base, lut_smem, ci.i0, v);
+  using VT = typename std::conditional<F64, uint64_t, uint32_t>::type;
+  VT* rv = reinterpret_cast<VT*>(c.rv);
+  const VT* vin = reinterpret_cast<const VT*>(c.vals);
+  auto body = [&](int64_t t, int32_t r, int32_t col, VT val) {
+    advance_view<BATCHED>(c, ci, lut_base, lut_smem, t, v);
+    uint32_t b, lk;
+    if (classify(v, r, col, b, lk)) {
+      const uint32_t slot = atomicAdd(&cur[b], 1u);
+      c.rk[slot] = ((uint64_t)lk << 32) | (uint32_t)t;
+      rv[slot] = val;
+      if (SEQ) c.rs[slot] = c.seq[t];
+    }
+  };
+  if (VEC) {
+    const int64_t nvec = (ci.e1 - ci.e0) >> 2;
+    const int4* r4p = reinterpret_cast<const int4*>(c.rows + ci.e0);
+    const int4* c4p = reinterpret_cast<const int4*>(c.cols + ci.e0);
+    for (int64_t q = threadIdx.x; q < nvec; q += blockDim.x) {
+      const int4 r4 = __ldcs(r4p + q), c4 = __ldcs(c4p + q);
+      const int64_t t = ci.e0 + 4 * q;
+      VT x0, x1, x2, x3;
+      if (F64) {
+        const ulonglong2* vp = reinterpret_cast<const ulonglong2*>(vin + t);
+        const ulonglong2 a = __ldcs(vp), bq = __ldcs(vp + 1);
+        x0 = (VT)a.x; x1 = (VT)a.y; x2 = (VT)bq.x; x3 = (VT)bq.y;
+      } else {
+        const uint4 a = __ldcs(reinterpret_cast<const uint4*>(vin + t));
+        x0 = (VT)a.x; x1 = (VT)a.y; x2 = (VT)a.z; x3 = (VT)a.w;
+      }
+      body(t, r4.x, c4.x, x0);
+      body(t + 1, r4.y, c4.y, x1);
+      body(t + 2, r4.z, c4.z, x2);
+      body(t + 3, r4.w, c4.w, x3);
+    }
+    for (int64_t t = ci.e0 + 4 * nvec + threadIdx.x; t < ci.e1; t += blockDim.x)
+      body(t, c.rows[t], c.cols[t], vin[t]);
+  } else {
+    for (int64_t t = ci.e0 + threadIdx.x; t < ci.e1; t += blockDim.x) body(t, c.rows[t], c.cols[t], vin[t]);
+  }
+}
+
+// ===========================================================================
+// Resolve: one bucket at a time per block (persistent)
+// ===========================================================================
+struct ResolveSmem {
+  uint64_t* rk;    // [kCap] records (key-in-bucket << 32 | stream position)
+  void* rv;        // [kCap] raw values
+  uint32_t* orig;  // [kCap] index of the record in its bucket (window mode only)
+  uint16_t* perm;  // [kCap] sorted order
+  uint32_t* sub_a; // [2^sub_bits + 1]
+  uint32_t* sub_b; // [2^sub_bits]
+};
+
+struct BlockShared {
+  uint32_t buf[32];
+  uint32_t tot;
+  uint32_t ticket;
+  int64_t excl;
+  uint32_t taken, cum;
+  int32_t wmode;
+  uint32_t n_w;
+  unsigned long long red_u64[32];
+  uint32_t red_u32[32];
+  double red_f64[32];
+};
+
+// Wait (bounded) for the look-back chain of bucket b to provide its exclusive
+// prefix (the number of stored elements of the same matrix in all earlier
+// buckets).  Called by one thread; publishes nothing.
+__device__ int64_t lookback_wait(const Ctx& c, int64_t b) {
+  int64_t excl = 0;
+  int64_t bb = b - 1;
+  const uint64_t t_start = global_timer_ns();
+  uint32_t spins = 0;
+  while (true) {
+    const uint64_t s = ld_acquire_u64(&c.bk_state[bb]);
+    const uint64_t flag = s & ~kStMask;
+    if (flag == 0) {
+      if (is_aborted(c)) break;
+      if ((++spins & 63) == 0 && global_timer_ns() - t_start > 2000000000ull) {
+        record_fatal(c, SPM_ERR_TIMEOUT);
+        break;
+      }
+      continue;
+    }
+    excl += (int64_t)(s & kStMask);
+    if (flag == kStIncl) break;
+    --bb;
+  }
+  return excl;
+}
+
+// Decoupled look-back: publish this bucket's count, wait for the prefix,
+// publish the inclusive value.  Called by one thread.
+__device__ int64_t lookback(const Ctx& c, int64_t b, uint32_t nnz) {
+  st_release_u64(&c.bk_state[b], kStAgg | nnz);
+  const int64_t excl = lookback_wait(c, b);
+  st_release_u64(&c.bk_state[b], kStIncl | (uint64_t)(excl + nnz));
+  return excl;
+}
+
+template <bool F64>
+__device__ __forceinline__ double widen_raw(uint64_t bits) {
+  if (F64) return __longlong_as_double((long long)bits);
+  return (double)__uint_as_float((uint32_t)bits);
+}
+
+// Process the `n` records in shared memory that fall in keys [klo, klo+span)
+// of matrix `mm`: sort, resolve, count; then either look back (bucket mode)
+// or use `base_in` (window mode) as the matrix-relative output position of
+// the first element; write values, row indices, column offsets and the map.
+// Returns the number of stored elements.
+template <bool F64, bool SUM, bool SEQ>
+__device__ uint32_t resolve_records(const Ctx& c, const MatMeta& mm, int64_t b, uint64_t klo, uint64_t span,
+                                    uint32_t n, const ResolveSmem& S, BlockShared& B, bool window, int64_t base_in,
+                                    int64_t seg_start) {
+  using VT = typename std::conditional<F64, uint64_t, uint32_t>::type;
+  const VT* rv_s = reinterpret_cast<const VT*>(S.rv);
+  const int tid = threadIdx.x, NT = blockDim.x;
+  const int sbits_max = c.sub_bits;
+  const int sbits = span <= 1 ? 0 : ceil_log2_u64(span);
+  const int sshift = sbits > sbits_max ? sbits - sbits_max : 0;
+  const uint32_t nsub = (uint32_t)(((span - 1) >> sshift) + 1);
+  for (uint32_t s = tid; s <= nsub; s += NT) S.sub_a[s] = 0u;
+  __syncthreads();
+  for (uint32_t k = tid; k < n; k += NT) atomicAdd(&S.sub_a[(uint32_t)(S.rk[k] >> 32) >> sshift], 1u);
+  __syncthreads();
+  // exclusive scan of the sub-bin counts
+  {
+    const uint32_t per = (nsub + NT - 1) / NT;
+    const uint32_t a = min(nsub, (uint32_t)tid * per), e = min(nsub, a + per);
+    uint32_t local = 0;
+    for (uint32_t s = a; s < e; ++s) local += S.sub_a[s];
+    uint32_t run = block_scan_excl<uint32_t>(local, &B.tot, B.buf);
+    for (uint32_t s = a; s < e; ++s) {
+      const uint32_t x = S.sub_a[s];
+      S.sub_a[s] = run;
+      S.sub_b[s] = run;
+      run += x;
+    }
+    if (tid == 0) S.sub_a[nsub] = n;
+  }
+  __syncthreads();
+  for (uint32_t k = tid; k < n; k += NT) {
+    const uint32_t p = atomicAdd(&S.sub_b[(uint32_t)(S.rk[k] >> 32) >> sshift], 1u);
+    S.perm[p] = (uint16_t)k;
+  }
+  __syncthreads();
+  // this thread's sub-bins and key range
+  const uint32_t sa = (uint32_t)(((uint64_t)tid * nsub) / NT), sb = (uint32_t)(((uint64_t)(tid + 1) * nsub) / NT);
+  const uint32_t ea = S.sub_a[sa], eb = S.sub_a[sb];
+  const uint64_t kend = klo + span;
+  const uint64_t kt_lo = min(klo + ((uint64_t)sa << sshift), kend);
+  const uint64_t kt_hi = min(klo + ((uint64_t)sb << sshift), kend);
+  auto seq_of = [&](uint32_t k) -> uint64_t { return c.rs[seg_start + (S.orig ? S.orig[k] : k)]; };
+  auto less = [&](uint32_t x, uint32_t y) -> bool {
+    const uint64_t rx = S.rk[x], ry = S.rk[y];
+    if (!SEQ) return rx < ry;
+    const uint32_t lx = (uint32_t)(rx >> 32), ly = (uint32_t)(ry >> 32);
+    if (lx != ly) return lx < ly;
+    const uint64_t qx = seq_of(x), qy = seq_of(y);
+    if (qx != qy) return qx < qy;
+    return (uint32_t)rx < (uint32_t)ry;
+  };
+  // insertion sort of this thread's range (already grouped by sub-bin)
+  for (uint32_t x = ea + 1; x < eb; ++x) {
+    const uint16_t v = S.perm[x];
+    uint32_t y = x;
+    while (y > ea && less(v, S.perm[y - 1])) {
+      S.perm[y] = S.perm[y - 1];
+      --y;
+    }
+    S.perm[y] = v;
+  }
+  // resolve one run [p, q) of equal keys: value bits and whether it is kept
+  auto resolve_run = [&](uint32_t p, uint32_t q, uint64_t& bits) -> bool {
+    if (SUM) {
+      double acc = widen_raw<F64>((uint64_t)rv_s[S.perm[p]]);
+      for (uint32_t x = p + 1; x < q; ++x) acc += widen_raw<F64>((uint64_t)rv_s[S.perm[x]]);
+      if (F64) {
+        bits = (uint64_t)__double_as_longlong(acc);
+        return acc != 0.0;
+      }
+      const float f = __double2float_rn(acc);
+      bits = (uint64_t)__float_as_uint(f);
+      return f != 0.0f;
+    } else {
+      bits = (uint64_t)rv_s[S.perm[q - 1]];
+      if (F64) return __longlong_as_double((long long)bits) != 0.0;
+      return __uint_as_float((uint32_t)bits) != 0.0f;
+    }
+  };
+  auto run_end = [&](uint32_t p) -> uint32_t {
+    const uint32_t key = (uint32_t)(S.rk[S.perm[p]] >> 32);
+    uint32_t q = p + 1;
+    while (q < eb && (uint32_t)(S.rk[S.perm[q]] >> 32) == key) ++q;
+    return q;
+  };
+  // phase 1: count kept elements
+  uint32_t kept = 0;
+  for (uint32_t p = ea; p < eb;) {
+    const uint32_t q = run_end(p);
+    uint64_t bits;
+    if (resolve_run(p, q, bits)) ++kept;
+    p = q;
+  }
+  uint32_t nnz;
+  const uint32_t off = block_scan_excl<uint32_t>(kept, &B.tot, B.buf);
+  nnz = B.tot;
+  if (tid == 0) B.excl = window ? base_in : ((klo == 0) ? 0 : -1);
+  __syncthreads();
+  if (!window && tid == 0) {
+    if (b == c.withhold) B.excl = 0;  // fault injection: publish nothing, wait for nothing
+    else if (klo == 0) st_release_u64(&c.bk_state[b], kStIncl | (uint64_t)nnz);
+    else B.excl = lookback(c, b, nnz);
+  }
+  __syncthreads();
+  // phase 2: write
+  const int64_t excl = B.excl;
+  int64_t idx = excl + off;
+  const uint64_t nr = (uint64_t)mm.n_rows;
+  uint64_t j = (kt_lo + nr - 1) / nr;  // first column whose start key is in this thread's range
+  uint64_t next_start = j * nr;
+  int64_t* colp = c.col_ptr + mm.col_base;
+  int32_t* rowp = c.row_idx + mm.t0;
+  VT* outp = reinterpret_cast<VT*>(c.out_vals) + mm.t0;
+  for (uint32_t p = ea; p < eb;) {
+    const uint32_t q = run_end(p);
+    uint64_t bits;
+    const bool keep = resolve_run(p, q, bits);
+    const uint64_t key = klo + (S.rk[S.perm[p]] >> 32);
+    int64_t slot = -2;
+    if (keep) {
+      while (next_start <= key) {
+        colp[j] = idx;
+        ++j;
+        next_start += nr;
+      }
+      const uint64_t col = j - 1;
+      rowp[idx] = (int32_t)(key - col * nr);
+      outp[idx] = (VT)bits;
+      slot = idx;
+      ++idx;
+    }
+    if (c.keep_map) {
+      for (uint32_t x = p; x < q; ++x) {
+        const uint32_t pos = (uint32_t)S.rk[S.perm[x]];
+        c.map[pos] = (!SUM && x != q - 1) ? -1 : (int32_t)slot;
+      }
+    }
+    p = q;
+  }
+  while (next_start < kt_hi) {
+    colp[j] = idx;
+    ++j;
+    next_start += nr;
+  }
+  __syncthreads();
+  return nnz;
+}
+
+// A single key with more writes than fit in shared memory: streaming reduction.
+template <bool F64, bool SUM, bool SEQ>
+__device__ uint32_t resolve_single_key(const Ctx& c, const MatMeta& mm, uint64_t key, uint32_t lkey, int64_t start,
+                                       uint32_t n, BlockShared& B, int64_t base) {
+  using VT = typename std::conditional<F64, uint64_t, uint32_t>::type;
+  const VT* rv = reinterpret_cast<const VT*>(c.rv);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  // last write: the largest (seq, position); sum: per-thread partial sums combined in thread order
+  unsigned long long best_seq = 0;
+  uint32_t best_pos = 0;
+  int64_t best_k = -1;
+  double acc = 0.0;
+  for (int64_t k = tid; k < n; k += blockDim.x) {
+    const uint64_t r = c.rk[start + k];
+    if ((uint32_t)(r >> 32) != lkey) continue;
+    if (SUM) {
+      acc += widen_raw<F64>((uint64_t)rv[start + k]);
+    } else {
+      const unsigned long long sq = SEQ ? c.rs[start + k] : 0ull;
+      const uint32_t pos = (uint32_t)r;
+      if (best_k < 0 || sq > best_seq || (sq == best_seq && pos > best_pos)) {
+        best_seq = sq;
+        best_pos = pos;
+        best_k = k;
+      }
+    }
+  }
+  uint64_t bits = 0;
+  bool keep;
+  int64_t win_k = -1;
+  if (SUM) {
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (lane == 0) B.red_f64[warp] = acc;
+    __syncthreads();
+    if (tid == 0) {
+      double s = 0.0;
+      for (int w = 0; w < nw; ++w) s += B.red_f64[w];
+      B.red_f64[0] = s;
+    }
+    __syncthreads();
+    const double s = B.red_f64[0];
+    if (F64) {
+      bits = (uint64_t)__double_as_longlong(s);
+      keep = s != 0.0;
+    } else {
+      const float f = __double2float_rn(s);
+      bits = __float_as_uint(f);
+      keep = f != 0.0f;
+    }
+    __syncthreads();
+  } else {
+    // arg-max of (seq, pos) over the block
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long s2 = __shfl_down_sync(0xffffffffu, best_seq, o);
+      const uint32_t p2 = __shfl_down_sync(0xffffffffu, best_pos, o);
+      const long long k2 = __shfl_down_sync(0xffffffffu, (long long)best_k, o);
+      if (k2 >= 0 && (best_k < 0 || s2 > best_seq || (s2 == best_seq && p2 > best_pos))) {
+        best_seq = s2;
+        best_pos = p2;
+        best_k = k2;
+      }
+    }
+    if (lane == 0) {
+      B.red_u64[warp] = best_seq;
+      B.red_u32[warp] = best_pos;
+      B.red_f64[warp] = __longlong_as_double(best_k);
+    }
+    __syncthreads();
+    if (tid == 0) {
+      long long bk = -1;
+      unsigned long long bs = 0;
+      uint32_t bp = 0;
+      for (int w = 0; w < nw; ++w) {
+        const long long k2 = __double_as_longlong(B.red_f64[w]);
+        if (k2 >= 0 && (bk < 0 || B.red_u64[w] > bs || (B.red_u64[w] == bs && B.red_u32[w] > bp))) {
+          bk = k2;
+          bs = B.red_u64[w];
+          bp = B.red_u32[w];
+        }
+      }
+      B.red_f64[0] = __longlong_as_double(bk);
+    }
+    __syncthreads();
+    win_k = __double_as_longlong(B.red_f64[0]);
+    bits = (uint64_t)rv[start + win_k];
+    keep = F64 ? (__longlong_as_double((long long)bits) != 0.0) : (__uint_as_float((uint32_t)bits) != 0.0f);
+    __syncthreads();
+  }
+  const uint64_t nr = (uint64_t)mm.n_rows;
+  if (tid == 0) {
+    const uint64_t col = key / nr;
+    if (col * nr == key) c.col_ptr[mm.col_base + col] = base;
+    if (keep) {
+      c.row_idx[mm.t0 + base] = (int32_t)(key - col * nr);
+      reinterpret_cast<VT*>(c.out_vals)[mm.t0 + base] = (VT)bits;
+    }
+  }
+  if (c.keep_map) {
+    for (int64_t k = tid; k < n; k += blockDim.x) {
+      const uint64_t r = c.rk[start + k];
+      if ((uint32_t)(r >> 32) != lkey) continue;
+      c.map[(uint32_t)r] = (!SUM && k != win_k) ? -1 : (keep ? (int32_t)base : -2);
+    }
+  }
+  __syncthreads();
+  return keep ? 1u : 0u;
+}
+
+template <bool F64, bool SUM, bool SEQ>
+__global__ void __launch_bounds__(512) k_resolve(Ctx c) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ BlockShared B;
+  __shared__ MatMeta mm;
+  using VT = typename std::conditional<F64, uint64_t, uint32_t>::type;
+  ResolveSmem S;
+  S.rk = reinterpret_cast<uint64_t*>(smraw);
+  S.rv = smraw + (size_t)kCap * 8;
+  S.perm = reinterpret_cast<uint16_t*>(smraw + (size_t)kCap * (8 + sizeof(VT)));
+  S.sub_a = reinterpret_cast<uint32_t*>(smraw + (size_t)kCap * (10 + sizeof(VT)));
+  S.sub_b = S.sub_a + (1 << c.sub_bits) + 4;
+  uint32_t* orig_store = S.sub_b + (1 << c.sub_bits);  // [kCap], used in window mode
+  const VT* rvg = reinterpret_cast<const VT*>(c.rv);
+  const int tid = threadIdx.x, NT = blockDim.x;
+  const uint32_t NB = c.scal->NB;
+  while (true) {
+    if (tid == 0) B.ticket = is_aborted(c) ? 0xffffffffu : atomicAdd(&c.scal->ticket, 1u);
+    __syncthreads();
+    const uint32_t b = B.ticket;
+    if (b >= NB) break;
+    const uint32_t info = c.bk_info[b];
+    const int64_t mi = info >> 6;
+    const int w = info & 63;
+    if (tid == 0) mm = c.meta[mi];
+    __syncthreads();
+    const uint64_t klo = c.bk_lo[b];
+    if (mm.K == 0) {
+      for (int64_t jj = tid; jj <= mm.n_cols; jj += NT) c.col_ptr[mm.col_base + jj] = 0;
+      if (tid == 0) {
+        c.d_nnz[mi] = 0;
+        st_release_u64(&c.bk_state[b], kStIncl);
+      }
+      __syncthreads();
+      continue;
+    }
+    const uint64_t span = min(uint64_t{1} << w, mm.K - klo);
+    const int64_t start = c.bk_start[b];
+    const uint32_t n = c.bk_count[b];
+    int64_t total;
+    if (n <= (uint32_t)kCap) {
+      for (uint32_t k = tid; k < n; k += NT) {
+        S.rk[k] = c.rk[start + k];
+        reinterpret_cast<VT*>(S.rv)[k] = rvg[start + k];
+      }
+      S.orig = nullptr;
+      __syncthreads();
+      const uint32_t nnz = resolve_records<F64, SUM, SEQ>(c, mm, b, klo, span, n, S, B, false, 0, start);
+      total = B.excl + nnz;
+    } else {
+      // more writes than fit: windows of the key range, each sorted in shared memory
+      if (tid == 0) B.excl = (klo == 0) ? 0 : lookback_wait(c, b);
+      __syncthreads();
+      int64_t base = B.excl;
+      __syncthreads();
+      uint64_t wlo = 0;
+      S.orig = orig_store;
+      while (wlo < span) {
+        int hs = (span - wlo <= 1) ? 0 : max(0, ceil_log2_u64(span - wlo) - c.sub_bits);
+        uint64_t wend = span;
+        uint64_t whi = wlo + 1;
+        int mode = 0;  // 1 = window, 2 = single key
+        while (true) {
+          const uint32_t nbins = (uint32_t)(((wend - wlo - 1) >> hs) + 1);
+          for (uint32_t s = tid; s < nbins; s += NT) S.sub_a[s] = 0u;
+          __syncthreads();
+          for (uint32_t k = tid; k < n; k += NT) {
+            const uint64_t l = c.rk[start + k] >> 32;
+            if (l >= wlo && l < wend) atomicAdd(&S.sub_a[(uint32_t)((l - wlo) >> hs)], 1u);
+          }
+          __syncthreads();
+          if (tid == 0) {
+            uint32_t cum = 0, taken = 0;
+            while (taken < nbins && cum + S.sub_a[taken] <= (uint32_t)kCap) cum += S.sub_a[taken++];
+            B.taken = taken;
+            B.cum = cum;
+          }
+          __syncthreads();
+          if (B.taken > 0) {
+            whi = min(wlo + ((uint64_t)B.taken << hs), wend);
+            mode = 1;
+            break;
+          }
+          if (hs == 0) {
+            mode = 2;
+            break;
+          }
+          wend = wlo + (uint64_t{1} << hs);
+          hs = max(0, hs - c.sub_bits);
+        }
+        __syncthreads();
+        if (mode == 1) {
+          if (tid == 0) B.n_w = 0;
+          __syncthreads();
+          for (uint32_t k = tid; k < n; k += NT) {
+            const uint64_t r = c.rk[start + k];
+            const uint64_t l = r >> 32;
+            if (l >= wlo && l < whi) {
+              const uint32_t q = atomicAdd(&B.n_w, 1u);
+              S.rk[q] = ((l - wlo) << 32) | (uint32_t)r;
+              reinterpret_cast<VT*>(S.rv)[q] = rvg[start + k];
+              S.orig[q] = k;
+            }
+          }
+          __syncthreads();
+          const uint32_t nw = B.n_w;
+          base += resolve_records<F64, SUM, SEQ>(c, mm, b, klo + wlo, whi - wlo, nw, S, B, true, base, start);
+          wlo = whi;
+        } else {
+          base += resolve_single_key<F64, SUM, SEQ>(c, mm, klo + wlo, (uint32_t)wlo, start, n, B, base);
+          wlo = wlo + 1;
+        }
+        __syncthreads();
+      }
+      total = base;
+      // the inclusive value of a bucket is the matrix-relative end of its output
+      if (tid == 0) st_release_u64(&c.bk_state[b], kStIncl | (uint64_t)total);
+    }
+    if (tid == 0 && klo + span == mm.K) {
+      c.col_ptr[mm.col_base + mm.n_cols] = total;
+      c.d_nnz[mi] = total;
+    }
+    __syncthreads();
+  }
+}
+
+// ===========================================================================
+// Host side
+// ===========================================================================
+namespace {
+
+spm_tuning g_tuning = {4096, 12, 1024, 512};
+int64_t g_withhold = -1;
+std::mutex g_mutex;
+
+// measurement hooks
+constexpr int kStages = 5;
+constexpr int kRing = 64;
+struct StageRing {
+  bool on = false;
+  int dev = -1;
+  cudaEvent_t ev[kRing][kStages + 1] = {};
+  int64_t calls = 0;
+};
+StageRing g_ring;
+std::atomic<int64_t> g_launches{0};
+
+void stage_mark(cudaStream_t st, int64_t call, int boundary) {
+  if (call < 0) return;
+  cudaEventRecord(g_ring.ev[call % kRing][boundary], st);
+}
+
+struct DevState {
+  bool init = false;
+  int sms = 0;
+};
+DevState g_dev[64];
+
+constexpr size_t kAlign = 256;
+size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
+
+size_t resolve_smem_bytes(int sv, int sub_bits) {
+  return (size_t)kCap * (8 + sv + 2) + ((size_t)(1 << sub_bits) + 4) * 4 + ((size_t)1 << sub_bits) * 4 +
+         (size_t)kCap * 4;
+}
+
+size_t partition_smem_bytes() { return (size_t)(kHistCapSmem + kLutCapSmem) * 4; }
+
+template <typename K>
+void set_smem_attr(K kernel, size_t bytes) {
+  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+spm_status device_init(int& dev, DevState*& ds) {
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return SPM_ERR_CUDA;
+  ds = &g_dev[dev];
+  if (ds->init) return SPM_OK;
+  std::lock_guard<std::mutex> lk(g_mutex);
+  if (ds->init) return SPM_OK;
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) return SPM_ERR_CUDA;
+  const size_t ps = partition_smem_bytes();
+  set_smem_attr(k_hist<false, false>, ps);
+  set_smem_attr(k_hist<false, true>, ps);
+  set_smem_attr(k_hist<true, false>, ps);
+  set_smem_attr(k_hist<true, true>, ps);
+#define SPM_SET_SCATTER(BA, VE)                                  \
+  set_smem_attr(k_scatter<BA, VE, false, false>, ps);            \
+  set_smem_attr(k_scatter<BA, VE, false, true>, ps);             \
+  set_smem_attr(k_scatter<BA, VE, true, false>, ps);             \
+  set_smem_attr(k_scatter<BA, VE, true, true>, ps);
+  SPM_SET_SCATTER(false, false)
+  SPM_SET_SCATTER(false, true)
+  SPM_SET_SCATTER(true, false)
+  SPM_SET_SCATTER(true, true)
+#undef SPM_SET_SCATTER
+  const size_t r4 = resolve_smem_bytes(4, 12), r8 = resolve_smem_bytes(8, 12);
+  set_smem_attr(k_resolve<false, false, false>, r4);
+  set_smem_attr(k_resolve<false, false, true>, r4);
+  set_smem_attr(k_resolve<false, true, false>, r4);
+  set_smem_attr(k_resolve<false, true, true>, r4);
+  set_smem_attr(k_resolve<true, false, false>, r8);
+  set_smem_attr(k_resolve<true, false, true>, r8);
+  set_smem_attr(k_resolve<true, true, false>, r8);
+  set_smem_attr(k_resolve<true, true, true>, r8);
+  if (cudaGetLastError() != cudaSuccess) return SPM_ERR_CUDA;
+  ds->sms = sms;
+  ds->init = true;
+  return SPM_OK;
+}
+
+int num_sms_for_sizing() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+  if (g_dev[dev].init) return g_dev[dev].sms;
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) {
+    cudaGetLastError();
+    return 152;
+  }
+  return sms;
+}
+
+struct HostPlan {
+  Layout L;
+  MatMeta single;  // B == 1
+};
+
+// Validate the sizes and compute the workspace layout.
+spm_status host_plan(int64_t B, const int64_t* h_nr, const int64_t* h_nc, const int64_t* h_tp, int sv, bool seq,
+                     int64_t tgt, int C, HostPlan& hp) {
+  if (B < 0 || (B > 0 && (!h_nr || !h_nc || !h_tp))) return SPM_ERR_INVALID_ARG;
+  if (B >= (int64_t{1} << 26)) return SPM_ERR_UNSUPPORTED;
+  if (B > 0 && h_tp[0] != 0) return SPM_ERR_INVALID_ARG;
+  Layout& L = hp.L;
+  L.B = B;
+  L.sv = sv;
+  L.seq = seq;
+  L.C = C;
+  const int64_t m_total = B > 0 ? h_tp[B] : 0;
+  if (m_total < 0 || m_total >= (int64_t{1} << 32) - 64) return m_total < 0 ? SPM_ERR_INVALID_ARG : SPM_ERR_UNSUPPORTED;
+  L.m_total = m_total;
+  std::vector<int64_t> nbcap_prefix((size_t)B + 1, 0);
+  int64_t S = 0, lut = 0, l2 = 0, nbcap = 0, cols = 0;
+  for (int64_t i = 0; i < B; ++i) {
+    const int64_t nr = h_nr[i], nc = h_nc[i], m = h_tp[i + 1] - h_tp[i];
+    if (nr < 0 || nc < 0 || m < 0) return SPM_ERR_INVALID_ARG;
+    if (nr > 0x7fffffffLL || nc > 0x7fffffffLL) return SPM_ERR_UNSUPPORTED;
+    const Derived d = derive(nr, nc, m, m_total, tgt);
+    if (d.bbits > kMaxKeyBits) return SPM_ERR_UNSUPPORTED;
+    if (d.nbcap >= (int64_t{1} << kBaseBits)) return SPM_ERR_UNSUPPORTED;
+    if (B == 1) {
+      MatMeta& mm = hp.single;
+      memset(&mm, 0, sizeof(mm));
+      mm.t0 = 0;
+      mm.m = m;
+      mm.n_rows = nr;
+      mm.n_cols = nc;
+      mm.K = d.K;
+      mm.bbits = d.bbits;
+      mm.L1 = d.L1;
+      mm.s1 = d.s1;
+      mm.H2 = d.H2;
+      mm.ns = d.ns;
+      mm.lut_len = d.lut_len;
+      mm.nbcap = d.nbcap;
+    }
+    S += d.ns;
+    lut += d.lut_len;
+    l2 += d.H2;
+    nbcap += d.nbcap;
+    cols += nc + 1;
+    nbcap_prefix[(size_t)i + 1] = nbcap;
+  }
+  L.S_total = S;
+  L.lut_total = lut;
+  L.l2_total = l2;
+  L.nbcap_total = nbcap;
+  // bound of the per-block bucket ranges
+  int64_t hist = 0;
+  auto mat_of = [&](int64_t t) {
+    int64_t lo = 0, hi = B - 1;
+    while (lo < hi) {
+      const int64_t mid = lo + (hi - lo + 1) / 2;
+      if (h_tp[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+  };
+  for (int64_t cc = 0; cc < C && B > 0; ++cc) {
+    const int64_t e0 = chunk_begin(m_total, cc, C), e1 = chunk_begin(m_total, cc + 1, C);
+    if (e0 >= e1) continue;
+    const int64_t i0 = mat_of(e0), i1 = mat_of(e1 - 1);
+    hist += nbcap_prefix[(size_t)i1 + 1] - nbcap_prefix[(size_t)i0];
+  }
+  L.hist_bound = hist;
+  L.scan_blocks = (nbcap + kScanBlock - 1) / kScanBlock;
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = o;
+    o = align_up(o + bytes);
+    return at;
+  };
+  L.meta = take(sizeof(MatMeta) * (size_t)std::max<int64_t>(B, 1));
+  L.scal = take(sizeof(Scalars));
+  L.cta = take(sizeof(CtaInfo) * (size_t)C);
+  L.samp = take(8 * (size_t)std::max<int64_t>(S, 1));
+  L.cellcnt = take(4 * (size_t)std::max<int64_t>(lut, 1));
+  L.lut = take(4 * (size_t)std::max<int64_t>(lut, 1));
+  L.l2cell = take(4 * (size_t)std::max<int64_t>(l2, 1));
+  L.bk_lo = take(8 * (size_t)std::max<int64_t>(nbcap, 1));
+  L.bk_info = take(4 * (size_t)std::max<int64_t>(nbcap, 1));
+  L.bk_count = take(4 * (size_t)std::max<int64_t>(nbcap, 1));
+  L.bk_start = take(4 * (size_t)std::max<int64_t>(nbcap, 1));
+  L.bk_state = take(8 * (size_t)std::max<int64_t>(nbcap, 1));
+  L.scanpart = take(4 * (size_t)std::max<int64_t>(L.scan_blocks, 1));
+  L.hist = take(4 * (size_t)std::max<int64_t>(hist, 1));
+  L.rk = take(8 * (size_t)(m_total + 4));
+  L.rv = take((size_t)sv * (size_t)(m_total + 4));
+  L.rs = seq ? take(8 * (size_t)(m_total + 4)) : o;
+  L.total = o;
+  return SPM_OK;
+}
+
+template <bool BATCHED>
+void launch_partition(const Ctx& ctx, const Layout& L, bool vec, cudaStream_t st, int threads, int64_t call) {
+  const size_t ps = partition_smem_bytes();
+  const int C = (int)L.C;
+  if (vec) k_hist<BATCHED, true><<<C, threads, ps, st>>>(ctx);
+  else k_hist<BATCHED, false><<<C, threads, ps, st>>>(ctx);
+  stage_mark(st, call, 2);
+  k_colscan<<<(unsigned)((L.nbcap_total + 255) / 256), 256, 0, st>>>(ctx);
+  k_scan_reduce<<<(unsigned)L.scan_blocks, kScanBlock, 0, st>>>(ctx);
+  k_scan_top<<<1, 1024, 0, st>>>(ctx, L.scan_blocks);
+  k_scan_down<<<(unsigned)L.scan_blocks, kScanBlock, 0, st>>>(ctx);
+  stage_mark(st, call, 3);
+#define SPM_SCATTER(VE, F6, SQ) k_scatter<BATCHED, VE, F6, SQ><<<C, threads, ps, st>>>(ctx)
+  const bool f64 = ctx.f64 != 0, sq = ctx.has_seq != 0;
+  if (vec) {
+    if (f64) { if (sq) SPM_SCATTER(true, true, true); else SPM_SCATTER(true, true, false); }
+    else { if (sq) SPM_SCATTER(true, false, true); else SPM_SCATTER(true, false, false); }
+  } else {
+    if (f64) { if (sq) SPM_SCATTER(false, true, true); else SPM_SCATTER(false, true, false); }
+    else { if (sq) SPM_SCATTER(false, false, true); else SPM_SCATTER(false, false, false); }
+  }
+#undef SPM_SCATTER
+  stage_mark(st, call, 4);
+}
+
+void launch_resolve(const Ctx& ctx, int sms, cudaStream_t st, int threads) {
+  const size_t rs = resolve_smem_bytes(ctx.f64 ? 8 : 4, ctx.sub_bits);
+  const int grid = sms * (rs <= 110 * 1024 ? 2 : 1);
+#define SPM_RES(F6, SU, SQ) k_resolve<F6, SU, SQ><<<grid, threads, rs, st>>>(ctx)
+  if (ctx.f64) {
+    if (ctx.sum_mode) { if (ctx.has_seq) SPM_RES(true, true, true); else SPM_RES(true, true, false); }
+    else { if (ctx.has_seq) SPM_RES(true, false, true); else SPM_RES(true, false, false); }
+  } else {
+    if (ctx.sum_mode) { if (ctx.has_seq) SPM_RES(false, true, true); else SPM_RES(false, true, false); }
+    else { if (ctx.has_seq) SPM_RES(false, false, true); else SPM_RES(false, false, false); }
+  }
+#undef SPM_RES
+}
+
+spm_status run_assembly(int64_t B, const int64_t* h_nr, const int64_t* h_nc, const int64_t* h_tp, const int64_t* d_nr,
+                        const int64_t* d_nc, const int64_t* d_tp, const int32_t* rows, const int32_t* cols,
+                        const void* vals, const uint64_t* seq, spm_dtype dtype, spm_mode mode, uint32_t flags,
+                        int64_t* col_ptr, int32_t* row_idx, void* out_vals, int64_t* d_nnz, int32_t* map,
+                        int32_t* d_status, void* workspace, size_t ws_bytes, void* stream) {
+  if (dtype != SPM_F32 && dtype != SPM_F64) return SPM_ERR_INVALID_ARG;
+  if (mode != SPM_MODE_LAST_WRITE && mode != SPM_MODE_SUM) return SPM_ERR_INVALID_ARG;
+  if (flags & ~7u) return SPM_ERR_INVALID_ARG;
+  const bool has_seq = (flags & SPM_SEQ_EXPLICIT) != 0;
+  if (has_seq != (seq != nullptr)) return SPM_ERR_INVALID_ARG;
+  const bool keep_map = (flags & SPM_KEEP_MAP) != 0;
+  if (keep_map && map == nullptr) return SPM_ERR_INVALID_ARG;
+  if (!d_status || !d_nnz || !col_ptr) return SPM_ERR_INVALID_ARG;
+  int dev;
+  DevState* ds;
+  spm_status s = device_init(dev, ds);
+  if (s != SPM_OK) return s;
+  spm_tuning tun;
+  int64_t withhold;
+  {
+    std::lock_guard<std::mutex> lk(g_mutex);
+    tun = g_tuning;
+    withhold = g_withhold;
+  }
+  const int sv = dtype == SPM_F64 ? 8 : 4;
+  HostPlan hp;
+  s = host_plan(B, h_nr, h_nc, h_tp, sv, has_seq, tun.bucket_target, ds->sms, hp);
+  if (s != SPM_OK) return s;
+  const Layout& L = hp.L;
+  if (L.m_total > 0 && (!rows || !cols || !vals || !row_idx || !out_vals)) return SPM_ERR_INVALID_ARG;
+  if (!workspace || ws_bytes < L.total) return SPM_ERR_WORKSPACE_TOO_SMALL;
+  if (B == 0) return SPM_OK;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  char* ws = static_cast<char*>(workspace);
+  Ctx ctx;
+  memset(&ctx, 0, sizeof(ctx));
+  ctx.rows = rows;
+  ctx.cols = cols;
+  ctx.vals = vals;
+  ctx.seq = seq;
+  ctx.col_ptr = col_ptr;
+  ctx.row_idx = row_idx;
+  ctx.out_vals = out_vals;
+  ctx.d_nnz = d_nnz;
+  ctx.map = map;
+  ctx.status = d_status;
+  ctx.meta = reinterpret_cast<MatMeta*>(ws + L.meta);
+  ctx.scal = reinterpret_cast<Scalars*>(ws + L.scal);
+  ctx.cta = reinterpret_cast<CtaInfo*>(ws + L.cta);
+  ctx.samp = reinterpret_cast<uint64_t*>(ws + L.samp);
+  ctx.cellcnt = reinterpret_cast<uint32_t*>(ws + L.cellcnt);
+  ctx.lut = reinterpret_cast<uint32_t*>(ws + L.lut);
+  ctx.l2cell = reinterpret_cast<int32_t*>(ws + L.l2cell);
+  ctx.bk_lo = reinterpret_cast<uint64_t*>(ws + L.bk_lo);
+  ctx.bk_info = reinterpret_cast<uint32_t*>(ws + L.bk_info);
+  ctx.bk_count = reinterpret_cast<uint32_t*>(ws + L.bk_count);
+  ctx.bk_start = reinterpret_cast<uint32_t*>(ws + L.bk_start);
+  ctx.bk_state = reinterpret_cast<uint64_t*>(ws + L.bk_state);
+  ctx.scanpart = reinterpret_cast<uint32_t*>(ws + L.scanpart);
+  ctx.hist = reinterpret_cast<uint32_t*>(ws + L.hist);
+  ctx.rk = reinterpret_cast<uint64_t*>(ws + L.rk);
+  ctx.rv = ws + L.rv;
+  ctx.rs = has_seq ? reinterpret_cast<uint64_t*>(ws + L.rs) : nullptr;
+  ctx.B = L.B;
+  ctx.m_total = L.m_total;
+  ctx.S_total = L.S_total;
+  ctx.lut_total = L.lut_total;
+  ctx.nbcap_total = L.nbcap_total;
+  ctx.hist_bound = L.hist_bound;
+  ctx.C = L.C;
+  ctx.sum_mode = mode == SPM_MODE_SUM;
+  ctx.f64 = dtype == SPM_F64;
+  ctx.keep_map = keep_map;
+  ctx.has_seq = has_seq;
+  ctx.tgt = tun.bucket_target;
+  ctx.sub_bits = tun.sub_bits;
+  ctx.withhold = withhold;
+
+  int64_t call = -1;
+  {
+    std::lock_guard<std::mutex> lk(g_mutex);
+    if (g_ring.on && g_ring.dev == dev) call = g_ring.calls++;
+  }
+  stage_mark(st, call, 0);
+  cudaMemsetAsync(d_status, 0, sizeof(int32_t), st);
+  cudaMemsetAsync(ws + L.scal, 0, sizeof(Scalars), st);
+  cudaMemsetAsync(ws + L.cellcnt, 0, 4 * (size_t)std::max<int64_t>(L.lut_total, 1), st);
+  cudaMemsetAsync(ws + L.bk_state, 0, 8 * (size_t)std::max<int64_t>(L.nbcap_total, 1), st);
+  if (B == 1 && d_tp == nullptr) {
+    k_setup_single<<<1, 32, 0, st>>>(ctx, hp.single);
+  } else {
+    int64_t ncols_total = 0;
+    unsigned long long h = 0;
+    for (int64_t i = 0; i < B; ++i) {
+      ncols_total += h_nc[i] + 1;
+      h += (unsigned long long)meta_term(i, h_nr[i], h_nc[i], h_tp[i + 1]);
+    }
+    k_setup_batched<<<1, 1024, 0, st>>>(ctx, d_nr, d_nc, d_tp, L.S_total, L.lut_total, L.l2_total, L.nbcap_total,
+                                        ncols_total, h);
+  }
+  if (L.S_total > 0) k_sample<<<(unsigned)((L.S_total + 255) / 256), 256, 0, st>>>(ctx);
+  k_plan<<<(unsigned)B, 512, 0, st>>>(ctx);
+  k_bucket_scan<<<1, 1024, 0, st>>>(ctx);
+  k_bucket_fill<<<(unsigned)((L.lut_total * 32 + 255) / 256), 256, 0, st>>>(ctx);
+  stage_mark(st, call, 1);
+  const bool vec = ((reinterpret_cast<uintptr_t>(rows) | reinterpret_cast<uintptr_t>(cols) |
+                     reinterpret_cast<uintptr_t>(vals)) & 15u) == 0;
+  const bool batched = B > 1;
+  if (batched) launch_partition<true>(ctx, L, vec, st, tun.partition_threads, call);
+  else launch_partition<false>(ctx, L, vec, st, tun.partition_threads, call);
+  launch_resolve(ctx, ds->sms, st, tun.resolve_threads);
+  stage_mark(st, call, 5);
+  g_launches += 11 + (L.S_total > 0 ? 1 : 0);  // setup, plan, 2 bucket kernels, 6 partition, resolve
+  if (cudaGetLastError() != cudaSuccess) return SPM_ERR_CUDA;
+  return SPM_OK;
+}
+
+}  // namespace
+
+void count_launches(int64_t n) { g_launches += n; }
+
+}  // namespace spm
+
+using namespace spm;
+
+extern "C" {
+
+const char* spm_status_string(spm_status s) {
+  switch (s) {
+    case SPM_OK: return "SPM_OK";
+    case SPM_ERR_INVALID_ARG: return "SPM_ERR_INVALID_ARG";
+    case SPM_ERR_INDEX_OUT_OF_RANGE: return "SPM_ERR_INDEX_OUT_OF_RANGE";
+    case SPM_ERR_WORKSPACE_TOO_SMALL: return "SPM_ERR_WORKSPACE_TOO_SMALL";
+    case SPM_ERR_UNSUPPORTED: return "SPM_ERR_UNSUPPORTED";
+    case SPM_ERR_CUDA: return "SPM_ERR_CUDA";
+    case SPM_ERR_TIMEOUT: return "SPM_ERR_TIMEOUT";
+  }
+  return "SPM_ERR_UNKNOWN";
+}
+
+int32_t spm_version(void) { return 10000; }
+
+spm_status spm_set_tuning(const spm_tuning* t) {
+  std::lock_guard<std::mutex> lk(g_mutex);
+  if (!t) {
+    g_tuning = spm_tuning{4096, 12, 1024, 512};
+    return SPM_OK;
+  }
+  if (t->bucket_target < 256 || t->bucket_target > 8192) return SPM_ERR_INVALID_ARG;
+  if (t->sub_bits < 8 || t->sub_bits > 12) return SPM_ERR_INVALID_ARG;
+  if (t->partition_threads != 256 && t->partition_threads != 512 && t->partition_threads != 1024)
+    return SPM_ERR_INVALID_ARG;
+  if (t->resolve_threads != 256 && t->resolve_threads != 512) return SPM_ERR_INVALID_ARG;
+  g_tuning = *t;
+  return SPM_OK;
+}
+
+spm_status spm_debug_withhold_publication(int64_t bucket) {
+  if (bucket < -1) return SPM_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(g_mutex);
+  g_withhold = bucket;
+  return SPM_OK;
+}
+
+spm_status spm_debug_stage_timing(int32_t enable) {
+  std::lock_guard<std::mutex> lk(g_mutex);
+  if (enable) {
+    if (g_ring.on) return SPM_OK;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return SPM_ERR_CUDA;
+    for (int i = 0; i < kRing; ++i)
+      for (int j = 0; j <= kStages; ++j)
+        if (cudaEventCreate(&g_ring.ev[i][j]) != cudaSuccess) return SPM_ERR_CUDA;
+    g_ring.dev = dev;
+    g_ring.calls = 0;
+    g_ring.on = true;
+  } else if (g_ring.on) {
+    for (int i = 0; i < kRing; ++i)
+      for (int j = 0; j <= kStages; ++j) cudaEventDestroy(g_ring.ev[i][j]);
+    g_ring.on = false;
+  }
+  return SPM_OK;
+}
+
+spm_status spm_debug_stage_times(int32_t back, float* ms, int32_t n) {
+  std::lock_guard<std::mutex> lk(g_mutex);
+  if (!ms || n < 0 || n > kStages || back < 0 || back >= kRing) return SPM_ERR_INVALID_ARG;
+  if (!g_ring.on || back >= g_ring.calls) return SPM_ERR_INVALID_ARG;
+  const int64_t call = g_ring.calls - 1 - back;
+  for (int j = 0; j < n; ++j) {
+    if (cudaEventElapsedTime(&ms[j], g_ring.ev[call % kRing][j], g_ring.ev[call % kRing][j + 1]) != cudaSuccess)
+      return SPM_ERR_CUDA;
+  }
+  return SPM_OK;
+}
+
+int64_t spm_debug_launch_count(void) { return g_launches.load(); }
+
+spm_status spm_get_tuning(spm_tuning* t) {
+  if (!t) return SPM_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(g_mutex);
+  *t = g_tuning;
+  return SPM_OK;
+}
+
+spm_status spm_assemble_csc_batched_workspace(int64_t batch, const int64_t* h_n_rows, const int64_t* h_n_cols,
+                                              const int64_t* h_trip_ptr, spm_dtype dtype, spm_mode mode,
+                                              uint32_t flags, size_t* bytes) {
+  if (!bytes) return SPM_ERR_INVALID_ARG;
+  if (dtype != SPM_F32 && dtype != SPM_F64) return SPM_ERR_INVALID_ARG;
+  if (mode != SPM_MODE_LAST_WRITE && mode != SPM_MODE_SUM) return SPM_ERR_INVALID_ARG;
+  if (flags & ~7u) return SPM_ERR_INVALID_ARG;
+  spm_tuning tun;
+  {
+    std::lock_guard<std::mutex> lk(g_mutex);
+    tun = g_tuning;
+  }
+  HostPlan hp;
+  const spm_status s = host_plan(batch, h_n_rows, h_n_cols, h_trip_ptr, dtype == SPM_F64 ? 8 : 4,
+                                 (flags & SPM_SEQ_EXPLICIT) != 0, tun.bucket_target, num_sms_for_sizing(), hp);
+  if (s != SPM_OK) return s;
+  *bytes = hp.L.total;
+  return SPM_OK;
+}
+
+spm_status spm_assemble_csc_workspace(int64_t n_rows, int64_t n_cols, int64_t m, spm_dtype dtype, spm_mode mode,
+                                      uint32_t flags, size_t* bytes) {
+  if (m < 0) return SPM_ERR_INVALID_ARG;
+  const int64_t tp[2] = {0, m};
+  return spm_assemble_csc_batched_workspace(1, &n_rows, &n_cols, tp, dtype, mode, flags, bytes);
+}
+
+spm_status spm_assemble_csc(int64_t n_rows, int64_t n_cols, int64_t m, const int32_t* rows, const int32_t* cols,
+                            const void* vals, const uint64_t* seq, spm_dtype dtype, spm_mode mode, uint32_t flags,
+                            int64_t* col_ptr, int32_t* row_idx, void* out_vals, int64_t* d_nnz, int32_t* map,
+                            int32_t* d_status, void* workspace, size_t ws_bytes, void* stream) {
+  if (m < 0) return SPM_ERR_INVALID_ARG;
+  const int64_t tp[2] = {0, m};
+  return run_assembly(1, &n_rows, &n_cols, tp, nullptr, nullptr, nullptr, rows, cols, vals, seq, dtype, mode, flags,
+                      col_ptr, row_idx, out_vals, d_nnz, map, d_status, workspace, ws_bytes, stream);
+}
+
+spm_status spm_assemble_csc_batched(int64_t batch, const int64_t* h_n_rows, const int64_t* h_n_cols,
+                                    const int64_t* h_trip_ptr, const int64_t* d_n_rows, const int64_t* d_n_cols,
+                                    const int64_t* d_trip_ptr, const int32_t* rows, const int32_t* cols,
+                                    const void* vals, const uint64_t* seq, spm_dtype dtype, spm_mode mode,
+                                    uint32_t flags, int64_t* col_ptr, int32_t* row_idx, void* out_vals,
+                                    int64_t* d_nnz, int32_t* map, int32_t* d_status, void* workspace,
+                                    size_t ws_bytes, void* stream) {
+  if (batch > 0 && (!d_n_rows || !d_n_cols || !d_trip_ptr)) return SPM_ERR_INVALID_ARG;
+  return run_assembly(batch, h_n_rows, h_n_cols, h_trip_ptr, d_n_rows, d_n_cols, d_trip_ptr, rows, cols, vals, seq,
+                      dtype, mode, flags, col_ptr, row_idx, out_vals, d_nnz, map, d_status, workspace, ws_bytes,
+                      stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,126 @@
+"""The C-ABI library: builds for sm_103a, loads, exports every entry point that
+include/spm.h declares, and rejects bad arguments on the host (no GPU needed:
+nothing here launches a kernel)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    names = []
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names += re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*(spm_[a-z0-9_]+)\s*\(", text, re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def spm():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1805_03380_gb300 as spm
+    return spm
+
+
+def test_library_exports_every_declared_symbol(spm):
+    declared = _declared_functions()
+    assert len(declared) >= 10
+    lib = ctypes.CDLL(spm.LIB_PATH)
+    for name in declared:
+        assert hasattr(lib, name), f"{name} declared in include/ but not exported"
+    assert set(declared) == set(spm.EXPORTED)
+
+
+def test_status_strings_and_version(spm):
+    L = spm.lib()
+    assert L.spm_status_string(0) == b"SPM_OK"
+    assert L.spm_status_string(6) == b"SPM_ERR_TIMEOUT"
+    assert L.spm_version() >= 10000
+
+
+def test_workspace_query_and_limits(spm):
+    import torch
+    ws = spm.spm_assemble_csc_workspace(100_000, 100_000, 100_000_000, torch.float64, "sum")
+    # records (8 + 8 bytes per write) dominate; planner tables are small next to them
+    assert 16 * 100_000_000 < ws < 22 * 100_000_000
+    ws_seq = spm.spm_assemble_csc_workspace(100_000, 100_000, 100_000_000, torch.float64, "sum", spm.SEQ_EXPLICIT)
+    assert ws_seq >= ws + 8 * 100_000_000
+    assert spm.spm_assemble_csc_workspace(1000, 1000, 0, torch.float32, "set") > 0
+    with pytest.raises(spm.SpmError) as e:
+        spm.spm_assemble_csc_workspace(1 << 30, 1 << 30, 10, torch.float64, "sum")  # 2^60 > 2^52 key space
+    assert e.value.code == 4
+    with pytest.raises(spm.SpmError) as e:
+        spm.spm_assemble_csc_workspace(-1, 5, 10, torch.float64, "sum")
+    assert e.value.code == 1
+    with pytest.raises(spm.SpmError):
+        spm.spm_assemble_csc_workspace(10, 10, 1 << 33, torch.float64, "sum")
+
+
+def test_batched_workspace_query(spm):
+    import torch
+    ws = spm.spm_assemble_csc_batched_workspace([10, 20, 30], [10, 20, 30], [0, 5, 5, 40], torch.float32, "set")
+    assert ws > 0
+    with pytest.raises(spm.SpmError):  # trip_ptr must start at 0 and not decrease
+        spm.spm_assemble_csc_batched_workspace([10, 20], [10, 20], [1, 5, 7], torch.float32, "set")
+    with pytest.raises(spm.SpmError):
+        spm.spm_assemble_csc_batched_workspace([10, 20], [10, 20], [0, 5, 3], torch.float32, "set")
+
+
+def test_host_argument_validation_launches_nothing(spm):
+    L = spm.lib()
+    # invalid dtype / mode / flags / missing status pointer are rejected before any CUDA call
+    args = dict(n_rows=10, n_cols=10, m=0)
+    null = None
+    assert L.spm_assemble_csc(10, 10, 0, null, null, null, null, 7, 0, 0, null, null, null, null, null, null, null, 0,
+                              null) == 1
+    assert L.spm_assemble_csc(10, 10, 0, null, null, null, null, 0, 9, 0, null, null, null, null, null, null, null, 0,
+                              null) == 1
+    assert L.spm_assemble_csc(10, 10, 0, null, null, null, null, 0, 0, 64, null, null, null, null, null, null, null,
+                              0, null) == 1
+    # SEQ_EXPLICIT without a seq pointer
+    assert L.spm_assemble_csc(10, 10, 0, null, null, null, null, 0, 0, 4, null, null, null, null, null, null, null,
+                              0, null) == 1
+    # KEEP_MAP without a map pointer
+    assert L.spm_assemble_csc(10, 10, 0, null, null, null, null, 0, 0, 1, null, null, null, null, null, null, null,
+                              0, null) == 1
+    assert L.spm_csc_mm(-1, 5, null, null, null, 0, 0, 4, null, 4, null, 4, null) == 1
+    assert L.spm_csc_mm(5, 5, null, null, null, 0, 2, 4, null, 4, null, 4, null) == 1
+    assert L.spm_triplet_dvals(-3, null, null, null, 0, 4, null, 4, null, 4, null, null) == 1
+    assert L.spm_triplet_dvals(0, null, null, null, 0, 4, null, 4, null, 4, null, null) == 0
+    del args
+
+
+def test_tuning_roundtrip(spm):
+    t0 = spm.spm_get_tuning()
+    try:
+        t = spm.spm_set_tuning(bucket_target=2048, sub_bits=10, partition_threads=512, resolve_threads=256)
+        assert t == {"bucket_target": 2048, "sub_bits": 10, "partition_threads": 512, "resolve_threads": 256}
+        with pytest.raises(spm.SpmError):
+            spm.spm_set_tuning(bucket_target=100)
+        with pytest.raises(spm.SpmError):
+            spm.spm_set_tuning(resolve_threads=1024)
+    finally:
+        spm.spm_set_tuning(reset=True)
+    assert spm.spm_get_tuning() == t0
+
+
+def test_product_package_does_not_import_the_oracle():
+    pkg = os.path.join(ROOT, "paper_1805_03380_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for fn in files:
+            if fn.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                text = open(os.path.join(dirpath, fn)).read()
+                assert not re.search(r"^\s*(import|from)\s+oracle\b", text, re.M), fn
+                assert "spm_oracle" not in text, fn
+    for fn in os.listdir(os.path.join(ROOT, "oracle")):
+        if fn.endswith((".py", ".cpp")):
+            text = open(os.path.join(ROOT, "oracle", fn)).read()
+            assert not re.search(r"^\s*(import|from)\s+paper_1805_03380_gb300\b", text, re.M), fn
+            assert not re.search(r"#\s*include\s*[<\"]spm\.h", text), fn
+            assert "libspm.so" not in text, fn
