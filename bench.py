@@ -221,6 +221,8 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=1_000_000, help="writes per step of --impl reference")
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", action="store_true",
+                    help="only the warm-up and timed steps (for ncu): no e2e, clock hold or CPU baseline")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -288,7 +290,7 @@ def main():
             stages.setdefault(kname, []).append(v)
     # keep the GPU under the same load for a moment so the clock sampler sees it
     t_extra = time.perf_counter()
-    while time.perf_counter() - t_extra < 1.0:
+    while not args.profile and time.perf_counter() - t_extra < 1.0:
         asm.run(rows, cols, vals)
         torch.cuda.synchronize()
     sampler.stop()
@@ -336,7 +338,10 @@ def main():
         torch.cuda.current_stream().synchronize()
         return 8 + (n_cols + 1) * 8 + k * (4 + sv)
 
-    e2e_step()
+    if args.profile:
+        e2e_steps = 0
+    else:
+        e2e_step()
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
@@ -344,13 +349,13 @@ def main():
     for _ in range(e2e_steps):
         d2h = e2e_step()
     e2e_s = time.perf_counter() - t0
-    e2e_tot_s, e2e_units = aggregate(e2e_s, m * e2e_steps, world, dev)
+    e2e_tot_s, e2e_units = aggregate(max(e2e_s, 1e-9), m * e2e_steps, world, dev)
     if int(asm.d_status.item()) != 0:
         raise RuntimeError("device status not OK after the e2e steps")
 
     # ---- CPU oracle baseline (rank 0, N = 1 only) ----
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.profile:
         sample = min(args.cpu_sample, m)
         rate, dt = oracle_rate(d, spec["mode"], sample)
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",

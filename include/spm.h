@@ -245,6 +245,17 @@ spm_status spm_debug_withhold_publication(int64_t bucket);
  * far in the process (all entry points).
  */
 spm_status spm_debug_stage_timing(int32_t enable);
+
+/*
+ * spm_debug_plan_stats -- after a single-matrix assembly call has completed,
+ * read back from its workspace (synchronous copies) statistics of the bucket
+ * plan: stats[0] buckets, [1] largest bucket, [2] buckets above the
+ * in-shared-memory capacity, [3] writes in those buckets, [4] capacity,
+ * [5] level-2 tables used, [6] planner's bucket bound.  Same sizing arguments
+ * as spm_assemble_csc_workspace.  A diagnostic; the paper has no counterpart.
+ */
+spm_status spm_debug_plan_stats(const void* workspace, size_t ws_bytes, int64_t n_rows, int64_t n_cols, int64_t m,
+                                spm_dtype dtype, spm_mode mode, uint32_t flags, int64_t* stats, int32_t n_stats);
 spm_status spm_debug_stage_times(int32_t back, float* ms, int32_t n);
 int64_t spm_debug_launch_count(void);
 

@@ -38,7 +38,7 @@ KEEP_MAP, CHECK_BOUNDS, SEQ_EXPLICIT = 1, 2, 4
 EXPORTED = ["spm_status_string", "spm_version", "spm_assemble_csc_workspace", "spm_assemble_csc",
             "spm_assemble_csc_batched_workspace", "spm_assemble_csc_batched", "spm_csc_mm", "spm_triplet_dvals",
             "spm_set_tuning", "spm_get_tuning", "spm_debug_withhold_publication", "spm_debug_stage_timing",
-            "spm_debug_stage_times", "spm_debug_launch_count"]
+            "spm_debug_stage_times", "spm_debug_launch_count", "spm_debug_plan_stats"]
 
 
 class SpmError(RuntimeError):
@@ -82,6 +82,8 @@ def lib():
     L.spm_debug_stage_timing.argtypes = [i32]
     L.spm_debug_stage_times.argtypes = [i32, ctypes.POINTER(ctypes.c_float), i32]
     L.spm_debug_launch_count.argtypes = []
+    L.spm_debug_plan_stats.argtypes = [p, sz, i64, i64, i64, ctypes.c_int, ctypes.c_int, u32,
+                                       ctypes.POINTER(ctypes.c_int64), i32]
     for name in EXPORTED:
         if name not in ("spm_status_string", "spm_version", "spm_debug_launch_count"):
             getattr(L, name).restype = ctypes.c_int
@@ -212,6 +214,16 @@ def spm_debug_stage_times(back=0):
 def spm_debug_launch_count():
     """Kernels launched by the library so far in this process."""
     return int(lib().spm_debug_launch_count())
+
+
+def spm_debug_plan_stats(asm):
+    """Bucket-plan statistics of the last call of an Assembler (synchronous)."""
+    out = (ctypes.c_int64 * 7)()
+    _check(lib().spm_debug_plan_stats(_ptr(asm.workspace), asm.workspace.numel(), asm.n_rows, asm.n_cols, asm.m,
+                                      _dtype_code(asm.dtype), _mode_code(asm.mode), asm.flags, out, 7),
+           "spm_debug_plan_stats")
+    keys = ("buckets", "largest", "over_capacity", "writes_over_capacity", "capacity", "l2_tables", "bucket_bound")
+    return dict(zip(keys, [int(x) for x in out]))
 
 
 def spm_get_tuning():

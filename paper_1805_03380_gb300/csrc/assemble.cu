@@ -1648,6 +1648,46 @@ spm_status spm_debug_stage_times(int32_t back, float* ms, int32_t n) {
 
 int64_t spm_debug_launch_count(void) { return g_launches.load(); }
 
+spm_status spm_debug_plan_stats(const void* workspace, size_t ws_bytes, int64_t n_rows, int64_t n_cols, int64_t m,
+                                spm_dtype dtype, spm_mode mode, uint32_t flags, int64_t* stats, int32_t n_stats) {
+  if (!workspace || !stats || n_stats < 0) return SPM_ERR_INVALID_ARG;
+  (void)mode;
+  spm_tuning tun;
+  {
+    std::lock_guard<std::mutex> lk(g_mutex);
+    tun = g_tuning;
+  }
+  int dev;
+  DevState* ds;
+  spm_status s = device_init(dev, ds);
+  if (s != SPM_OK) return s;
+  const int64_t tp[2] = {0, m};
+  HostPlan hp;
+  s = host_plan(1, &n_rows, &n_cols, tp, dtype == SPM_F64 ? 8 : 4, (flags & SPM_SEQ_EXPLICIT) != 0,
+                tun.bucket_target, ds->sms, hp);
+  if (s != SPM_OK) return s;
+  if (ws_bytes < hp.L.total) return SPM_ERR_WORKSPACE_TOO_SMALL;
+  const char* ws = static_cast<const char*>(workspace);
+  Scalars sc;
+  MatMeta mm;
+  if (cudaMemcpy(&sc, ws + hp.L.scal, sizeof(sc), cudaMemcpyDeviceToHost) != cudaSuccess) return SPM_ERR_CUDA;
+  if (cudaMemcpy(&mm, ws + hp.L.meta, sizeof(mm), cudaMemcpyDeviceToHost) != cudaSuccess) return SPM_ERR_CUDA;
+  std::vector<uint32_t> cnt(sc.NB);
+  if (sc.NB && cudaMemcpy(cnt.data(), ws + hp.L.bk_count, 4 * (size_t)sc.NB, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return SPM_ERR_CUDA;
+  int64_t mx = 0, over = 0, over_w = 0;
+  for (uint32_t c : cnt) {
+    mx = std::max<int64_t>(mx, c);
+    if (c > (uint32_t)kCap) {
+      ++over;
+      over_w += c;
+    }
+  }
+  const int64_t v[7] = {(int64_t)sc.NB, mx, over, over_w, kCap, mm.h2used, mm.nbcap};
+  for (int i = 0; i < n_stats && i < 7; ++i) stats[i] = v[i];
+  return SPM_OK;
+}
+
 spm_status spm_get_tuning(spm_tuning* t) {
   if (!t) return SPM_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> lk(g_mutex);
