@@ -20,9 +20,10 @@
  *     h_ (host memory).  The caller allocates and owns every buffer, including
  *     the workspace; the library never allocates, frees or synchronises.
  *   - Work is enqueued on `stream` (a cudaStream_t; NULL = legacy default
- *     stream) and returns immediately.  A call can be captured in a CUDA graph
- *     once its first call on the device has returned (that first call reads
- *     device attributes).
+ *     stream) and returns immediately.  spm_assemble_csc,
+ *     spm_assemble_csc_batched, spm_csc_mm and spm_triplet_dvals can be
+ *     captured in a CUDA graph once a first call on the device has returned
+ *     (that first call reads device attributes).
  *   - Host-detectable errors (NULL pointers, negative sizes, index spaces that
  *     are too large, a workspace that is too small) return an error status and
  *     launch nothing.  Errors found by the kernels (an index outside the
@@ -160,6 +161,37 @@ spm_status spm_assemble_csc_batched(int64_t batch, const int64_t* h_n_rows, cons
                                     int64_t* col_ptr, int32_t* row_idx, void* out_vals, int64_t* d_nnz,
                                     int32_t* map, int32_t* d_status, void* workspace, size_t ws_bytes,
                                     void* stream);
+
+/*
+ * spm_assemble_csc_static -- the same assembly as spm_assemble_csc, for
+ * callers that cannot allocate device memory and so cannot pass a workspace.
+ * The paper has no counterpart; this exists for integration only.  Typical
+ * such callers: code running inside a host application that owns every
+ * device allocation and gives it nothing but its inputs and outputs, or a
+ * loop that must not allocate once it has started.
+ *
+ * Instead of a workspace the call uses a 32 MiB scratch array that is part of
+ * this library's device image: every GPU on which the library is loaded
+ * holds that array until the process exits.  The call itself allocates
+ * nothing.  Sizes whose workspace (spm_assemble_csc_workspace) exceeds
+ * 32 MiB -- roughly 1.5 million float64 writes -- are rejected with
+ * SPM_ERR_WORKSPACE_TOO_SMALL before anything is launched.
+ *
+ * The first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.  All
+ * calls on a device share the one array and it keeps whatever the last call
+ * left in it; the call clears the parts that must start at zero itself.  Two
+ * calls whose kernels overlap on the GPU (different streams without
+ * ordering, or different host threads) race on the array and give wrong
+ * results: order them on one stream.
+ *
+ * Arguments, outputs and errors are exactly those of spm_assemble_csc
+ * without `workspace` and `ws_bytes`.
+ */
+spm_status spm_assemble_csc_static(int64_t n_rows, int64_t n_cols, int64_t m, const int32_t* rows,
+                                   const int32_t* cols, const void* vals, const uint64_t* seq, spm_dtype dtype,
+                                   spm_mode mode, uint32_t flags, int64_t* col_ptr, int32_t* row_idx,
+                                   void* out_vals, int64_t* d_nnz, int32_t* map, int32_t* d_status, void* stream);
 
 /*
  * spm_csc_mm -- Y = A X (transpose = 0) or Y = A^T X (transpose = 1) for A in

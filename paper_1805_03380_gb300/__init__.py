@@ -38,7 +38,7 @@ KEEP_MAP, CHECK_BOUNDS, SEQ_EXPLICIT = 1, 2, 4
 EXPORTED = ["spm_status_string", "spm_version", "spm_assemble_csc_workspace", "spm_assemble_csc",
             "spm_assemble_csc_batched_workspace", "spm_assemble_csc_batched", "spm_csc_mm", "spm_triplet_dvals",
             "spm_set_tuning", "spm_get_tuning", "spm_debug_withhold_publication", "spm_debug_stage_timing",
-            "spm_debug_stage_times", "spm_debug_launch_count", "spm_debug_plan_stats"]
+            "spm_debug_stage_times", "spm_debug_launch_count", "spm_debug_plan_stats", "spm_assemble_csc_static"]
 
 
 class SpmError(RuntimeError):
@@ -74,6 +74,8 @@ def lib():
                                                      ctypes.POINTER(sz)]
     L.spm_assemble_csc_batched.argtypes = [i64, p, p, p, p, p, p, p, p, p, p, ctypes.c_int, ctypes.c_int, u32, p, p,
                                            p, p, p, p, p, sz, p]
+    L.spm_assemble_csc_static.argtypes = [i64, i64, i64, p, p, p, p, ctypes.c_int, ctypes.c_int, u32, p, p, p, p, p,
+                                          p, p]
     L.spm_csc_mm.argtypes = [i64, i64, p, p, p, ctypes.c_int, i32, i64, p, i64, p, i64, p]
     L.spm_triplet_dvals.argtypes = [i64, p, p, p, ctypes.c_int, i64, p, i64, p, i64, p, p]
     L.spm_set_tuning.argtypes = [ctypes.POINTER(_Tuning)]
@@ -140,6 +142,17 @@ def spm_assemble_csc(n_rows, n_cols, rows, cols, vals, seq, mode, flags, col_ptr
                                   _ptr(row_idx), _ptr(out_vals), _ptr(d_nnz), _ptr(map), _ptr(d_status),
                                   _ptr(workspace), workspace.numel() * workspace.element_size(), _stream(stream))
     _check(code, "spm_assemble_csc")
+
+
+def spm_assemble_csc_static(n_rows, n_cols, rows, cols, vals, seq, mode, flags, col_ptr, row_idx, out_vals, d_nnz,
+                            map, d_status, stream=None):
+    """spm_assemble_csc without a workspace: the library's built-in 32 MiB
+    device scratch array is used instead (for callers that cannot allocate)."""
+    code = lib().spm_assemble_csc_static(int(n_rows), int(n_cols), rows.numel(), _ptr(rows), _ptr(cols), _ptr(vals),
+                                         _ptr(seq), _dtype_code(vals.dtype), _mode_code(mode), int(flags),
+                                         _ptr(col_ptr), _ptr(row_idx), _ptr(out_vals), _ptr(d_nnz), _ptr(map),
+                                         _ptr(d_status), _stream(stream))
+    _check(code, "spm_assemble_csc_static")
 
 
 def _host_i64(a):
