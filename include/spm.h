@@ -58,8 +58,11 @@ typedef enum {
 /* Duplicate resolution.  LAST_WRITE: element setting, X(r,c) = v (Table 1);
  * the write with the largest (seq, position) wins and its value is copied
  * bit for bit.  SUM: batch insertion with accumulation, X(r,c) += v (Fig. 2);
- * the writes to one element are added in (seq, position) order in double
- * precision and rounded once to the output type. */
+ * the exact sum of the writes to one element is rounded once to the output
+ * type (round-to-nearest-even), so the result does not depend on the order of
+ * the writes (seq has no effect in this mode).  Bits of a value lying more than
+ * 58 bits below the largest value of its bucket are dropped (at most 2^-110 of
+ * that value per write).  NaN and infinities follow IEEE addition. */
 typedef enum { SPM_MODE_LAST_WRITE = 0, SPM_MODE_SUM = 1 } spm_mode;
 
 /* Value type of the writes and of the CSC values.  SPM_F32 values are

@@ -38,6 +38,8 @@
 #include <vector>
 
 #include "spm_common.cuh"
+#include "exact_sum.cuh"
+#include <climits>
 
 namespace spm {
 
@@ -208,27 +210,36 @@ __global__ void k_setup_batched(Ctx c, const int64_t* __restrict__ d_n_rows, con
 // ===========================================================================
 // Sampling
 // ===========================================================================
+// Draw the samples (fixed positions: one per stride of the matrix's writes,
+// offset inside the stride by a hash) and count them per level-1 cell.  Lanes
+// of a warp that hit the same cell add their count with one atomic.
 __global__ void k_sample(Ctx c) {
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= c.S_total || is_aborted(c)) return;
-  const MatMeta* meta = c.meta;
-  const int64_t i = upper_index(0, c.B - 1, g, [&](int64_t j) { return meta[j].samp_off; });
-  const MatMeta& mm = meta[i];
-  const uint64_t k = (uint64_t)(g - mm.samp_off);
-  const uint64_t m = (uint64_t)mm.m, ns = (uint64_t)mm.ns;
-  uint64_t p;
-  if (ns >= m) {
-    p = k;
-  } else {
-    const uint64_t a = k * m / ns, b = (k + 1) * m / ns;
-    p = a + (b > a ? mix32((uint64_t)g * 0x9e3779b97f4a7c15ull + 17) % (b - a) : 0);
+  unsigned long long cidx = ~0ull;
+  if (g < c.S_total && !is_aborted(c)) {
+    const MatMeta* meta = c.meta;
+    const int64_t i = upper_index(0, c.B - 1, g, [&](int64_t j) { return meta[j].samp_off; });
+    const MatMeta& mm = meta[i];
+    const uint64_t k = (uint64_t)(g - mm.samp_off);
+    const uint64_t m = (uint64_t)mm.m, ns = (uint64_t)mm.ns;
+    uint64_t p;
+    if (ns >= m) {
+      p = k;
+    } else {
+      const uint64_t a = k * m / ns, b = (k + 1) * m / ns;
+      p = a + (b > a ? mix32((uint64_t)g * 0x9e3779b97f4a7c15ull + 17) % (b - a) : 0);
+    }
+    const int64_t t = mm.t0 + (int64_t)p;
+    const int32_t r = c.rows[t], col = c.cols[t];
+    uint64_t key = kBadKey;
+    if (r >= 0 && (int64_t)r < mm.n_rows && col >= 0 && (int64_t)col < mm.n_cols) {
+      key = (uint64_t)col * (uint64_t)mm.n_rows + (uint64_t)r;
+      cidx = (unsigned long long)mm.lut_off + (key >> mm.s1);
+    }
+    c.samp[g] = key;
   }
-  const int64_t t = mm.t0 + (int64_t)p;
-  const int32_t r = c.rows[t], col = c.cols[t];
-  uint64_t key = kBadKey;
-  if (r >= 0 && (int64_t)r < mm.n_rows && col >= 0 && (int64_t)col < mm.n_cols)
-    key = (uint64_t)col * (uint64_t)mm.n_rows + (uint64_t)r;
-  c.samp[g] = key;
+  const unsigned peers = __match_any_sync(0xffffffffu, cidx);
+  if (cidx != ~0ull && (int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&c.cellcnt[cidx], (uint32_t)__popc(peers));
 }
 
 // ===========================================================================
@@ -239,6 +250,9 @@ struct Split {
   uint32_t count;
 };
 
+// A leaf of 2^shift keys starting at lo, expected to receive `est` writes, is
+// split into 2^j equal buckets of at most about tgt writes each; buckets that
+// start at or beyond K are not created.
 __device__ __forceinline__ Split leaf_split(uint64_t lo, int shift, uint64_t est, uint64_t tgt, uint64_t K) {
   Split s{0, 0};
   if (lo >= K) return s;
@@ -255,28 +269,42 @@ __device__ __forceinline__ Split leaf_split(uint64_t lo, int shift, uint64_t est
   return s;
 }
 
-__device__ __forceinline__ uint64_t estimate(uint32_t cnt, const MatMeta& mm) {
+// Writes expected in a region that received `cnt` samples: the count plus a
+// two-standard-deviation margin, scaled by writes per sample.
+__device__ __forceinline__ uint64_t estimate(uint64_t cnt, const MatMeta& mm) {
   if (mm.ns <= 0) return 0;
   if (mm.ns >= mm.m) return cnt;
-  const uint64_t x = (uint64_t)cnt + 2ull * isqrt_u32(cnt) + 1ull;  // upper confidence margin
+  const uint64_t x = cnt + 2ull * (uint64_t)sqrtf((float)cnt) + 1ull;
   return x * (uint64_t)mm.m / (uint64_t)mm.ns;
 }
 
-__global__ void __launch_bounds__(512) k_plan(Ctx c) {
+constexpr int kMergeL1Max = 13;  // cells can be merged when the matrix has at most 2^13 of them
+constexpr size_t kPlanSmem = (size_t)kMaxL2Tables * kL2Size * 4 * 2 + ((size_t{1} << kMergeL1Max) + 1) * 8 +
+                             ((size_t{1} << kMergeL1Max) + 1) * 2 + 64;
+
+__global__ void __launch_bounds__(1024) k_plan(Ctx c) {
+  extern __shared__ __align__(16) unsigned char psm[];
+  uint32_t* cnt2 = reinterpret_cast<uint32_t*>(psm);                 // level-2 sample counts
+  uint32_t* spl2 = cnt2 + kMaxL2Tables * kL2Size;                    // level-2 splits: j << 27 | count
+  uint64_t* P = reinterpret_cast<uint64_t*>(spl2 + kMaxL2Tables * kL2Size);  // prefix of level-1 counts
+  uint16_t* T = reinterpret_cast<uint16_t*>(P + (size_t{1} << kMergeL1Max) + 1);  // prefix of table flags
   __shared__ MatMeta mm;
   __shared__ uint32_t buf[32];
-  __shared__ uint32_t s_tot;
-  __shared__ uint32_t s_red;
+  __shared__ unsigned long long buf64[32];
+  __shared__ uint32_t s_tot, s_red;
+  __shared__ unsigned long long s_tot64;
+  __shared__ uint32_t tbl_cell[kMaxL2Tables], tbl_nb[kMaxL2Tables], tbl_base[kMaxL2Tables];
   const int64_t i = blockIdx.x;
-  if (threadIdx.x == 0) mm = c.meta[i];
+  const int tid = threadIdx.x, NT = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarps = NT >> 5;
+  if (tid == 0) mm = c.meta[i];
   __syncthreads();
   if (is_aborted(c)) return;
-  uint32_t* cnt = c.cellcnt + mm.lut_off;
+  const uint32_t* cnt = c.cellcnt + mm.lut_off;
   uint32_t* lut = c.lut + mm.lut_off;
   int32_t* l2cell = c.l2cell + mm.l2_off;
   const int64_t L1size = int64_t{1} << mm.L1;
   if (mm.K == 0) {
-    if (threadIdx.x == 0) {
+    if (tid == 0) {
       lut[0] = 0;
       c.meta[i].nb = 1;
       c.meta[i].h2used = 0;
@@ -284,37 +312,30 @@ __global__ void __launch_bounds__(512) k_plan(Ctx c) {
     return;
   }
   const uint64_t* samp = c.samp + mm.samp_off;
-  // level-1 counts
-  for (int64_t k = threadIdx.x; k < mm.ns; k += blockDim.x) {
-    const uint64_t key = samp[k];
-    if (key != kBadKey) atomicAdd(&cnt[key >> mm.s1], 1u);
-  }
-  __syncthreads();
-  // choose the cells refined by a level-2 table: the heaviest cells whose
-  // estimate exceeds 8 buckets' worth, at most H2 of them
-  uint32_t h = 0;
   const uint64_t tgt = (uint64_t)c.tgt;
+  // ---- level-2 tables for the heaviest cells (at most H2, each worth > 8 buckets)
+  uint32_t h = 0;
   if (mm.H2 > 0) {
     const uint64_t thr = 8ull * tgt;
     uint32_t mx = 0;
-    for (int64_t cell = threadIdx.x; cell < L1size; cell += blockDim.x) mx = max(mx, cnt[cell]);
+    for (int64_t cell = tid; cell < L1size; cell += NT) mx = max(mx, cnt[cell]);
     for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if (threadIdx.x == 0) s_red = 0;
+    if (tid == 0) s_red = 0;
     __syncthreads();
-    if ((threadIdx.x & 31) == 0) atomicMax(&s_red, mx);
+    if (lane == 0) atomicMax(&s_red, mx);
     __syncthreads();
     mx = s_red;
     __syncthreads();
-    uint32_t lo = 1, hi = mx + 1;  // smallest tau with at most H2 candidates
+    uint32_t lo = 1, hi = mx + 1;
     while (lo < hi) {
       const uint32_t mid = lo + (hi - lo) / 2;
       uint32_t n = 0;
-      for (int64_t cell = threadIdx.x; cell < L1size; cell += blockDim.x)
+      for (int64_t cell = tid; cell < L1size; cell += NT)
         n += (cnt[cell] >= mid && estimate(cnt[cell], mm) > thr) ? 1u : 0u;
       for (int o = 16; o > 0; o >>= 1) n += __shfl_xor_sync(0xffffffffu, n, o);
-      if (threadIdx.x == 0) s_red = 0;
+      if (tid == 0) s_red = 0;
       __syncthreads();
-      if ((threadIdx.x & 31) == 0) atomicAdd(&s_red, n);
+      if (lane == 0) atomicAdd(&s_red, n);
       __syncthreads();
       n = s_red;
       __syncthreads();
@@ -322,105 +343,178 @@ __global__ void __launch_bounds__(512) k_plan(Ctx c) {
     }
     const uint32_t tau = lo;
     uint32_t carry = 0;
-    for (int64_t base = 0; base < L1size; base += blockDim.x) {
-      const int64_t cell = base + threadIdx.x;
+    for (int64_t base = 0; base < L1size; base += NT) {
+      const int64_t cell = base + tid;
       uint32_t f = 0;
       if (cell < L1size) f = (cnt[cell] >= tau && estimate(cnt[cell], mm) > thr) ? 1u : 0u;
       const uint32_t off = block_scan_excl<uint32_t>(f, &s_tot, buf) + carry;
       if (cell < L1size) {
         lut[cell] = f ? (kPtrFlag | off) : 0u;
-        if (f) l2cell[off] = (int32_t)cell;
+        if (f) {
+          l2cell[off] = (int32_t)cell;
+          tbl_cell[off] = (uint32_t)cell;
+        }
       }
       carry += s_tot;
     }
     h = carry;
   } else {
-    for (int64_t cell = threadIdx.x; cell < L1size; cell += blockDim.x) lut[cell] = 0u;
+    for (int64_t cell = tid; cell < L1size; cell += NT) lut[cell] = 0u;
   }
   __syncthreads();
-  // level-2 counts
+  const int s2 = mm.s1 - kL2Bits;
   if (h > 0) {
-    const int s2 = mm.s1 - kL2Bits;
-    for (int64_t k = threadIdx.x; k < mm.ns; k += blockDim.x) {
+    for (uint32_t q = tid; q < h * kL2Size; q += NT) cnt2[q] = 0u;
+    __syncthreads();
+    for (int64_t k = tid; k < mm.ns; k += NT) {
       const uint64_t key = samp[k];
       if (key == kBadKey) continue;
       const uint32_t e = lut[key >> mm.s1];
-      if (e & kPtrFlag)
-        atomicAdd(&cnt[L1size + (int64_t)(e & ~kPtrFlag) * kL2Size + ((key >> s2) & (kL2Size - 1))], 1u);
+      if (e & kPtrFlag) atomicAdd(&cnt2[(e & ~kPtrFlag) * kL2Size + ((key >> s2) & (kL2Size - 1))], 1u);
+    }
+  }
+  // ---- prefix sums for merging cold level-1 cells into aligned groups
+  const bool merging = mm.L1 <= kMergeL1Max;
+  if (merging) {
+    unsigned long long carry = 0;
+    uint32_t tcarry = 0;
+    for (int64_t base = 0; base < L1size; base += NT) {
+      const int64_t cell = base + tid;
+      const unsigned long long v = cell < L1size ? (unsigned long long)cnt[cell] : 0ull;
+      const uint32_t f = (cell < L1size && (lut[cell] & kPtrFlag)) ? 1u : 0u;
+      const unsigned long long off = block_scan_excl<unsigned long long>(v, &s_tot64, buf64) + carry;
+      const uint32_t toff = block_scan_excl<uint32_t>(f, &s_tot, buf) + tcarry;
+      if (cell < L1size) {
+        P[cell] = off;
+        T[cell] = (uint16_t)toff;
+      }
+      carry += s_tot64;
+      tcarry += s_tot;
+    }
+    if (tid == 0) {
+      P[L1size] = carry;
+      T[L1size] = (uint16_t)tcarry;
     }
   }
   __syncthreads();
-  // number of buckets per leaf; retry with a larger target if over the cap
+  const int gcap = min(min(mm.L1, 32 - mm.s1), kMergeL1Max);
+  // largest g such that the aligned block of 2^g cells around `cell` has no
+  // table and is expected to hold at most tg writes
+  auto gmax_of = [&](int64_t cell, uint64_t tg) -> int {
+    if (!merging) return 0;
+    int g = 0;
+    for (int gg = 1; gg <= gcap; ++gg) {
+      const int64_t lo_c = (cell >> gg) << gg, hi_c = lo_c + (int64_t{1} << gg);
+      if (T[hi_c] != T[lo_c]) break;
+      if (estimate(P[hi_c] - P[lo_c], mm) > tg) break;
+      g = gg;
+    }
+    return g;
+  };
+  // ---- buckets per leaf; retry with a larger target while over the bound
   uint64_t tg = tgt;
   uint32_t nb_total = 0;
   for (int attempt = 0;; ++attempt) {
-    uint32_t carry = 0;
-    for (int64_t base = 0; base < L1size; base += blockDim.x) {
-      const int64_t cell = base + threadIdx.x;
+    for (uint32_t q = tid; q < h * kL2Size; q += NT) {
+      const uint32_t tb = q >> kL2Bits, u = q & (kL2Size - 1);
+      const uint64_t lo = ((uint64_t)tbl_cell[tb] << mm.s1) + ((uint64_t)u << s2);
+      const Split sp = leaf_split(lo, s2, estimate(cnt2[q], mm), tg, mm.K);
+      spl2[q] = ((uint32_t)sp.j << 27) | sp.count;
+    }
+    __syncthreads();
+    for (uint32_t tb = warp; tb < h; tb += nwarps) {
+      uint32_t sum = 0;
+      for (int u = lane; u < kL2Size; u += 32) sum += spl2[tb * kL2Size + u] & 0x7FFFFFFu;
+      for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+      if (lane == 0) tbl_nb[tb] = sum;
+    }
+    __syncthreads();
+    uint32_t total = 0;
+    for (int64_t base = 0; base < L1size; base += NT) {
+      const int64_t cell = base + tid;
       uint32_t nbc = 0;
       if (cell < L1size) {
         const uint32_t e = lut[cell];
         const uint64_t clo = (uint64_t)cell << mm.s1;
         if (e & kPtrFlag) {
-          const uint32_t* c2 = cnt + L1size + (int64_t)(e & ~kPtrFlag) * kL2Size;
-          const int s2 = mm.s1 - kL2Bits;
-          for (int u = 0; u < kL2Size; ++u)
-            nbc += leaf_split(clo + ((uint64_t)u << s2), s2, estimate(c2[u], mm), tg, mm.K).count;
+          nbc = tbl_nb[e & ~kPtrFlag];
         } else {
-          nbc = leaf_split(clo, mm.s1, estimate(cnt[cell], mm), tg, mm.K).count;
+          const int g = gmax_of(cell, tg);
+          if (g > 0) nbc = ((cell & ((int64_t{1} << g) - 1)) == 0 && clo < mm.K) ? 1u : 0u;
+          else nbc = leaf_split(clo, mm.s1, estimate(cnt[cell], mm), tg, mm.K).count;
         }
       }
       block_scan_excl<uint32_t>(nbc, &s_tot, buf);
-      carry += s_tot;
+      total += s_tot;
     }
-    nb_total = carry;
-    if ((int64_t)nb_total <= mm.nbcap || attempt >= 48) break;
+    nb_total = total;
+    if ((int64_t)nb_total <= mm.nbcap || attempt >= 40) break;
     tg *= 2;
   }
   if ((int64_t)nb_total > mm.nbcap) {
-    if (threadIdx.x == 0) record_fatal(c, SPM_ERR_UNSUPPORTED);
+    if (tid == 0) record_fatal(c, SPM_ERR_UNSUPPORTED);
     return;
   }
-  // write the leaf entries: j in bits 26..30, first local bucket in bits 0..25
+  // ---- write the entries: level-1 cells (and the bases of the tables)
   uint32_t carry = 0;
-  for (int64_t base = 0; base < L1size; base += blockDim.x) {
-    const int64_t cell = base + threadIdx.x;
-    uint32_t nbc = 0;
-    uint32_t e = 0;
-    Split s1v{0, 0};
-    const uint64_t clo = (uint64_t)cell << mm.s1;
+  for (int64_t base = 0; base < L1size; base += NT) {
+    const int64_t cell = base + tid;
+    uint32_t nbc = 0, ent = 0;
     if (cell < L1size) {
-      e = lut[cell];
+      const uint32_t e = lut[cell];
+      const uint64_t clo = (uint64_t)cell << mm.s1;
       if (e & kPtrFlag) {
-        const uint32_t* c2 = cnt + L1size + (int64_t)(e & ~kPtrFlag) * kL2Size;
-        const int s2 = mm.s1 - kL2Bits;
-        for (int u = 0; u < kL2Size; ++u)
-          nbc += leaf_split(clo + ((uint64_t)u << s2), s2, estimate(c2[u], mm), tg, mm.K).count;
+        nbc = tbl_nb[e & ~kPtrFlag];
+        ent = e;
       } else {
-        s1v = leaf_split(clo, mm.s1, estimate(cnt[cell], mm), tg, mm.K);
-        nbc = s1v.count;
+        const int g = gmax_of(cell, tg);
+        if (g > 0) {
+          const bool first = (cell & ((int64_t{1} << g) - 1)) == 0;
+          const int64_t glo_cell = (cell >> g) << g;
+          nbc = (first && clo < mm.K) ? 1u : 0u;
+          ent = kMergeFlag | ((uint32_t)g << kXShift);
+          // members point at their group's bucket
+          ent |= first ? 0u : ((((uint64_t)glo_cell << mm.s1) < mm.K) ? 0x80000000u : 0u);  // marker, fixed below
+        } else {
+          const Split sp = leaf_split(clo, mm.s1, estimate(cnt[cell], mm), tg, mm.K);
+          nbc = sp.count;
+          ent = (uint32_t)sp.j << kXShift;
+        }
       }
     }
     const uint32_t off = block_scan_excl<uint32_t>(nbc, &s_tot, buf) + carry;
     if (cell < L1size) {
-      if (e & kPtrFlag) {
-        const int64_t tb = (int64_t)(e & ~kPtrFlag);
-        const uint32_t* c2 = cnt + L1size + tb * kL2Size;
-        uint32_t* l2 = lut + L1size + tb * kL2Size;
-        const int s2 = mm.s1 - kL2Bits;
-        uint32_t run = off;
-        for (int u = 0; u < kL2Size; ++u) {
-          const Split sp = leaf_split(clo + ((uint64_t)u << s2), s2, estimate(c2[u], mm), tg, mm.K);
-          l2[u] = ((uint32_t)sp.j << kBaseBits) | run;
-          run += sp.count;
+      if (ent & kPtrFlag) {
+        if (ent & kMergeFlag) {
+          // merged member whose group exists: the group's bucket precedes this cell
+          lut[cell] = (ent & ~kPtrFlag) | ((off - 1) & kBaseMask);
+        } else {
+          tbl_base[ent & ~kPtrFlag] = off;
         }
       } else {
-        lut[cell] = ((uint32_t)s1v.j << kBaseBits) | off;
+        lut[cell] = ent | (off & kBaseMask);
       }
     }
     carry += s_tot;
   }
-  if (threadIdx.x == 0) {
+  __syncthreads();
+  // ---- level-2 entries: base of the table plus the prefix inside it
+  for (uint32_t tb = warp; tb < h; tb += nwarps) {
+    uint32_t run = tbl_base[tb];
+    for (int u0 = 0; u0 < kL2Size; u0 += 32) {
+      const uint32_t sp = spl2[tb * kL2Size + u0 + lane];
+      const uint32_t cntq = sp & 0x7FFFFFFu;
+      uint32_t x = cntq;
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+      }
+      const uint32_t excl = run + x - cntq;
+      lut[L1size + tb * kL2Size + u0 + lane] = ((sp >> 27) << kXShift) | (excl & kBaseMask);
+      run += __shfl_sync(0xffffffffu, x, 31);
+    }
+  }
+  if (tid == 0) {
     c.meta[i].nb = nb_total;
     c.meta[i].h2used = (int32_t)h;
   }
@@ -483,8 +577,8 @@ __global__ void k_bucket_scan(Ctx c) {
   if (threadIdx.x == 0 && hcarry > (unsigned long long)c.hist_bound) record_fatal(c, SPM_ERR_UNSUPPORTED);
 }
 
-// Bucket descriptors (first key and width) from the leaf entries: one warp per
-// LUT entry.
+// Bucket descriptors (first key and width) from the LUT entries: one warp per
+// entry.
 __global__ void k_bucket_fill(Ctx c) {
   const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
@@ -518,11 +612,20 @@ __global__ void k_bucket_fill(Ctx c) {
     lo = ((uint64_t)cell << mm.s1) + ((uint64_t)u << shift);
   }
   if (lo >= mm.K) return;
-  const int j = (ent >> kBaseBits) & 31;
+  const int x = (ent >> kXShift) & 31;
   const uint32_t base = ent & kBaseMask;
-  const int w = shift - j;
+  if (ent & kMergeFlag) {
+    if ((e & ((int64_t{1} << x) - 1)) != 0) return;  // not the first cell of its group
+    if (lane == 0) {
+      const int64_t b = mm.bucket_off + base;
+      c.bk_lo[b] = lo;
+      c.bk_info[b] = ((uint32_t)i << 6) | (uint32_t)(shift + x);
+    }
+    return;
+  }
+  const int w = shift - x;
   const uint64_t n = ((mm.K - lo) + ((uint64_t{1} << w) - 1)) >> w;
-  const uint64_t full = uint64_t{1} << j;
+  const uint64_t full = uint64_t{1} << x;
   const uint64_t count = n < full ? n : full;
   for (uint64_t q = lane; q < count; q += 32) {
     const int64_t b = mm.bucket_off + base + (int64_t)q;
@@ -568,9 +671,16 @@ __device__ __forceinline__ bool classify(const MatView& v, int32_t r, int32_t co
     sh = v.s1 - kL2Bits;
     e = v.lut[v.L1size + (int64_t)(e & ~kPtrFlag) * kL2Size + ((key >> sh) & (kL2Size - 1))];
   }
-  const int j = (e >> kBaseBits) & 31;
-  const int w = sh - j;
-  const uint32_t sub = (uint32_t)((key >> w) & ((uint64_t{1} << j) - 1));
+  const int x = (e >> kXShift) & 31;
+  int w;
+  uint32_t sub;
+  if (e & kMergeFlag) {
+    w = sh + x;
+    sub = 0;
+  } else {
+    w = sh - x;
+    sub = (uint32_t)((key >> w) & ((uint64_t{1} << x) - 1));
+  }
   brel = (uint32_t)(v.bucket_rel + (int64_t)(e & kBaseMask) + sub);
   lkey = (uint32_t)(key & ((uint64_t{1} << w) - 1));
   return true;
@@ -631,7 +741,22 @@ __global__ void __launch_bounds__(1024) k_hist(Ctx c) {
     const int64_t nvec = (ci.e1 - ci.e0) >> 2;
     const int4* r4p = reinterpret_cast<const int4*>(c.rows + ci.e0);
     const int4* c4p = reinterpret_cast<const int4*>(c.cols + ci.e0);
-    for (int64_t q = threadIdx.x; q < nvec; q += blockDim.x) {
+    const int64_t NT = blockDim.x;
+    int64_t q = threadIdx.x;
+    for (; q + NT < nvec; q += 2 * NT) {  // two independent 16-byte loads per array in flight
+      const int4 ra = __ldcs(r4p + q), ca = __ldcs(c4p + q);
+      const int4 rb = __ldcs(r4p + q + NT), cb = __ldcs(c4p + q + NT);
+      const int64_t ta = ci.e0 + 4 * q, tb = ci.e0 + 4 * (q + NT);
+      body(ta, ra.x, ca.x);
+      body(ta + 1, ra.y, ca.y);
+      body(ta + 2, ra.z, ca.z);
+      body(ta + 3, ra.w, ca.w);
+      body(tb, rb.x, cb.x);
+      body(tb + 1, rb.y, cb.y);
+      body(tb + 2, rb.z, cb.z);
+      body(tb + 3, rb.w, cb.w);
+    }
+    for (; q < nvec; q += NT) {
       const int4 r4 = __ldcs(r4p + q), c4 = __ldcs(c4p + q);
       const int64_t t = ci.e0 + 4 * q;
       body(t, r4.x, c4.x);
@@ -650,20 +775,32 @@ __global__ void __launch_bounds__(1024) k_hist(Ctx c) {
 }
 
 // Per bucket: exclusive prefix over the partition blocks (in place) and total.
-__global__ void k_colscan(Ctx c) {
+constexpr int kMaxCtas = 1024;
+__global__ void __launch_bounds__(256) k_colscan(Ctx c) {
+  __shared__ uint32_t s_cb0[kMaxCtas], s_cb1[kMaxCtas];
+  __shared__ int64_t s_hoff[kMaxCtas];
   const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= c.nbcap_total) return;
   if (is_aborted(c)) return;
+  const int C = (int)c.C;
+  for (int cc = threadIdx.x; cc < C; cc += blockDim.x) {
+    const CtaInfo& ci = c.cta[cc];
+    const bool nonempty = ci.e0 < ci.e1;
+    s_cb0[cc] = nonempty ? ci.cb0 : 1u;
+    s_cb1[cc] = nonempty ? ci.cb1 : 0u;
+    s_hoff[cc] = ci.hoff;
+  }
+  __syncthreads();
+  if (b >= c.nbcap_total) return;
   const int64_t NB = c.scal->NB;
   if (b >= NB) {
     c.bk_count[b] = 0u;
     return;
   }
   uint32_t running = 0;
-  for (int64_t cc = 0; cc < c.C; ++cc) {
-    const uint32_t cb0 = c.cta[cc].cb0, cb1 = c.cta[cc].cb1;
-    if ((uint32_t)b >= cb0 && (uint32_t)b < cb1 && c.cta[cc].e0 < c.cta[cc].e1) {
-      uint32_t* p = c.hist + c.cta[cc].hoff + (b - cb0);
+  for (int cc = 0; cc < C; ++cc) {
+    const uint32_t cb0 = s_cb0[cc];
+    if ((uint32_t)b >= cb0 && (uint32_t)b < s_cb1[cc]) {
+      uint32_t* p = c.hist + s_hoff[cc] + (b - cb0);
       const uint32_t v = *p;
       *p = running;
       running += v;
@@ -720,15 +857,14 @@ __global__ void __launch_bounds__(1024) k_scatter(Ctx c) {
   MatView v;
   load_view(c, ci, lut_base, lut_smem, ci.i0, v);
   using VT = typename std::conditional<F64, uint64_t, uint32_t>::type;
-  VT* rv = reinterpret_cast<VT*>(c.rv);
   const VT* vin = reinterpret_cast<const VT*>(c.vals);
   auto body = [&](int64_t t, int32_t r, int32_t col, VT val) {
     advance_view<BATCHED>(c, ci, lut_base, lut_smem, t, v);
     uint32_t b, lk;
     if (classify(v, r, col, b, lk)) {
       const uint32_t slot = atomicAdd(&cur[b], 1u);
-      c.rk[slot] = ((uint64_t)lk << 32) | (uint32_t)t;
-      rv[slot] = val;
+      const uint64_t vb = (uint64_t)val;
+      *reinterpret_cast<uint4*>(c.rec + slot) = make_uint4(lk, (uint32_t)t, (uint32_t)vb, (uint32_t)(vb >> 32));
       if (SEQ) c.rs[slot] = c.seq[t];
     }
   };
@@ -763,26 +899,56 @@ __global__ void __launch_bounds__(1024) k_scatter(Ctx c) {
 // ===========================================================================
 // Resolve: one bucket at a time per block (persistent)
 // ===========================================================================
-struct ResolveSmem {
-  uint64_t* rk;    // [kCap] records (key-in-bucket << 32 | stream position)
-  void* rv;        // [kCap] raw values
-  uint32_t* orig;  // [kCap] index of the record in its bucket (window mode only)
-  uint16_t* perm;  // [kCap] sorted order
-  uint32_t* sub_a; // [2^sub_bits + 1]
-  uint32_t* sub_b; // [2^sub_bits]
+// Shared-memory layout of the resolve kernel (host and device agree on it).
+struct RLayout {
+  size_t keys, vals, pos, perm, orig, sub_a, sub_b, slots, total;
+};
+
+struct __align__(8) Slot {
+  uint64_t a, b;      // add mode: accumulator (lo, hi); last-write mode: seq, pos | idx << 32
+  uint32_t flags;     // add mode: NaN/Inf flags; last-write mode: 1 if a write is present
+  uint32_t has_head;  // the thread's range contains the start of a run (or is past the end)
+};
+
+__host__ __device__ inline RLayout resolve_layout(int cap, bool pos, bool seq, int nt, int sub_bits) {
+  RLayout L;
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = o;
+    o = (o + bytes + 15) & ~size_t{15};
+    return at;
+  };
+  L.keys = take(4ull * cap);
+  L.vals = take(8ull * cap);
+  L.pos = pos ? take(4ull * cap) : o;
+  L.perm = take(2ull * cap);
+  L.orig = seq ? take(4ull * cap) : o;
+  L.sub_a = take(4ull * ((size_t{1} << sub_bits) + 4));
+  L.sub_b = take(4ull * (size_t{1} << sub_bits));
+  L.slots = take(sizeof(Slot) * (size_t)nt);
+  L.total = o;
+  return L;
+}
+
+struct RSmem {
+  uint32_t* keys;   // key within the bucket (or window)
+  uint64_t* vals;   // raw value bits (float32 in the low half)
+  uint32_t* pos;    // stream position (last-write mode, or when the map is kept)
+  uint16_t* perm;   // sorted order
+  uint32_t* orig;   // index of the record in its bucket (window mode, explicit seq)
+  uint32_t* sub_a;
+  uint32_t* sub_b;
+  Slot* slots;
 };
 
 struct BlockShared {
   uint32_t buf[32];
   uint32_t tot;
-  uint32_t ticket;
+  uint32_t ticket, next;
+  int32_t emax;
   int64_t excl;
-  uint32_t taken, cum;
-  int32_t wmode;
-  uint32_t n_w;
-  unsigned long long red_u64[32];
-  uint32_t red_u32[32];
-  double red_f64[32];
+  uint32_t taken, cum, n_w;
+  int32_t red_i[32];
 };
 
 // Wait (bounded) for the look-back chain of bucket b to provide its exclusive
@@ -820,158 +986,241 @@ __device__ int64_t lookback(const Ctx& c, int64_t b, uint32_t nnz) {
   return excl;
 }
 
-template <bool F64>
-__device__ __forceinline__ double widen_raw(uint64_t bits) {
-  if (F64) return __longlong_as_double((long long)bits);
-  return (double)__uint_as_float((uint32_t)bits);
+__device__ __forceinline__ uint64_t f32_bits_to_f64_bits(uint64_t v) {
+  return (uint64_t)__double_as_longlong((double)__uint_as_float((uint32_t)v));
 }
 
-// Process the `n` records in shared memory that fall in keys [klo, klo+span)
-// of matrix `mm`: sort, resolve, count; then either look back (bucket mode)
-// or use `base_in` (window mode) as the matrix-relative output position of
-// the first element; write values, row indices, column offsets and the map.
-// Returns the number of stored elements.
-template <bool F64, bool SUM, bool SEQ>
+__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
+  if (bytes >= 16) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes & ~15u) : "memory");
+}
+
+__device__ __forceinline__ int block_max_int(int v, BlockShared& B) {
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0) B.red_i[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    int x = threadIdx.x < (blockDim.x >> 5) ? B.red_i[threadIdx.x] : INT_MIN;
+    for (int o = 16; o > 0; o >>= 1) x = max(x, __shfl_xor_sync(0xffffffffu, x, o));
+    if (threadIdx.x == 0) B.red_i[0] = x;
+  }
+  __syncthreads();
+  const int r = B.red_i[0];
+  __syncthreads();
+  return r;
+}
+
+// Reduction state of one run (equal keys): add mode sums exactly, last-write
+// mode keeps the write with the largest (seq, position).
+template <bool F64, bool SUM, bool SEQ, bool POS>
+struct Red {
+  Acc acc;
+  uint64_t seq;
+  uint32_t pos, idx;  // idx = ~0u: no write
+
+  __device__ __forceinline__ void clear() {
+    if (SUM) acc = acc_zero();
+    else { seq = 0; pos = 0; idx = ~0u; }
+  }
+  __device__ __forceinline__ bool better(uint64_t s2, uint32_t p2) const {
+    return idx == ~0u || s2 > seq || (s2 == seq && p2 > pos);
+  }
+  __device__ __forceinline__ void add(uint32_t k, const RSmem& S, const Ctx& c, int64_t seg_start, int emax) {
+    if (SUM) {
+      const uint64_t v = S.vals[k];
+      acc_add_bits(acc, F64 ? v : f32_bits_to_f64_bits(v), emax);
+    } else {
+      const uint64_t s2 = SEQ ? c.rs[seg_start + (S.orig ? S.orig[k] : k)] : 0ull;
+      const uint32_t p2 = S.pos[k];
+      if (better(s2, p2)) { seq = s2; pos = p2; idx = k; }
+    }
+  }
+  __device__ __forceinline__ void merge(const Slot& o) {
+    if (SUM) {
+      Acc b{o.a, (int64_t)o.b, o.flags};
+      acc_merge(acc, b);
+    } else if (o.flags) {
+      const uint32_t p2 = (uint32_t)o.b, k2 = (uint32_t)(o.b >> 32);
+      if (better(o.a, p2)) { seq = o.a; pos = p2; idx = k2; }
+    }
+  }
+  __device__ __forceinline__ Slot to_slot(uint32_t has_head) const {
+    Slot s;
+    if (SUM) { s.a = acc.lo; s.b = (uint64_t)acc.hi; s.flags = acc.flags; }
+    else { s.a = seq; s.b = (uint64_t)pos | ((uint64_t)idx << 32); s.flags = idx != ~0u ? 1u : 0u; }
+    s.has_head = has_head;
+    return s;
+  }
+  // Final value bits of the element and whether it is stored.
+  __device__ __forceinline__ uint64_t finish(const RSmem& S, int emax, bool& keep) const {
+    if (SUM) return acc_round(acc, emax, !F64, &keep);
+    const uint64_t bits = S.vals[idx];
+    keep = F64 ? (__longlong_as_double((long long)bits) != 0.0) : (__uint_as_float((uint32_t)bits) != 0.0f);
+    return bits;
+  }
+};
+
+// Process the n records in shared memory (keys relative to klo, in
+// [0, span)): sort them by key, reduce each run of equal keys, drop zeros,
+// and write the stored elements, the column offsets of every column that
+// starts inside [klo, klo + span) and the map.  The output position of the
+// first element comes from the look-back (bucket mode) or is base_in
+// (window mode).  Returns the number of stored elements.
+template <bool F64, bool SUM, bool SEQ, bool POS>
 __device__ uint32_t resolve_records(const Ctx& c, const MatMeta& mm, int64_t b, uint64_t klo, uint64_t span,
-                                    uint32_t n, const ResolveSmem& S, BlockShared& B, bool window, int64_t base_in,
-                                    int64_t seg_start) {
+                                    uint32_t n, const RSmem& S, BlockShared& B, bool window, int64_t base_in,
+                                    int64_t seg_start, int emax) {
   using VT = typename std::conditional<F64, uint64_t, uint32_t>::type;
-  const VT* rv_s = reinterpret_cast<const VT*>(S.rv);
+  using R = Red<F64, SUM, SEQ, POS>;
   const int tid = threadIdx.x, NT = blockDim.x;
-  const int sbits_max = c.sub_bits;
+  // ---- counting sort on the top key bits
   const int sbits = span <= 1 ? 0 : ceil_log2_u64(span);
-  const int sshift = sbits > sbits_max ? sbits - sbits_max : 0;
+  const int sshift = sbits > c.sub_bits ? sbits - c.sub_bits : 0;
   const uint32_t nsub = (uint32_t)(((span - 1) >> sshift) + 1);
-  for (uint32_t s = tid; s <= nsub; s += NT) S.sub_a[s] = 0u;
+  for (uint32_t q = tid; q <= nsub; q += NT) S.sub_a[q] = 0u;
   __syncthreads();
-  for (uint32_t k = tid; k < n; k += NT) atomicAdd(&S.sub_a[(uint32_t)(S.rk[k] >> 32) >> sshift], 1u);
+  for (uint32_t k = tid; k < n; k += NT) atomicAdd(&S.sub_a[S.keys[k] >> sshift], 1u);
   __syncthreads();
-  // exclusive scan of the sub-bin counts
   {
     const uint32_t per = (nsub + NT - 1) / NT;
     const uint32_t a = min(nsub, (uint32_t)tid * per), e = min(nsub, a + per);
     uint32_t local = 0;
-    for (uint32_t s = a; s < e; ++s) local += S.sub_a[s];
+    for (uint32_t q = a; q < e; ++q) local += S.sub_a[q];
     uint32_t run = block_scan_excl<uint32_t>(local, &B.tot, B.buf);
-    for (uint32_t s = a; s < e; ++s) {
-      const uint32_t x = S.sub_a[s];
-      S.sub_a[s] = run;
-      S.sub_b[s] = run;
+    for (uint32_t q = a; q < e; ++q) {
+      const uint32_t x = S.sub_a[q];
+      S.sub_a[q] = run;
+      S.sub_b[q] = run;
       run += x;
     }
     if (tid == 0) S.sub_a[nsub] = n;
   }
   __syncthreads();
-  for (uint32_t k = tid; k < n; k += NT) {
-    const uint32_t p = atomicAdd(&S.sub_b[(uint32_t)(S.rk[k] >> 32) >> sshift], 1u);
-    S.perm[p] = (uint16_t)k;
-  }
+  for (uint32_t k = tid; k < n; k += NT) S.perm[atomicAdd(&S.sub_b[S.keys[k] >> sshift], 1u)] = (uint16_t)k;
   __syncthreads();
-  // this thread's sub-bins and key range
-  const uint32_t sa = (uint32_t)(((uint64_t)tid * nsub) / NT), sb = (uint32_t)(((uint64_t)(tid + 1) * nsub) / NT);
-  const uint32_t ea = S.sub_a[sa], eb = S.sub_a[sb];
-  const uint64_t kend = klo + span;
-  const uint64_t kt_lo = min(klo + ((uint64_t)sa << sshift), kend);
-  const uint64_t kt_hi = min(klo + ((uint64_t)sb << sshift), kend);
-  auto seq_of = [&](uint32_t k) -> uint64_t { return c.rs[seg_start + (S.orig ? S.orig[k] : k)]; };
-  auto less = [&](uint32_t x, uint32_t y) -> bool {
-    const uint64_t rx = S.rk[x], ry = S.rk[y];
-    if (!SEQ) return rx < ry;
-    const uint32_t lx = (uint32_t)(rx >> 32), ly = (uint32_t)(ry >> 32);
-    if (lx != ly) return lx < ly;
-    const uint64_t qx = seq_of(x), qy = seq_of(y);
-    if (qx != qy) return qx < qy;
-    return (uint32_t)rx < (uint32_t)ry;
-  };
-  // insertion sort of this thread's range (already grouped by sub-bin)
-  for (uint32_t x = ea + 1; x < eb; ++x) {
-    const uint16_t v = S.perm[x];
-    uint32_t y = x;
-    while (y > ea && less(v, S.perm[y - 1])) {
-      S.perm[y] = S.perm[y - 1];
-      --y;
-    }
-    S.perm[y] = v;
-  }
-  // resolve one run [p, q) of equal keys: value bits and whether it is kept
-  auto resolve_run = [&](uint32_t p, uint32_t q, uint64_t& bits) -> bool {
-    if (SUM) {
-      double acc = widen_raw<F64>((uint64_t)rv_s[S.perm[p]]);
-      for (uint32_t x = p + 1; x < q; ++x) acc += widen_raw<F64>((uint64_t)rv_s[S.perm[x]]);
-      if (F64) {
-        bits = (uint64_t)__double_as_longlong(acc);
-        return acc != 0.0;
+  if (sshift > 0) {  // sub-bins hold several keys: order them by key
+    const uint32_t sa = (uint32_t)(((uint64_t)tid * nsub) / NT), sb = (uint32_t)(((uint64_t)(tid + 1) * nsub) / NT);
+    const uint32_t ea = S.sub_a[sa], eb = S.sub_a[sb];
+    for (uint32_t x = ea + 1; x < eb; ++x) {
+      const uint16_t v = S.perm[x];
+      const uint32_t kv = S.keys[v];
+      uint32_t y = x;
+      while (y > ea && S.keys[S.perm[y - 1]] > kv) {
+        S.perm[y] = S.perm[y - 1];
+        --y;
       }
-      const float f = __double2float_rn(acc);
-      bits = (uint64_t)__float_as_uint(f);
-      return f != 0.0f;
-    } else {
-      bits = (uint64_t)rv_s[S.perm[q - 1]];
-      if (F64) return __longlong_as_double((long long)bits) != 0.0;
-      return __uint_as_float((uint32_t)bits) != 0.0f;
+      S.perm[y] = v;
     }
-  };
-  auto run_end = [&](uint32_t p) -> uint32_t {
-    const uint32_t key = (uint32_t)(S.rk[S.perm[p]] >> 32);
-    uint32_t q = p + 1;
-    while (q < eb && (uint32_t)(S.rk[S.perm[q]] >> 32) == key) ++q;
-    return q;
-  };
-  // phase 1: count kept elements
+    __syncthreads();
+  }
+  // ---- balanced ranges of sorted positions; runs may cross range boundaries
+  const uint32_t E = (n + NT - 1) / NT;
+  const uint32_t p0 = min(n, (uint32_t)tid * E), p1 = min(n, p0 + E);
+  auto key_at = [&](uint32_t p) -> uint32_t { return S.keys[S.perm[p]]; };
+  auto is_head = [&](uint32_t p) -> bool { return p == 0 || key_at(p) != key_at(p - 1); };
+  R first, cur;
+  first.clear();
+  cur.clear();
+  bool owned = false, seen = false;
   uint32_t kept = 0;
-  for (uint32_t p = ea; p < eb;) {
-    const uint32_t q = run_end(p);
-    uint64_t bits;
-    if (resolve_run(p, q, bits)) ++kept;
-    p = q;
+  for (uint32_t p = p0; p < p1; ++p) {
+    if (is_head(p)) {
+      if (owned) {
+        bool k2;
+        cur.finish(S, emax, k2);
+        kept += k2 ? 1u : 0u;
+      } else if (p > p0) {
+        first = cur;
+      }
+      cur.clear();
+      owned = seen = true;
+    }
+    cur.add(S.perm[p], S, c, seg_start, emax);
   }
-  uint32_t nnz;
+  if (!seen) first = cur;
+  S.slots[tid] = first.to_slot((seen || p0 >= n) ? 1u : 0u);
+  __syncthreads();
+  uint64_t open_bits = 0;
+  bool open_keep = false;
+  uint32_t open_win = ~0u;
+  if (seen) {  // the last run starting here may continue into the following ranges
+    for (int t2 = tid + 1; t2 < NT; ++t2) {
+      const Slot sl = S.slots[t2];
+      cur.merge(sl);
+      if (sl.has_head) break;
+    }
+    open_bits = cur.finish(S, emax, open_keep);
+    open_win = cur.idx;
+    kept += open_keep ? 1u : 0u;
+  }
   const uint32_t off = block_scan_excl<uint32_t>(kept, &B.tot, B.buf);
-  nnz = B.tot;
-  if (tid == 0) B.excl = window ? base_in : ((klo == 0) ? 0 : -1);
-  __syncthreads();
-  if (!window && tid == 0) {
-    if (b == c.withhold) B.excl = 0;  // fault injection: publish nothing, wait for nothing
-    else if (klo == 0) st_release_u64(&c.bk_state[b], kStIncl | (uint64_t)nnz);
-    else B.excl = lookback(c, b, nnz);
+  const uint32_t nnz = B.tot;
+  if (tid == 0) {
+    if (window) B.excl = base_in;
+    else if (b == c.withhold) B.excl = 0;  // fault injection: publish nothing, wait for nothing
+    else if (klo == 0) {
+      st_release_u64(&c.bk_state[b], kStIncl | (uint64_t)nnz);
+      B.excl = 0;
+    } else {
+      B.excl = lookback(c, b, nnz);
+    }
   }
   __syncthreads();
-  // phase 2: write
-  const int64_t excl = B.excl;
-  int64_t idx = excl + off;
+  // ---- write, walking the runs this thread owns (those starting in its range)
+  int64_t idx = B.excl + off;
   const uint64_t nr = (uint64_t)mm.n_rows;
-  uint64_t j = (kt_lo + nr - 1) / nr;  // first column whose start key is in this thread's range
+  auto range_start = [&](uint32_t p) -> uint64_t {  // first key owned by the range starting at p
+    if (p >= n) return span;
+    return (uint64_t)key_at(p) + (is_head(p) ? 0u : 1u);
+  };
+  const uint64_t gstart = klo + (tid == 0 ? 0ull : range_start(p0));
+  const uint64_t gend = klo + range_start(p1);
+  uint64_t j = (gstart + nr - 1) / nr;  // first column whose start key lies in this thread's range
   uint64_t next_start = j * nr;
   int64_t* colp = c.col_ptr + mm.col_base;
   int32_t* rowp = c.row_idx + mm.t0;
   VT* outp = reinterpret_cast<VT*>(c.out_vals) + mm.t0;
-  for (uint32_t p = ea; p < eb;) {
-    const uint32_t q = run_end(p);
-    uint64_t bits;
-    const bool keep = resolve_run(p, q, bits);
-    const uint64_t key = klo + (S.rk[S.perm[p]] >> 32);
-    int64_t slot = -2;
+  auto emit = [&](uint32_t hp, uint32_t end_p, uint64_t bits, bool keep, uint32_t win) {
+    const uint64_t key = klo + key_at(hp);
+    int32_t slot = -2;
     if (keep) {
       while (next_start <= key) {
         colp[j] = idx;
         ++j;
         next_start += nr;
       }
-      const uint64_t col = j - 1;
-      rowp[idx] = (int32_t)(key - col * nr);
+      rowp[idx] = (int32_t)(key - (j - 1) * nr);
       outp[idx] = (VT)bits;
-      slot = idx;
+      slot = (int32_t)idx;
       ++idx;
     }
-    if (c.keep_map) {
-      for (uint32_t x = p; x < q; ++x) {
-        const uint32_t pos = (uint32_t)S.rk[S.perm[x]];
-        c.map[pos] = (!SUM && x != q - 1) ? -1 : (int32_t)slot;
+    if (c.keep_map && POS) {
+      for (uint32_t x = hp; x < end_p; ++x) {
+        const uint32_t k = S.perm[x];
+        c.map[S.pos[k]] = (!SUM && k != win) ? -1 : slot;
       }
     }
-    p = q;
+  };
+  owned = false;
+  uint32_t hp = 0;
+  for (uint32_t p = p0; p < p1; ++p) {
+    if (is_head(p)) {
+      if (owned) {
+        bool k2;
+        const uint64_t bits = cur.finish(S, emax, k2);
+        emit(hp, p, bits, k2, cur.idx);
+      }
+      cur.clear();
+      owned = true;
+      hp = p;
+    }
+    if (owned) cur.add(S.perm[p], S, c, seg_start, emax);
   }
-  while (next_start < kt_hi) {
+  if (owned) {
+    uint32_t end_p = p1;
+    if (c.keep_map) while (end_p < n && !is_head(end_p)) ++end_p;
+    emit(hp, end_p, open_bits, open_keep, open_win);
+  }
+  while (next_start < gend) {
     colp[j] = idx;
     ++j;
     next_start += nr;
@@ -980,96 +1229,61 @@ __device__ uint32_t resolve_records(const Ctx& c, const MatMeta& mm, int64_t b, 
   return nnz;
 }
 
-// A single key with more writes than fit in shared memory: streaming reduction.
-template <bool F64, bool SUM, bool SEQ>
+// A single key with more writes than fit in shared memory: streaming
+// reduction over its records in global memory.
+template <bool F64, bool SUM, bool SEQ, bool POS>
 __device__ uint32_t resolve_single_key(const Ctx& c, const MatMeta& mm, uint64_t key, uint32_t lkey, int64_t start,
-                                       uint32_t n, BlockShared& B, int64_t base) {
+                                       uint32_t n, const RSmem& S, BlockShared& B, int64_t base) {
   using VT = typename std::conditional<F64, uint64_t, uint32_t>::type;
-  const VT* rv = reinterpret_cast<const VT*>(c.rv);
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-  // last write: the largest (seq, position); sum: per-thread partial sums combined in thread order
-  unsigned long long best_seq = 0;
-  uint32_t best_pos = 0;
-  int64_t best_k = -1;
-  double acc = 0.0;
-  for (int64_t k = tid; k < n; k += blockDim.x) {
-    const uint64_t r = c.rk[start + k];
-    if ((uint32_t)(r >> 32) != lkey) continue;
-    if (SUM) {
-      acc += widen_raw<F64>((uint64_t)rv[start + k]);
-    } else {
-      const unsigned long long sq = SEQ ? c.rs[start + k] : 0ull;
-      const uint32_t pos = (uint32_t)r;
-      if (best_k < 0 || sq > best_seq || (sq == best_seq && pos > best_pos)) {
-        best_seq = sq;
-        best_pos = pos;
-        best_k = k;
-      }
-    }
-  }
-  uint64_t bits = 0;
-  bool keep;
-  int64_t win_k = -1;
+  using R = Red<F64, SUM, SEQ, POS>;
+  const int tid = threadIdx.x, NT = blockDim.x;
+  const uint4* recs = reinterpret_cast<const uint4*>(c.rec + start);
+  auto val_of = [&](const uint4& r) -> uint64_t {
+    const uint64_t v = ((uint64_t)r.w << 32) | r.z;
+    return F64 ? v : f32_bits_to_f64_bits(v);
+  };
+  int emax = 1;
   if (SUM) {
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-    if (lane == 0) B.red_f64[warp] = acc;
-    __syncthreads();
-    if (tid == 0) {
-      double s = 0.0;
-      for (int w = 0; w < nw; ++w) s += B.red_f64[w];
-      B.red_f64[0] = s;
+    int el = 0;
+    for (uint32_t k = tid; k < n; k += NT) {
+      const uint4 r = recs[k];
+      if (r.x == lkey) el = max(el, f64_align_exponent(val_of(r)));
     }
-    __syncthreads();
-    const double s = B.red_f64[0];
-    if (F64) {
-      bits = (uint64_t)__double_as_longlong(s);
-      keep = s != 0.0;
-    } else {
-      const float f = __double2float_rn(s);
-      bits = __float_as_uint(f);
-      keep = f != 0.0f;
-    }
-    __syncthreads();
-  } else {
-    // arg-max of (seq, pos) over the block
-    for (int o = 16; o > 0; o >>= 1) {
-      const unsigned long long s2 = __shfl_down_sync(0xffffffffu, best_seq, o);
-      const uint32_t p2 = __shfl_down_sync(0xffffffffu, best_pos, o);
-      const long long k2 = __shfl_down_sync(0xffffffffu, (long long)best_k, o);
-      if (k2 >= 0 && (best_k < 0 || s2 > best_seq || (s2 == best_seq && p2 > best_pos))) {
-        best_seq = s2;
-        best_pos = p2;
-        best_k = k2;
-      }
-    }
-    if (lane == 0) {
-      B.red_u64[warp] = best_seq;
-      B.red_u32[warp] = best_pos;
-      B.red_f64[warp] = __longlong_as_double(best_k);
-    }
-    __syncthreads();
-    if (tid == 0) {
-      long long bk = -1;
-      unsigned long long bs = 0;
-      uint32_t bp = 0;
-      for (int w = 0; w < nw; ++w) {
-        const long long k2 = __double_as_longlong(B.red_f64[w]);
-        if (k2 >= 0 && (bk < 0 || B.red_u64[w] > bs || (B.red_u64[w] == bs && B.red_u32[w] > bp))) {
-          bk = k2;
-          bs = B.red_u64[w];
-          bp = B.red_u32[w];
-        }
-      }
-      B.red_f64[0] = __longlong_as_double(bk);
-    }
-    __syncthreads();
-    win_k = __double_as_longlong(B.red_f64[0]);
-    bits = (uint64_t)rv[start + win_k];
-    keep = F64 ? (__longlong_as_double((long long)bits) != 0.0) : (__uint_as_float((uint32_t)bits) != 0.0f);
-    __syncthreads();
+    emax = max(1, block_max_int(el, B));
   }
-  const uint64_t nr = (uint64_t)mm.n_rows;
+  R st;
+  st.clear();
+  for (uint32_t k = tid; k < n; k += NT) {
+    const uint4 r = recs[k];
+    if (r.x != lkey) continue;
+    if (SUM) {
+      acc_add_bits(st.acc, val_of(r), emax);
+    } else {
+      const uint64_t s2 = SEQ ? c.rs[start + k] : 0ull;
+      if (st.better(s2, r.y)) { st.seq = s2; st.pos = r.y; st.idx = k; }
+    }
+  }
+  S.slots[tid] = st.to_slot(0u);
+  __syncthreads();
+  __shared__ uint64_t s_bits;
+  __shared__ uint32_t s_keep, s_win;
   if (tid == 0) {
+    R all;
+    all.clear();
+    for (int t2 = 0; t2 < NT; ++t2) all.merge(S.slots[t2]);
+    bool keep;
+    uint64_t bits;
+    if (SUM) {
+      bits = acc_round(all.acc, emax, !F64, &keep);
+    } else {
+      const uint4 r = recs[all.idx];
+      bits = ((uint64_t)r.w << 32) | r.z;
+      keep = F64 ? (__longlong_as_double((long long)bits) != 0.0) : (__uint_as_float((uint32_t)bits) != 0.0f);
+    }
+    s_bits = bits;
+    s_keep = keep ? 1u : 0u;
+    s_win = all.idx;
+    const uint64_t nr = (uint64_t)mm.n_rows;
     const uint64_t col = key / nr;
     if (col * nr == key) c.col_ptr[mm.col_base + col] = base;
     if (keep) {
@@ -1077,35 +1291,50 @@ __device__ uint32_t resolve_single_key(const Ctx& c, const MatMeta& mm, uint64_t
       reinterpret_cast<VT*>(c.out_vals)[mm.t0 + base] = (VT)bits;
     }
   }
+  __syncthreads();
+  const bool keep = s_keep != 0;
   if (c.keep_map) {
-    for (int64_t k = tid; k < n; k += blockDim.x) {
-      const uint64_t r = c.rk[start + k];
-      if ((uint32_t)(r >> 32) != lkey) continue;
-      c.map[(uint32_t)r] = (!SUM && k != win_k) ? -1 : (keep ? (int32_t)base : -2);
+    for (uint32_t k = tid; k < n; k += NT) {
+      const uint4 r = recs[k];
+      if (r.x != lkey) continue;
+      c.map[r.y] = (!SUM && k != s_win) ? -1 : (keep ? (int32_t)base : -2);
     }
   }
   __syncthreads();
   return keep ? 1u : 0u;
 }
 
-template <bool F64, bool SUM, bool SEQ>
-__global__ void __launch_bounds__(512) k_resolve(Ctx c) {
+template <bool F64, bool SUM, bool SEQ, bool POS>
+__global__ void __launch_bounds__(1024) k_resolve(Ctx c) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ BlockShared B;
   __shared__ MatMeta mm;
-  using VT = typename std::conditional<F64, uint64_t, uint32_t>::type;
-  ResolveSmem S;
-  S.rk = reinterpret_cast<uint64_t*>(smraw);
-  S.rv = smraw + (size_t)kCap * 8;
-  S.perm = reinterpret_cast<uint16_t*>(smraw + (size_t)kCap * (8 + sizeof(VT)));
-  S.sub_a = reinterpret_cast<uint32_t*>(smraw + (size_t)kCap * (10 + sizeof(VT)));
-  S.sub_b = S.sub_a + (1 << c.sub_bits) + 4;
-  uint32_t* orig_store = S.sub_b + (1 << c.sub_bits);  // [kCap], used in window mode
-  const VT* rvg = reinterpret_cast<const VT*>(c.rv);
   const int tid = threadIdx.x, NT = blockDim.x;
+  const RLayout RL = resolve_layout(c.cap, POS, SEQ, NT, c.sub_bits);
+  RSmem S;
+  S.keys = reinterpret_cast<uint32_t*>(smraw + RL.keys);
+  S.vals = reinterpret_cast<uint64_t*>(smraw + RL.vals);
+  S.pos = reinterpret_cast<uint32_t*>(smraw + RL.pos);
+  S.perm = reinterpret_cast<uint16_t*>(smraw + RL.perm);
+  S.orig = nullptr;
+  S.sub_a = reinterpret_cast<uint32_t*>(smraw + RL.sub_a);
+  S.sub_b = reinterpret_cast<uint32_t*>(smraw + RL.sub_b);
+  S.slots = reinterpret_cast<Slot*>(smraw + RL.slots);
+  uint32_t* orig_store = reinterpret_cast<uint32_t*>(smraw + RL.orig);
   const uint32_t NB = c.scal->NB;
+  const uint32_t cap = (uint32_t)c.cap;
+  if (tid == 0) B.next = is_aborted(c) ? ~0u : atomicAdd(&c.scal->ticket, 1u);
+  __syncthreads();
   while (true) {
-    if (tid == 0) B.ticket = is_aborted(c) ? 0xffffffffu : atomicAdd(&c.scal->ticket, 1u);
+    if (tid == 0) {
+      // hold the next bucket's ticket too, and warm L2 with its records
+      B.ticket = B.next;
+      B.next = (B.ticket < NB && !is_aborted(c)) ? atomicAdd(&c.scal->ticket, 1u) : ~0u;
+      if (B.next < NB) {
+        const uint32_t nn = c.bk_count[B.next];
+        if (nn <= cap) prefetch_l2(c.rec + c.bk_start[B.next], nn * 16u);
+      }
+    }
     __syncthreads();
     const uint32_t b = B.ticket;
     if (b >= NB) break;
@@ -1127,24 +1356,31 @@ __global__ void __launch_bounds__(512) k_resolve(Ctx c) {
     const uint64_t span = min(uint64_t{1} << w, mm.K - klo);
     const int64_t start = c.bk_start[b];
     const uint32_t n = c.bk_count[b];
+    const uint4* recs = reinterpret_cast<const uint4*>(c.rec + start);
     int64_t total;
-    if (n <= (uint32_t)kCap) {
+    if (n <= cap) {
+      int el = 0;
       for (uint32_t k = tid; k < n; k += NT) {
-        S.rk[k] = c.rk[start + k];
-        reinterpret_cast<VT*>(S.rv)[k] = rvg[start + k];
+        const uint4 r = __ldcg(recs + k);
+        S.keys[k] = r.x;
+        if (POS) S.pos[k] = r.y;
+        const uint64_t v = ((uint64_t)r.w << 32) | r.z;
+        S.vals[k] = v;
+        if (SUM) el = max(el, f64_align_exponent(F64 ? v : f32_bits_to_f64_bits(v)));
       }
       S.orig = nullptr;
+      const int emax = SUM ? max(1, block_max_int(el, B)) : 1;
       __syncthreads();
-      const uint32_t nnz = resolve_records<F64, SUM, SEQ>(c, mm, b, klo, span, n, S, B, false, 0, start);
+      const uint32_t nnz = resolve_records<F64, SUM, SEQ, POS>(c, mm, b, klo, span, n, S, B, false, 0, start, emax);
       total = B.excl + nnz;
     } else {
       // more writes than fit: windows of the key range, each sorted in shared memory
-      if (tid == 0) B.excl = (klo == 0) ? 0 : lookback_wait(c, b);
+      if (tid == 0) B.excl = (klo == 0 || b == c.withhold) ? 0 : lookback_wait(c, b);
       __syncthreads();
       int64_t base = B.excl;
       __syncthreads();
       uint64_t wlo = 0;
-      S.orig = orig_store;
+      S.orig = SEQ ? orig_store : nullptr;
       while (wlo < span) {
         int hs = (span - wlo <= 1) ? 0 : max(0, ceil_log2_u64(span - wlo) - c.sub_bits);
         uint64_t wend = span;
@@ -1152,16 +1388,16 @@ __global__ void __launch_bounds__(512) k_resolve(Ctx c) {
         int mode = 0;  // 1 = window, 2 = single key
         while (true) {
           const uint32_t nbins = (uint32_t)(((wend - wlo - 1) >> hs) + 1);
-          for (uint32_t s = tid; s < nbins; s += NT) S.sub_a[s] = 0u;
+          for (uint32_t q = tid; q < nbins; q += NT) S.sub_a[q] = 0u;
           __syncthreads();
           for (uint32_t k = tid; k < n; k += NT) {
-            const uint64_t l = c.rk[start + k] >> 32;
+            const uint64_t l = recs[k].x;
             if (l >= wlo && l < wend) atomicAdd(&S.sub_a[(uint32_t)((l - wlo) >> hs)], 1u);
           }
           __syncthreads();
           if (tid == 0) {
             uint32_t cum = 0, taken = 0;
-            while (taken < nbins && cum + S.sub_a[taken] <= (uint32_t)kCap) cum += S.sub_a[taken++];
+            while (taken < nbins && cum + S.sub_a[taken] <= cap) cum += S.sub_a[taken++];
             B.taken = taken;
             B.cum = cum;
           }
@@ -1182,29 +1418,35 @@ __global__ void __launch_bounds__(512) k_resolve(Ctx c) {
         if (mode == 1) {
           if (tid == 0) B.n_w = 0;
           __syncthreads();
+          int el = 0;
           for (uint32_t k = tid; k < n; k += NT) {
-            const uint64_t r = c.rk[start + k];
-            const uint64_t l = r >> 32;
+            const uint4 r = recs[k];
+            const uint64_t l = r.x;
             if (l >= wlo && l < whi) {
               const uint32_t q = atomicAdd(&B.n_w, 1u);
-              S.rk[q] = ((l - wlo) << 32) | (uint32_t)r;
-              reinterpret_cast<VT*>(S.rv)[q] = rvg[start + k];
-              S.orig[q] = k;
+              S.keys[q] = (uint32_t)(l - wlo);
+              if (POS) S.pos[q] = r.y;
+              const uint64_t v = ((uint64_t)r.w << 32) | r.z;
+              S.vals[q] = v;
+              if (SEQ) S.orig[q] = k;
+              if (SUM) el = max(el, f64_align_exponent(F64 ? v : f32_bits_to_f64_bits(v)));
             }
           }
+          const int emax = SUM ? max(1, block_max_int(el, B)) : 1;
           __syncthreads();
           const uint32_t nw = B.n_w;
-          base += resolve_records<F64, SUM, SEQ>(c, mm, b, klo + wlo, whi - wlo, nw, S, B, true, base, start);
+          base += resolve_records<F64, SUM, SEQ, POS>(c, mm, b, klo + wlo, whi - wlo, nw, S, B, true, base, start,
+                                                      emax);
           wlo = whi;
         } else {
-          base += resolve_single_key<F64, SUM, SEQ>(c, mm, klo + wlo, (uint32_t)wlo, start, n, B, base);
+          base += resolve_single_key<F64, SUM, SEQ, POS>(c, mm, klo + wlo, (uint32_t)wlo, start, n, S, B, base);
           wlo = wlo + 1;
         }
         __syncthreads();
       }
       total = base;
       // the inclusive value of a bucket is the matrix-relative end of its output
-      if (tid == 0) st_release_u64(&c.bk_state[b], kStIncl | (uint64_t)total);
+      if (tid == 0 && b != c.withhold) st_release_u64(&c.bk_state[b], kStIncl | (uint64_t)total);
     }
     if (tid == 0 && klo + span == mm.K) {
       c.col_ptr[mm.col_base + mm.n_cols] = total;
@@ -1219,7 +1461,7 @@ __global__ void __launch_bounds__(512) k_resolve(Ctx c) {
 // ===========================================================================
 namespace {
 
-spm_tuning g_tuning = {4096, 12, 1024, 512};
+spm_tuning g_tuning = {6144, 11, 1024, 1024};
 int64_t g_withhold = -1;
 std::mutex g_mutex;
 
@@ -1249,9 +1491,28 @@ DevState g_dev[64];
 constexpr size_t kAlign = 256;
 size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 
-size_t resolve_smem_bytes(int sv, int sub_bits) {
-  return (size_t)kCap * (8 + sv + 2) + ((size_t)(1 << sub_bits) + 4) * 4 + ((size_t)1 << sub_bits) * 4 +
-         (size_t)kCap * 4;
+// Per-mode parameters: whether the resolve kernel keeps stream positions
+// (last-write mode, or the map) and seq (last-write mode with seq), the
+// bucket capacity those choices leave in shared memory, and the planner's
+// target scaled to it.
+struct ModeParams {
+  bool pos, seq;
+  int cap;
+  int64_t tgt;
+};
+
+ModeParams mode_params(spm_mode mode, uint32_t flags, const spm_tuning& tun) {
+  ModeParams p;
+  const bool sum = mode == SPM_MODE_SUM;
+  p.pos = !sum || (flags & SPM_KEEP_MAP) != 0;
+  p.seq = !sum && (flags & SPM_SEQ_EXPLICIT) != 0;
+  p.cap = !p.pos ? kCapSum : (p.seq ? 7680 : kCapSet);
+  p.tgt = std::max<int64_t>(256, (int64_t)tun.bucket_target * p.cap / kCapSum);
+  return p;
+}
+
+size_t resolve_smem_bytes(const ModeParams& mp, int threads, int sub_bits) {
+  return resolve_layout(mp.cap, mp.pos, mp.seq, threads, sub_bits).total;
 }
 
 size_t partition_smem_bytes() { return (size_t)(kHistCapSmem + kLutCapSmem) * 4; }
@@ -1284,15 +1545,21 @@ spm_status device_init(int& dev, DevState*& ds) {
   SPM_SET_SCATTER(true, false)
   SPM_SET_SCATTER(true, true)
 #undef SPM_SET_SCATTER
-  const size_t r4 = resolve_smem_bytes(4, 12), r8 = resolve_smem_bytes(8, 12);
-  set_smem_attr(k_resolve<false, false, false>, r4);
-  set_smem_attr(k_resolve<false, false, true>, r4);
-  set_smem_attr(k_resolve<false, true, false>, r4);
-  set_smem_attr(k_resolve<false, true, true>, r4);
-  set_smem_attr(k_resolve<true, false, false>, r8);
-  set_smem_attr(k_resolve<true, false, true>, r8);
-  set_smem_attr(k_resolve<true, true, false>, r8);
-  set_smem_attr(k_resolve<true, true, true>, r8);
+  {
+    // the largest layout of each instantiation (1024 threads, the widest digit)
+    const size_t r_sum = resolve_layout(kCapSum, false, false, 1024, kSubBitsMax).total;
+    const size_t r_pos = resolve_layout(kCapSet, true, false, 1024, kSubBitsMax).total;
+    const size_t r_seq = resolve_layout(7680, true, true, 1024, kSubBitsMax).total;
+    set_smem_attr(k_resolve<false, true, false, false>, r_sum);
+    set_smem_attr(k_resolve<true, true, false, false>, r_sum);
+    set_smem_attr(k_resolve<false, true, false, true>, r_pos);
+    set_smem_attr(k_resolve<true, true, false, true>, r_pos);
+    set_smem_attr(k_resolve<false, false, false, true>, r_pos);
+    set_smem_attr(k_resolve<true, false, false, true>, r_pos);
+    set_smem_attr(k_resolve<false, false, true, true>, r_seq);
+    set_smem_attr(k_resolve<true, false, true, true>, r_seq);
+    set_smem_attr(k_plan, kPlanSmem);
+  }
   if (cudaGetLastError() != cudaSuccess) return SPM_ERR_CUDA;
   ds->sms = sms;
   ds->init = true;
@@ -1339,6 +1606,7 @@ spm_status host_plan(int64_t B, const int64_t* h_nr, const int64_t* h_nc, const 
     const Derived d = derive(nr, nc, m, m_total, tgt);
     if (d.bbits > kMaxKeyBits) return SPM_ERR_UNSUPPORTED;
     if (d.nbcap >= (int64_t{1} << kBaseBits)) return SPM_ERR_UNSUPPORTED;
+    if (C > kMaxCtas) return SPM_ERR_UNSUPPORTED;
     if (B == 1) {
       MatMeta& mm = hp.single;
       memset(&mm, 0, sizeof(mm));
@@ -1404,8 +1672,7 @@ spm_status host_plan(int64_t B, const int64_t* h_nr, const int64_t* h_nc, const 
   L.bk_state = take(8 * (size_t)std::max<int64_t>(nbcap, 1));
   L.scanpart = take(4 * (size_t)std::max<int64_t>(L.scan_blocks, 1));
   L.hist = take(4 * (size_t)std::max<int64_t>(hist, 1));
-  L.rk = take(8 * (size_t)(m_total + 4));
-  L.rv = take((size_t)sv * (size_t)(m_total + 4));
+  L.rec = take(sizeof(Rec) * (size_t)(m_total + 4));
   L.rs = seq ? take(8 * (size_t)(m_total + 4)) : o;
   L.total = o;
   return SPM_OK;
@@ -1436,16 +1703,16 @@ void launch_partition(const Ctx& ctx, const Layout& L, bool vec, cudaStream_t st
   stage_mark(st, call, 4);
 }
 
-void launch_resolve(const Ctx& ctx, int sms, cudaStream_t st, int threads) {
-  const size_t rs = resolve_smem_bytes(ctx.f64 ? 8 : 4, ctx.sub_bits);
+void launch_resolve(const Ctx& ctx, const ModeParams& mp, int sms, cudaStream_t st, int threads) {
+  const size_t rs = resolve_smem_bytes(mp, threads, ctx.sub_bits);
   const int grid = sms * (rs <= 110 * 1024 ? 2 : 1);
-#define SPM_RES(F6, SU, SQ) k_resolve<F6, SU, SQ><<<grid, threads, rs, st>>>(ctx)
+#define SPM_RES(F6, SU, SQ, PO) k_resolve<F6, SU, SQ, PO><<<grid, threads, rs, st>>>(ctx)
   if (ctx.f64) {
-    if (ctx.sum_mode) { if (ctx.has_seq) SPM_RES(true, true, true); else SPM_RES(true, true, false); }
-    else { if (ctx.has_seq) SPM_RES(true, false, true); else SPM_RES(true, false, false); }
+    if (ctx.sum_mode) { if (mp.pos) SPM_RES(true, true, false, true); else SPM_RES(true, true, false, false); }
+    else { if (mp.seq) SPM_RES(true, false, true, true); else SPM_RES(true, false, false, true); }
   } else {
-    if (ctx.sum_mode) { if (ctx.has_seq) SPM_RES(false, true, true); else SPM_RES(false, true, false); }
-    else { if (ctx.has_seq) SPM_RES(false, false, true); else SPM_RES(false, false, false); }
+    if (ctx.sum_mode) { if (mp.pos) SPM_RES(false, true, false, true); else SPM_RES(false, true, false, false); }
+    else { if (mp.seq) SPM_RES(false, false, true, true); else SPM_RES(false, false, false, true); }
   }
 #undef SPM_RES
 }
@@ -1475,8 +1742,9 @@ spm_status run_assembly(int64_t B, const int64_t* h_nr, const int64_t* h_nc, con
     withhold = g_withhold;
   }
   const int sv = dtype == SPM_F64 ? 8 : 4;
+  const ModeParams mp = mode_params(mode, flags, tun);
   HostPlan hp;
-  s = host_plan(B, h_nr, h_nc, h_tp, sv, has_seq, tun.bucket_target, ds->sms, hp);
+  s = host_plan(B, h_nr, h_nc, h_tp, sv, mp.seq, mp.tgt, ds->sms, hp);
   if (s != SPM_OK) return s;
   const Layout& L = hp.L;
   if (L.m_total > 0 && (!rows || !cols || !vals || !row_idx || !out_vals)) return SPM_ERR_INVALID_ARG;
@@ -1510,9 +1778,8 @@ spm_status run_assembly(int64_t B, const int64_t* h_nr, const int64_t* h_nc, con
   ctx.bk_state = reinterpret_cast<uint64_t*>(ws + L.bk_state);
   ctx.scanpart = reinterpret_cast<uint32_t*>(ws + L.scanpart);
   ctx.hist = reinterpret_cast<uint32_t*>(ws + L.hist);
-  ctx.rk = reinterpret_cast<uint64_t*>(ws + L.rk);
-  ctx.rv = ws + L.rv;
-  ctx.rs = has_seq ? reinterpret_cast<uint64_t*>(ws + L.rs) : nullptr;
+  ctx.rec = reinterpret_cast<Rec*>(ws + L.rec);
+  ctx.rs = mp.seq ? reinterpret_cast<uint64_t*>(ws + L.rs) : nullptr;
   ctx.B = L.B;
   ctx.m_total = L.m_total;
   ctx.S_total = L.S_total;
@@ -1523,8 +1790,9 @@ spm_status run_assembly(int64_t B, const int64_t* h_nr, const int64_t* h_nc, con
   ctx.sum_mode = mode == SPM_MODE_SUM;
   ctx.f64 = dtype == SPM_F64;
   ctx.keep_map = keep_map;
-  ctx.has_seq = has_seq;
-  ctx.tgt = tun.bucket_target;
+  ctx.has_seq = mp.seq;
+  ctx.tgt = mp.tgt;
+  ctx.cap = mp.cap;
   ctx.sub_bits = tun.sub_bits;
   ctx.withhold = withhold;
 
@@ -1551,7 +1819,7 @@ spm_status run_assembly(int64_t B, const int64_t* h_nr, const int64_t* h_nc, con
                                         ncols_total, h);
   }
   if (L.S_total > 0) k_sample<<<(unsigned)((L.S_total + 255) / 256), 256, 0, st>>>(ctx);
-  k_plan<<<(unsigned)B, 512, 0, st>>>(ctx);
+  k_plan<<<(unsigned)B, 1024, kPlanSmem, st>>>(ctx);
   k_bucket_scan<<<1, 1024, 0, st>>>(ctx);
   k_bucket_fill<<<(unsigned)((L.lut_total * 32 + 255) / 256), 256, 0, st>>>(ctx);
   stage_mark(st, call, 1);
@@ -1560,7 +1828,7 @@ spm_status run_assembly(int64_t B, const int64_t* h_nr, const int64_t* h_nc, con
   const bool batched = B > 1;
   if (batched) launch_partition<true>(ctx, L, vec, st, tun.partition_threads, call);
   else launch_partition<false>(ctx, L, vec, st, tun.partition_threads, call);
-  launch_resolve(ctx, ds->sms, st, tun.resolve_threads);
+  launch_resolve(ctx, mp, ds->sms, st, tun.resolve_threads);
   stage_mark(st, call, 5);
   g_launches += 11 + (L.S_total > 0 ? 1 : 0);  // setup, plan, 2 bucket kernels, 6 partition, resolve
   if (cudaGetLastError() != cudaSuccess) return SPM_ERR_CUDA;
@@ -1595,14 +1863,15 @@ int32_t spm_version(void) { return 10000; }
 spm_status spm_set_tuning(const spm_tuning* t) {
   std::lock_guard<std::mutex> lk(g_mutex);
   if (!t) {
-    g_tuning = spm_tuning{4096, 12, 1024, 512};
+    g_tuning = spm_tuning{6144, 11, 1024, 1024};
     return SPM_OK;
   }
-  if (t->bucket_target < 256 || t->bucket_target > 8192) return SPM_ERR_INVALID_ARG;
-  if (t->sub_bits < 8 || t->sub_bits > 12) return SPM_ERR_INVALID_ARG;
+  if (t->bucket_target < 256 || t->bucket_target > kCapSum) return SPM_ERR_INVALID_ARG;
+  if (t->sub_bits < 8 || t->sub_bits > kSubBitsMax) return SPM_ERR_INVALID_ARG;
   if (t->partition_threads != 256 && t->partition_threads != 512 && t->partition_threads != 1024)
     return SPM_ERR_INVALID_ARG;
-  if (t->resolve_threads != 256 && t->resolve_threads != 512) return SPM_ERR_INVALID_ARG;
+  if (t->resolve_threads != 256 && t->resolve_threads != 512 && t->resolve_threads != 1024)
+    return SPM_ERR_INVALID_ARG;
   g_tuning = *t;
   return SPM_OK;
 }
@@ -1651,7 +1920,6 @@ int64_t spm_debug_launch_count(void) { return g_launches.load(); }
 spm_status spm_debug_plan_stats(const void* workspace, size_t ws_bytes, int64_t n_rows, int64_t n_cols, int64_t m,
                                 spm_dtype dtype, spm_mode mode, uint32_t flags, int64_t* stats, int32_t n_stats) {
   if (!workspace || !stats || n_stats < 0) return SPM_ERR_INVALID_ARG;
-  (void)mode;
   spm_tuning tun;
   {
     std::lock_guard<std::mutex> lk(g_mutex);
@@ -1663,8 +1931,8 @@ spm_status spm_debug_plan_stats(const void* workspace, size_t ws_bytes, int64_t 
   if (s != SPM_OK) return s;
   const int64_t tp[2] = {0, m};
   HostPlan hp;
-  s = host_plan(1, &n_rows, &n_cols, tp, dtype == SPM_F64 ? 8 : 4, (flags & SPM_SEQ_EXPLICIT) != 0,
-                tun.bucket_target, ds->sms, hp);
+  const ModeParams mp = mode_params(mode, flags, tun);
+  s = host_plan(1, &n_rows, &n_cols, tp, dtype == SPM_F64 ? 8 : 4, mp.seq, mp.tgt, ds->sms, hp);
   if (s != SPM_OK) return s;
   if (ws_bytes < hp.L.total) return SPM_ERR_WORKSPACE_TOO_SMALL;
   const char* ws = static_cast<const char*>(workspace);
@@ -1678,12 +1946,12 @@ spm_status spm_debug_plan_stats(const void* workspace, size_t ws_bytes, int64_t 
   int64_t mx = 0, over = 0, over_w = 0;
   for (uint32_t c : cnt) {
     mx = std::max<int64_t>(mx, c);
-    if (c > (uint32_t)kCap) {
+    if (c > (uint32_t)mp.cap) {
       ++over;
       over_w += c;
     }
   }
-  const int64_t v[7] = {(int64_t)sc.NB, mx, over, over_w, kCap, mm.h2used, mm.nbcap};
+  const int64_t v[7] = {(int64_t)sc.NB, mx, over, over_w, mp.cap, mm.h2used, mm.nbcap};
   for (int i = 0; i < n_stats && i < 7; ++i) stats[i] = v[i];
   return SPM_OK;
 }
@@ -1708,8 +1976,9 @@ spm_status spm_assemble_csc_batched_workspace(int64_t batch, const int64_t* h_n_
     tun = g_tuning;
   }
   HostPlan hp;
-  const spm_status s = host_plan(batch, h_n_rows, h_n_cols, h_trip_ptr, dtype == SPM_F64 ? 8 : 4,
-                                 (flags & SPM_SEQ_EXPLICIT) != 0, tun.bucket_target, num_sms_for_sizing(), hp);
+  const ModeParams mp = mode_params(mode, flags, tun);
+  const spm_status s = host_plan(batch, h_n_rows, h_n_cols, h_trip_ptr, dtype == SPM_F64 ? 8 : 4, mp.seq, mp.tgt,
+                                 num_sms_for_sizing(), hp);
   if (s != SPM_OK) return s;
   *bytes = hp.L.total;
   return SPM_OK;

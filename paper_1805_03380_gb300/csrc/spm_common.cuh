@@ -29,19 +29,34 @@ constexpr int kL2Bits = 8;                // a level-2 table refines one cell in
 constexpr int kL2Size = 1 << kL2Bits;
 constexpr int kMaxL2Tables = 32;          // level-2 tables per matrix
 constexpr int kMaxKeyBits = 52;           // n_rows * n_cols <= 2^52
-constexpr int kCap = 8192;                // writes a bucket may hold for the in-shared-memory path
+constexpr int kCapSum = 12288;            // writes of one bucket held in shared memory (add mode)
+constexpr int kCapSet = 9216;             // ... (last-write mode or with the map: positions kept too)
+constexpr int kSubBitsMax = 11;           // counting-sort digit inside a bucket: up to 2048 sub-bins
 constexpr int64_t kSampleTotal = 1 << 19; // samples drawn per call (spread over the matrices)
 constexpr int64_t kSampleMin = 256;       // at least this many per matrix (or all of its writes)
-constexpr uint32_t kPtrFlag = 0x80000000u;// LUT entry refers to a level-2 table
-constexpr int kBaseBits = 26;             // LUT leaf: bucket base in the low 26 bits, j above
+// LUT entry: bit 31 = refers to a level-2 table (bits 0..30 = table id); otherwise bit 30 =
+// merged group of 2^x cells, bits 25..29 = x (split exponent j, or group exponent g), bits
+// 0..24 = first bucket of the leaf/group (relative to the matrix)
+constexpr uint32_t kPtrFlag = 0x80000000u;
+constexpr uint32_t kMergeFlag = 0x40000000u;
+constexpr int kXShift = 25;
+constexpr int kBaseBits = 25;
 constexpr uint32_t kBaseMask = (1u << kBaseBits) - 1;
 constexpr uint64_t kBadKey = ~0ull;       // sample sentinel for an out-of-range write
 constexpr uint64_t kStAgg = 1ull << 62;   // look-back states of a bucket
 constexpr uint64_t kStIncl = 2ull << 62;
 constexpr uint64_t kStMask = (1ull << 62) - 1;
 constexpr int kScanBlock = 1024;          // elements per block of the device-wide scan
-constexpr int kLutCapSmem = 16384;        // LUT entries a partition block keeps in shared memory
-constexpr int kHistCapSmem = 36864;       // bucket counters a partition block keeps in shared memory
+constexpr int kLutCapSmem = 12288;        // LUT entries a partition block keeps in shared memory
+constexpr int kHistCapSmem = 40960;       // bucket counters a partition block keeps in shared memory
+
+// A partitioned write: key within its bucket, stream position, raw value bits
+// (float32 values in the low half).  16 bytes, written with one vector store.
+struct __align__(16) Rec {
+  uint32_t lkey;
+  uint32_t pos;
+  uint64_t val;
+};
 
 // ---------------------------------------------------------------------------
 // Per-matrix metadata (one entry per matrix of a batch; a single matrix is a
@@ -78,10 +93,14 @@ struct Derived {
   int64_t ns, lut_len, nbcap;
 };
 
+// Smallest b with 2^b >= x (0 for x <= 1).
 __host__ __device__ inline int ceil_log2_u64(uint64_t x) {
-  int b = 0;
-  while (b < 63 && (uint64_t{1} << b) < x) ++b;
-  return b;
+  if (x <= 1) return 0;
+#ifdef __CUDA_ARCH__
+  return 64 - __clzll((long long)(x - 1));
+#else
+  return 64 - __builtin_clzll(x - 1);
+#endif
 }
 
 // The sizing formulas (identical on host and device).
@@ -91,7 +110,7 @@ __host__ __device__ inline Derived derive(int64_t n_rows, int64_t n_cols, int64_
   d.K = (uint64_t)n_rows * (uint64_t)n_cols;
   d.bbits = d.K <= 1 ? 0 : ceil_log2_u64(d.K);
   int L1 = 0;
-  if (m > tgt) L1 = ceil_log2_u64((uint64_t)((m + tgt - 1) / tgt)) + 2;
+  if (m > tgt) L1 = ceil_log2_u64((uint64_t)((m + tgt - 1) / tgt)) + 3;
   if (L1 > kMaxL1Smem) L1 = kMaxL1Smem;
   if (L1 < d.bbits - 32) L1 = d.bbits - 32;
   if (L1 > d.bbits) L1 = d.bbits;
@@ -141,7 +160,7 @@ struct Layout {
   bool seq;
   // byte offsets
   size_t meta, scal, cta, samp, cellcnt, lut, l2cell, bk_lo, bk_info, bk_count, bk_start, bk_state,
-      scanpart, hist, rk, rv, rs, total;
+      scanpart, hist, rec, rs, total;
 };
 
 // Device-side scalars block (in the workspace).
@@ -188,13 +207,13 @@ struct Ctx {
   uint64_t* bk_state;
   uint32_t* scanpart;
   uint32_t* hist;
-  uint64_t* rk;
-  void* rv;
+  Rec* rec;
   uint64_t* rs;
   // sizes
   int64_t B, m_total, S_total, lut_total, nbcap_total, hist_bound, C;
   int32_t sum_mode, f64, keep_map, has_seq;
-  int64_t tgt;
+  int64_t tgt;       // planner target (writes per bucket) for this call's mode
+  int32_t cap;       // writes a bucket may hold for the in-shared-memory path
   int32_t sub_bits;
   int64_t withhold;   // bucket whose look-back publication is withheld (tests), -1 = none
 };

@@ -69,3 +69,38 @@ def abs_contrib_per_entry(rows, cols, vals, shape, col_ptr, row_idx):
     col_of = np.repeat(np.arange(shape[1], dtype=np.int64), np.diff(col_ptr))
     ek = col_of * n_rows + row_idx
     return s[np.searchsorted(uk, ek)]
+
+
+def correctly_rounded_sums(d, col_ptr, row_idx):
+    """Per stored element: math.fsum of its writes (the exact sum rounded once
+    to float64), then float32 when the values are float32."""
+    import math
+    n_rows = d["shape"][0]
+    rows = np.asarray(d["rows"], dtype=np.int64)
+    cols = np.asarray(d["cols"], dtype=np.int64)
+    vals = np.asarray(d["vals"], dtype=np.float64)
+    key = cols * n_rows + rows
+    order = np.argsort(key, kind="stable")
+    sk, sv = key[order], vals[order]
+    cut = np.flatnonzero(np.diff(sk)) + 1
+    starts = np.concatenate([[0], cut])
+    ends = np.concatenate([cut, [len(sk)]])
+    ukeys = sk[starts]
+    col_of = np.repeat(np.arange(d["shape"][1], dtype=np.int64), np.diff(np.asarray(col_ptr)))
+    ek = col_of * n_rows + np.asarray(row_idx, dtype=np.int64)
+    gi = np.searchsorted(ukeys, ek)
+    out = np.array([math.fsum(sv[starts[g]:ends[g]]) for g in gi.tolist()])
+    return out
+
+
+def assert_correctly_rounded(got_vals, d, col_ptr, row_idx):
+    """float64: bit-equal to fsum; float32: within one float32 ulp of fsum
+    rounded to float32 (fsum then float32 may round twice)."""
+    want = correctly_rounded_sums(d, col_ptr, row_idx)
+    got = np.asarray(got_vals)
+    if got.dtype == np.float64:
+        assert_bit_exact(got, want)
+    else:
+        w32 = want.astype(np.float32)
+        diff = np.abs(got.view(np.int32).astype(np.int64) - w32.view(np.int32).astype(np.int64))
+        assert np.all(diff <= 1), f"{np.count_nonzero(diff > 1)} values more than 1 ulp from the rounded exact sum"

