@@ -40,6 +40,9 @@ def workload_spec(name):
     specs = {
         "n8": dict(desc="100,000 x 100,000, 10^8 writes, Zipf(1.1) columns, uniform rows, U(-1,1) float64, sum mode",
                    m=100_000_000, n=100_000, dtype=np.float64, mode="sum", kind="zipf"),
+        "zipf3e7": dict(desc="100,000 x 100,000, 3*10^7 writes, Zipf(1.1) columns, U(-1,1) float64, sum mode "
+                             "(a smaller case of the same stream, for profiling)",
+                        m=30_000_000, n=100_000, dtype=np.float64, mode="sum", kind="zipf"),
         "zipf1e7": dict(desc="100,000 x 100,000, 10^7 writes, Zipf(1.1) columns, U(-1,1) float64, sum mode",
                         m=10_000_000, n=100_000, dtype=np.float64, mode="sum", kind="zipf"),
         "zipf1e7_f32": dict(desc="100,000 x 100,000, 10^7 writes, Zipf(1.1) columns, U(-1,1) float32 values, "
@@ -216,7 +219,7 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="n8", choices=["n8", "zipf1e7", "zipf1e7_f32", "fem2048"])
+    ap.add_argument("--workload", default="n8", choices=["n8", "zipf3e7", "zipf1e7", "zipf1e7_f32", "fem2048"])
     ap.add_argument("--cpu-sample", type=int, default=10_000_000, help="writes the CPU oracle baseline times")
     ap.add_argument("--ref-sample", type=int, default=1_000_000, help="writes per step of --impl reference")
     ap.add_argument("--e2e-steps", type=int, default=None)

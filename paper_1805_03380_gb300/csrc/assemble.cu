@@ -226,8 +226,15 @@ __global__ void k_sample(Ctx c) {
     if (ns >= m) {
       p = k;
     } else {
-      const uint64_t a = k * m / ns, b = (k + 1) * m / ns;
-      p = a + (b > a ? mix32((uint64_t)g * 0x9e3779b97f4a7c15ull + 17) % (b - a) : 0);
+      // samples come in groups of eight consecutive writes (one 32-byte
+      // sector of rows and of cols per group); group j sits at a hashed
+      // offset inside the j-th stretch of m / groups writes
+      const uint64_t ng = (ns + 7) / 8, j = k >> 3;
+      const uint64_t a = j * m / ng, b = (j + 1) * m / ng;
+      const uint64_t room = b - a > 8 ? b - a - 8 : 0;
+      const uint64_t off = room ? (mix32(j * 0x9e3779b97f4a7c15ull + (uint64_t)i * 7919 + 17) % room) & ~7ull : 0;
+      p = a + off + (k & 7);
+      if (p >= m) p = m - 1;
     }
     const int64_t t = mm.t0 + (int64_t)p;
     const int32_t r = c.rows[t], col = c.cols[t];
@@ -270,11 +277,11 @@ __device__ __forceinline__ Split leaf_split(uint64_t lo, int shift, uint64_t est
 }
 
 // Writes expected in a region that received `cnt` samples: the count plus a
-// two-standard-deviation margin, scaled by writes per sample.
+// one-standard-deviation margin, scaled by writes per sample.
 __device__ __forceinline__ uint64_t estimate(uint64_t cnt, const MatMeta& mm) {
   if (mm.ns <= 0) return 0;
   if (mm.ns >= mm.m) return cnt;
-  const uint64_t x = cnt + 2ull * (uint64_t)sqrtf((float)cnt) + 1ull;
+  const uint64_t x = cnt + (uint64_t)sqrtf((float)cnt) + 1ull;
   return x * (uint64_t)mm.m / (uint64_t)mm.ns;
 }
 
@@ -797,13 +804,28 @@ __global__ void __launch_bounds__(256) k_colscan(Ctx c) {
     return;
   }
   uint32_t running = 0;
-  for (int cc = 0; cc < C; ++cc) {
-    const uint32_t cb0 = s_cb0[cc];
-    if ((uint32_t)b >= cb0 && (uint32_t)b < s_cb1[cc]) {
-      uint32_t* p = c.hist + s_hoff[cc] + (b - cb0);
-      const uint32_t v = *p;
-      *p = running;
-      running += v;
+  for (int c0 = 0; c0 < C; c0 += 8) {  // eight independent loads in flight
+    uint32_t v[8];
+    uint32_t* ptr[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int cc = c0 + u;
+      ptr[u] = nullptr;
+      v[u] = 0u;
+      if (cc < C) {
+        const uint32_t cb0 = s_cb0[cc];
+        if ((uint32_t)b >= cb0 && (uint32_t)b < s_cb1[cc]) {
+          ptr[u] = c.hist + s_hoff[cc] + (b - cb0);
+          v[u] = *ptr[u];
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      if (ptr[u]) {
+        *ptr[u] = running;
+        running += v[u];
+      }
     }
   }
   c.bk_count[b] = running;
@@ -858,13 +880,19 @@ __global__ void __launch_bounds__(1024) k_scatter(Ctx c) {
   load_view(c, ci, lut_base, lut_smem, ci.i0, v);
   using VT = typename std::conditional<F64, uint64_t, uint32_t>::type;
   const VT* vin = reinterpret_cast<const VT*>(c.vals);
+  uint64_t keep_policy;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(keep_policy));
   auto body = [&](int64_t t, int32_t r, int32_t col, VT val) {
     advance_view<BATCHED>(c, ci, lut_base, lut_smem, t, v);
     uint32_t b, lk;
     if (classify(v, r, col, b, lk)) {
       const uint32_t slot = atomicAdd(&cur[b], 1u);
       const uint64_t vb = (uint64_t)val;
-      *reinterpret_cast<uint4*>(c.rec + slot) = make_uint4(lk, (uint32_t)t, (uint32_t)vb, (uint32_t)(vb >> 32));
+      // records are written a few at a time per bucket: ask L2 to keep the
+      // partially written lines rather than the streamed inputs
+      asm volatile("st.global.L2::cache_hint.v4.u32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(c.rec + slot), "r"(lk),
+                   "r"((uint32_t)t), "r"((uint32_t)vb), "r"((uint32_t)(vb >> 32)), "l"(keep_policy)
+                   : "memory");
       if (SEQ) c.rs[slot] = c.seq[t];
     }
   };
@@ -872,10 +900,7 @@ __global__ void __launch_bounds__(1024) k_scatter(Ctx c) {
     const int64_t nvec = (ci.e1 - ci.e0) >> 2;
     const int4* r4p = reinterpret_cast<const int4*>(c.rows + ci.e0);
     const int4* c4p = reinterpret_cast<const int4*>(c.cols + ci.e0);
-    for (int64_t q = threadIdx.x; q < nvec; q += blockDim.x) {
-      const int4 r4 = __ldcs(r4p + q), c4 = __ldcs(c4p + q);
-      const int64_t t = ci.e0 + 4 * q;
-      VT x0, x1, x2, x3;
+    auto load_vals = [&](int64_t t, VT& x0, VT& x1, VT& x2, VT& x3) {
       if (F64) {
         const ulonglong2* vp = reinterpret_cast<const ulonglong2*>(vin + t);
         const ulonglong2 a = __ldcs(vp), bq = __ldcs(vp + 1);
@@ -884,6 +909,30 @@ __global__ void __launch_bounds__(1024) k_scatter(Ctx c) {
         const uint4 a = __ldcs(reinterpret_cast<const uint4*>(vin + t));
         x0 = (VT)a.x; x1 = (VT)a.y; x2 = (VT)a.z; x3 = (VT)a.w;
       }
+    };
+    const int64_t NT = blockDim.x;
+    int64_t q = threadIdx.x;
+    for (; q + NT < nvec; q += 2 * NT) {  // two groups of loads in flight per thread
+      const int4 ra = __ldcs(r4p + q), ca = __ldcs(c4p + q);
+      const int4 rb = __ldcs(r4p + q + NT), cb = __ldcs(c4p + q + NT);
+      const int64_t ta = ci.e0 + 4 * q, tb = ci.e0 + 4 * (q + NT);
+      VT a0, a1, a2, a3, b0, b1, b2, b3;
+      load_vals(ta, a0, a1, a2, a3);
+      load_vals(tb, b0, b1, b2, b3);
+      body(ta, ra.x, ca.x, a0);
+      body(ta + 1, ra.y, ca.y, a1);
+      body(ta + 2, ra.z, ca.z, a2);
+      body(ta + 3, ra.w, ca.w, a3);
+      body(tb, rb.x, cb.x, b0);
+      body(tb + 1, rb.y, cb.y, b1);
+      body(tb + 2, rb.z, cb.z, b2);
+      body(tb + 3, rb.w, cb.w, b3);
+    }
+    for (; q < nvec; q += NT) {
+      const int4 r4 = __ldcs(r4p + q), c4 = __ldcs(c4p + q);
+      const int64_t t = ci.e0 + 4 * q;
+      VT x0, x1, x2, x3;
+      load_vals(t, x0, x1, x2, x3);
       body(t, r4.x, c4.x, x0);
       body(t + 1, r4.y, c4.y, x1);
       body(t + 2, r4.z, c4.z, x2);
@@ -899,9 +948,12 @@ __global__ void __launch_bounds__(1024) k_scatter(Ctx c) {
 // ===========================================================================
 // Resolve: one bucket at a time per block (persistent)
 // ===========================================================================
-// Shared-memory layout of the resolve kernel (host and device agree on it).
+// Shared-memory layout of the resolve kernel (host and device agree on it):
+// only the keys and the sort permutation live in shared memory; values,
+// positions and results stay in the bucket's records (L2).  In window mode
+// the second half of the key array holds the record index of each key.
 struct RLayout {
-  size_t keys, vals, pos, perm, orig, sub_a, sub_b, slots, total;
+  size_t keys, perm, sub_a, sub_b, slots, total;
 };
 
 struct __align__(8) Slot {
@@ -910,7 +962,7 @@ struct __align__(8) Slot {
   uint32_t has_head;  // the thread's range contains the start of a run (or is past the end)
 };
 
-__host__ __device__ inline RLayout resolve_layout(int cap, bool pos, bool seq, int nt, int sub_bits) {
+__host__ __device__ inline RLayout resolve_layout(int cap, int nt, int sub_bits) {
   RLayout L;
   size_t o = 0;
   auto take = [&](size_t bytes) {
@@ -919,10 +971,7 @@ __host__ __device__ inline RLayout resolve_layout(int cap, bool pos, bool seq, i
     return at;
   };
   L.keys = take(4ull * cap);
-  L.vals = take(8ull * cap);
-  L.pos = pos ? take(4ull * cap) : o;
   L.perm = take(2ull * cap);
-  L.orig = seq ? take(4ull * cap) : o;
   L.sub_a = take(4ull * ((size_t{1} << sub_bits) + 4));
   L.sub_b = take(4ull * (size_t{1} << sub_bits));
   L.slots = take(sizeof(Slot) * (size_t)nt);
@@ -932,20 +981,18 @@ __host__ __device__ inline RLayout resolve_layout(int cap, bool pos, bool seq, i
 
 struct RSmem {
   uint32_t* keys;   // key within the bucket (or window)
-  uint64_t* vals;   // raw value bits (float32 in the low half)
-  uint32_t* pos;    // stream position (last-write mode, or when the map is kept)
   uint16_t* perm;   // sorted order
-  uint32_t* orig;   // index of the record in its bucket (window mode, explicit seq)
+  uint32_t* orig;   // window mode: record index of each key (else null: index = position)
   uint32_t* sub_a;
   uint32_t* sub_b;
   Slot* slots;
 };
 
 struct BlockShared {
+  uint64_t col0;
   uint32_t buf[32];
   uint32_t tot;
-  uint32_t ticket, next;
-  int32_t emax;
+  uint32_t ticket;
   int64_t excl;
   uint32_t taken, cum, n_w;
   int32_t red_i[32];
@@ -953,36 +1000,54 @@ struct BlockShared {
 
 // Wait (bounded) for the look-back chain of bucket b to provide its exclusive
 // prefix (the number of stored elements of the same matrix in all earlier
-// buckets).  Called by one thread; publishes nothing.
-__device__ int64_t lookback_wait(const Ctx& c, int64_t b) {
+// buckets).  Called by one full warp: each round reads the states of 32
+// predecessors at once, adds the counts back to the nearest one that holds an
+// inclusive value, or waits while any of those nearer ones has published
+// nothing yet.  Publishes nothing.  Every lane returns the prefix.
+__device__ int64_t lookback_wait_warp(const Ctx& c, int64_t b) {
+  const int lane = threadIdx.x & 31;
   int64_t excl = 0;
-  int64_t bb = b - 1;
+  int64_t top = b - 1;  // nearest predecessor not yet accounted for
   const uint64_t t_start = global_timer_ns();
   uint32_t spins = 0;
   while (true) {
-    const uint64_t s = ld_acquire_u64(&c.bk_state[bb]);
+    const int64_t bb = top - lane;
+    const uint64_t s = bb >= 0 ? ld_acquire_u64(&c.bk_state[bb]) : kStIncl;
     const uint64_t flag = s & ~kStMask;
-    if (flag == 0) {
-      if (is_aborted(c)) break;
-      if ((++spins & 63) == 0 && global_timer_ns() - t_start > 2000000000ull) {
-        record_fatal(c, SPM_ERR_TIMEOUT);
-        break;
-      }
+    const unsigned incl = __ballot_sync(0xffffffffu, flag == kStIncl);
+    const unsigned none = __ballot_sync(0xffffffffu, flag == 0);
+    const int first_incl = incl ? __ffs(incl) - 1 : 32;
+    const unsigned upto = first_incl >= 31 ? 0xffffffffu : ((2u << first_incl) - 1u);
+    if ((none & upto) == 0) {
+      uint64_t v = (lane <= first_incl) ? (s & kStMask) : 0ull;
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      excl += (int64_t)v;
+      if (first_incl < 32) break;
+      top -= 32;
       continue;
     }
-    excl += (int64_t)(s & kStMask);
-    if (flag == kStIncl) break;
-    --bb;
+    // leave the wait together: lane 0 decides for the warp
+    int stop = 0;
+    if (lane == 0) {
+      if (is_aborted(c)) {
+        stop = 1;
+      } else if ((++spins & 63) == 0 && global_timer_ns() - t_start > 2000000000ull) {
+        record_fatal(c, SPM_ERR_TIMEOUT);
+        stop = 1;
+      }
+    }
+    if (__shfl_sync(0xffffffffu, stop, 0)) break;
   }
   return excl;
 }
 
 // Decoupled look-back: publish this bucket's count, wait for the prefix,
-// publish the inclusive value.  Called by one thread.
-__device__ int64_t lookback(const Ctx& c, int64_t b, uint32_t nnz) {
-  st_release_u64(&c.bk_state[b], kStAgg | nnz);
-  const int64_t excl = lookback_wait(c, b);
-  st_release_u64(&c.bk_state[b], kStIncl | (uint64_t)(excl + nnz));
+// publish the inclusive value.  Called by one full warp.
+__device__ int64_t lookback_warp(const Ctx& c, int64_t b, uint32_t nnz) {
+  if ((threadIdx.x & 31) == 0) st_release_u64(&c.bk_state[b], kStAgg | nnz);
+  __syncwarp();
+  const int64_t excl = lookback_wait_warp(c, b);
+  if ((threadIdx.x & 31) == 0) st_release_u64(&c.bk_state[b], kStIncl | (uint64_t)(excl + nnz));
   return excl;
 }
 
@@ -1009,69 +1074,144 @@ __device__ __forceinline__ int block_max_int(int v, BlockShared& B) {
   return r;
 }
 
-// Reduction state of one run (equal keys): add mode sums exactly, last-write
-// mode keeps the write with the largest (seq, position).
-template <bool F64, bool SUM, bool SEQ, bool POS>
+__device__ __forceinline__ uint64_t rec_val(const uint4& r) { return ((uint64_t)r.w << 32) | r.z; }
+
+template <bool F64>
+__device__ __forceinline__ bool bits_nonzero(uint64_t bits) {
+  return F64 ? (bits & 0x7FFFFFFFFFFFFFFFull) != 0 : (bits & 0x7FFFFFFFull) != 0;
+}
+
+// Reduction state of one run (equal keys).  Add mode: the exact sum rounded
+// once -- a single write is its own value, two writes are one IEEE addition
+// (which rounds their exact sum), more writes go through the exact integer
+// accumulator.  Last-write mode: the write with the largest (seq, position).
+template <bool F64, bool SUM, bool SEQ>
 struct Red {
   Acc acc;
-  uint64_t seq;
-  uint32_t pos, idx;  // idx = ~0u: no write
+  uint32_t cnt;
+  uint64_t one, two;  // add mode: the first two values while cnt <= 2
+  uint64_t seq, wval;
+  uint32_t pos, idx;  // last-write mode: best write (idx = record index), ~0u = none
 
   __device__ __forceinline__ void clear() {
-    if (SUM) acc = acc_zero();
-    else { seq = 0; pos = 0; idx = ~0u; }
+    if (SUM) {
+      acc = acc_zero();
+      cnt = 0;
+      one = two = 0;
+    } else {
+      seq = 0;
+      wval = 0;
+      pos = 0;
+      idx = ~0u;
+    }
+  }
+  __device__ __forceinline__ static uint64_t wide(uint64_t v) { return F64 ? v : f32_bits_to_f64_bits(v); }
+  // Move the values held aside into the accumulator (cnt becomes >= 3).
+  __device__ __forceinline__ void spill(int emax) {
+    if (cnt >= 1 && cnt <= 2) {
+      acc_add_bits(acc, wide(one), emax);
+      if (cnt == 2) acc_add_bits(acc, wide(two), emax);
+      cnt = 3;
+    }
   }
   __device__ __forceinline__ bool better(uint64_t s2, uint32_t p2) const {
     return idx == ~0u || s2 > seq || (s2 == seq && p2 > pos);
   }
-  __device__ __forceinline__ void add(uint32_t k, const RSmem& S, const Ctx& c, int64_t seg_start, int emax) {
+  __device__ __forceinline__ void add(const uint4& r, uint32_t ridx, const Ctx& c, int64_t seg_start, int emax) {
     if (SUM) {
-      const uint64_t v = S.vals[k];
-      acc_add_bits(acc, F64 ? v : f32_bits_to_f64_bits(v), emax);
+      const uint64_t v = rec_val(r);
+      if (cnt == 0) {
+        one = v;
+        cnt = 1;
+      } else if (cnt == 1) {
+        two = v;
+        cnt = 2;
+      } else {
+        spill(emax);
+        acc_add_bits(acc, wide(v), emax);
+      }
     } else {
-      const uint64_t s2 = SEQ ? c.rs[seg_start + (S.orig ? S.orig[k] : k)] : 0ull;
-      const uint32_t p2 = S.pos[k];
-      if (better(s2, p2)) { seq = s2; pos = p2; idx = k; }
+      const uint64_t s2 = SEQ ? c.rs[seg_start + ridx] : 0ull;
+      if (better(s2, r.y)) {
+        seq = s2;
+        pos = r.y;
+        idx = ridx;
+        wval = rec_val(r);
+      }
     }
   }
-  __device__ __forceinline__ void merge(const Slot& o) {
+  // (the caller spills an add-mode state before merging)
+  __device__ __forceinline__ void merge(const Slot& o, const uint4* recs) {
     if (SUM) {
       Acc b{o.a, (int64_t)o.b, o.flags};
       acc_merge(acc, b);
+      cnt = 3;
     } else if (o.flags) {
       const uint32_t p2 = (uint32_t)o.b, k2 = (uint32_t)(o.b >> 32);
-      if (better(o.a, p2)) { seq = o.a; pos = p2; idx = k2; }
+      if (better(o.a, p2)) {
+        seq = o.a;
+        pos = p2;
+        idx = k2;
+        wval = rec_val(recs[k2]);
+      }
     }
   }
-  __device__ __forceinline__ Slot to_slot(uint32_t has_head) const {
+  // Publishable state (add mode: everything in the accumulator).
+  __device__ __forceinline__ Slot to_slot(uint32_t has_head, int emax) {
     Slot s;
-    if (SUM) { s.a = acc.lo; s.b = (uint64_t)acc.hi; s.flags = acc.flags; }
-    else { s.a = seq; s.b = (uint64_t)pos | ((uint64_t)idx << 32); s.flags = idx != ~0u ? 1u : 0u; }
+    if (SUM) {
+      spill(emax);
+      s.a = acc.lo;
+      s.b = (uint64_t)acc.hi;
+      s.flags = acc.flags;
+    } else {
+      s.a = seq;
+      s.b = (uint64_t)pos | ((uint64_t)idx << 32);
+      s.flags = idx != ~0u ? 1u : 0u;
+    }
     s.has_head = has_head;
     return s;
   }
   // Final value bits of the element and whether it is stored.
-  __device__ __forceinline__ uint64_t finish(const RSmem& S, int emax, bool& keep) const {
-    if (SUM) return acc_round(acc, emax, !F64, &keep);
-    const uint64_t bits = S.vals[idx];
-    keep = F64 ? (__longlong_as_double((long long)bits) != 0.0) : (__uint_as_float((uint32_t)bits) != 0.0f);
-    return bits;
+  __device__ __forceinline__ uint64_t finish(int emax, bool& keep) const {
+    if (SUM) {
+      uint64_t bits;
+      if (cnt == 1) {
+        bits = one;
+      } else if (cnt == 2) {
+        if (F64) {
+          bits = (uint64_t)__double_as_longlong(
+              __dadd_rn(__longlong_as_double((long long)one), __longlong_as_double((long long)two)));
+        } else {
+          const double sum = __dadd_rn((double)__uint_as_float((uint32_t)one), (double)__uint_as_float((uint32_t)two));
+          bits = (uint64_t)__float_as_uint(__double2float_rn(sum));
+        }
+      } else {
+        return acc_round(acc, emax, !F64, &keep);
+      }
+      keep = bits_nonzero<F64>(bits);
+      return bits;
+    }
+    keep = bits_nonzero<F64>(wval);
+    return wval;
   }
 };
 
-// Process the n records in shared memory (keys relative to klo, in
-// [0, span)): sort them by key, reduce each run of equal keys, drop zeros,
-// and write the stored elements, the column offsets of every column that
-// starts inside [klo, klo + span) and the map.  The output position of the
-// first element comes from the look-back (bucket mode) or is base_in
-// (window mode).  Returns the number of stored elements.
+// Process the n keys in shared memory (relative to klo, in [0, span)): sort
+// them, reduce each run of equal keys (values from the bucket's records),
+// drop zeros, and write the stored elements, the column offsets of every
+// column that starts inside [klo, klo + span) and the map.  The output
+// position of the first element comes from the look-back (bucket mode) or is
+// base_in (window mode).  Returns the number of stored elements.
 template <bool F64, bool SUM, bool SEQ, bool POS>
 __device__ uint32_t resolve_records(const Ctx& c, const MatMeta& mm, int64_t b, uint64_t klo, uint64_t span,
                                     uint32_t n, const RSmem& S, BlockShared& B, bool window, int64_t base_in,
                                     int64_t seg_start, int emax) {
   using VT = typename std::conditional<F64, uint64_t, uint32_t>::type;
-  using R = Red<F64, SUM, SEQ, POS>;
+  using R = Red<F64, SUM, SEQ>;
   const int tid = threadIdx.x, NT = blockDim.x;
+  uint4* recs = reinterpret_cast<uint4*>(c.rec + seg_start);
+  if (tid == 0) B.col0 = klo / (uint64_t)mm.n_rows;  // visible after the next barrier
   // ---- counting sort on the top key bits
   const int sbits = span <= 1 ? 0 : ceil_log2_u64(span);
   const int sshift = sbits > c.sub_bits ? sbits - c.sub_bits : 0;
@@ -1117,27 +1257,51 @@ __device__ uint32_t resolve_records(const Ctx& c, const MatMeta& mm, int64_t b, 
   const uint32_t p0 = min(n, (uint32_t)tid * E), p1 = min(n, p0 + E);
   auto key_at = [&](uint32_t p) -> uint32_t { return S.keys[S.perm[p]]; };
   auto is_head = [&](uint32_t p) -> bool { return p == 0 || key_at(p) != key_at(p - 1); };
+  auto ridx_of = [&](uint32_t q) -> uint32_t { return S.orig ? S.orig[q] : q; };
   R first, cur;
   first.clear();
   cur.clear();
   bool owned = false, seen = false;
   uint32_t kept = 0;
-  for (uint32_t p = p0; p < p1; ++p) {
-    if (is_head(p)) {
-      if (owned) {
-        bool k2;
-        cur.finish(S, emax, k2);
-        kept += k2 ? 1u : 0u;
-      } else if (p > p0) {
-        first = cur;
+  uint32_t hp1 = 0;
+  uint32_t prev_key = p0 > 0 && p0 < n ? key_at(p0 - 1) : ~0u;
+  for (uint32_t pb = p0; pb < p1; pb += 4) {
+    // four records in flight per thread
+    uint4 rr[4];
+    uint32_t qq[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (pb + u < p1) {
+        qq[u] = S.perm[pb + u];
+        rr[u] = recs[ridx_of(qq[u])];
       }
-      cur.clear();
-      owned = seen = true;
     }
-    cur.add(S.perm[p], S, c, seg_start, emax);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const uint32_t p = pb + u;
+      if (p >= p1) break;
+      const uint32_t kk = S.keys[qq[u]];
+      if (p == 0 || kk != prev_key) {
+        if (owned) {
+          // a complete run (head and end in this range): its result goes to
+          // the head's record for the write pass (only this thread touches it)
+          bool k2;
+          const uint64_t bits = cur.finish(emax, k2);
+          kept += k2 ? 1u : 0u;
+          if (!c.keep_map) recs[ridx_of(S.perm[hp1])].z = (uint32_t)bits, recs[ridx_of(S.perm[hp1])].w = (uint32_t)(bits >> 32);
+        } else if (p > p0) {
+          first = cur;
+        }
+        cur.clear();
+        owned = seen = true;
+        hp1 = p;
+      }
+      prev_key = kk;
+      cur.add(rr[u], ridx_of(qq[u]), c, seg_start, emax);
+    }
   }
   if (!seen) first = cur;
-  S.slots[tid] = first.to_slot((seen || p0 >= n) ? 1u : 0u);
+  S.slots[tid] = first.to_slot((seen || p0 >= n) ? 1u : 0u, emax);
   __syncthreads();
   uint64_t open_bits = 0;
   bool open_keep = false;
@@ -1145,23 +1309,30 @@ __device__ uint32_t resolve_records(const Ctx& c, const MatMeta& mm, int64_t b, 
   if (seen) {  // the last run starting here may continue into the following ranges
     for (int t2 = tid + 1; t2 < NT; ++t2) {
       const Slot sl = S.slots[t2];
-      cur.merge(sl);
+      if (sl.has_head && !(sl.flags | sl.a | sl.b)) break;  // next range starts a run: nothing to add
+      if (SUM) cur.spill(emax);
+      cur.merge(sl, recs);
       if (sl.has_head) break;
     }
-    open_bits = cur.finish(S, emax, open_keep);
-    open_win = cur.idx;
+    open_bits = cur.finish(emax, open_keep);
+    open_win = SUM ? 0u : cur.idx;
     kept += open_keep ? 1u : 0u;
   }
   const uint32_t off = block_scan_excl<uint32_t>(kept, &B.tot, B.buf);
   const uint32_t nnz = B.tot;
-  if (tid == 0) {
-    if (window) B.excl = base_in;
-    else if (b == c.withhold) B.excl = 0;  // fault injection: publish nothing, wait for nothing
-    else if (klo == 0) {
-      st_release_u64(&c.bk_state[b], kStIncl | (uint64_t)nnz);
-      B.excl = 0;
+  if (tid < 32) {
+    if (window) {
+      if (tid == 0) B.excl = base_in;
+    } else if (b == c.withhold) {
+      if (tid == 0) B.excl = 0;  // fault injection: publish nothing, wait for nothing
+    } else if (klo == 0) {
+      if (tid == 0) {
+        st_release_u64(&c.bk_state[b], kStIncl | (uint64_t)nnz);
+        B.excl = 0;
+      }
     } else {
-      B.excl = lookback(c, b, nnz);
+      const int64_t ex = lookback_warp(c, b, nnz);
+      if (tid == 0) B.excl = ex;
     }
   }
   __syncthreads();
@@ -1174,7 +1345,11 @@ __device__ uint32_t resolve_records(const Ctx& c, const MatMeta& mm, int64_t b, 
   };
   const uint64_t gstart = klo + (tid == 0 ? 0ull : range_start(p0));
   const uint64_t gend = klo + range_start(p1);
-  uint64_t j = (gstart + nr - 1) / nr;  // first column whose start key lies in this thread's range
+  // first column whose start key lies in this thread's range; the bucket's
+  // first column c0 is computed once per bucket
+  const uint64_t c0 = B.col0, d0 = gstart - c0 * nr;
+  uint64_t j = c0 + ((d0 >> 32) == 0 && (nr >> 32) == 0 ? (uint64_t)(((uint32_t)d0 + (uint32_t)nr - 1u) / (uint32_t)nr)
+                                                        : (d0 + nr - 1) / nr);
   uint64_t next_start = j * nr;
   int64_t* colp = c.col_ptr + mm.col_base;
   int32_t* rowp = c.row_idx + mm.t0;
@@ -1193,27 +1368,44 @@ __device__ uint32_t resolve_records(const Ctx& c, const MatMeta& mm, int64_t b, 
       slot = (int32_t)idx;
       ++idx;
     }
-    if (c.keep_map && POS) {
+    if (POS && c.keep_map) {
       for (uint32_t x = hp; x < end_p; ++x) {
-        const uint32_t k = S.perm[x];
-        c.map[S.pos[k]] = (!SUM && k != win) ? -1 : slot;
+        const uint32_t rk = ridx_of(S.perm[x]);
+        c.map[recs[rk].y] = (!SUM && rk != win) ? -1 : slot;
       }
     }
   };
   owned = false;
   uint32_t hp = 0;
-  for (uint32_t p = p0; p < p1; ++p) {
-    if (is_head(p)) {
-      if (owned) {
-        bool k2;
-        const uint64_t bits = cur.finish(S, emax, k2);
-        emit(hp, p, bits, k2, cur.idx);
+  if (!c.keep_map) {
+    // results of complete runs were stored in pass 1
+    for (uint32_t p = p0; p < p1; ++p) {
+      if (is_head(p)) {
+        if (owned) {
+          const uint64_t r = rec_val(recs[ridx_of(S.perm[hp])]);
+          emit(hp, p, r, bits_nonzero<F64>(r), 0u);
+        }
+        owned = true;
+        hp = p;
       }
-      cur.clear();
-      owned = true;
-      hp = p;
     }
-    if (owned) cur.add(S.perm[p], S, c, seg_start, emax);
+  } else {
+    for (uint32_t p = p0; p < p1; ++p) {
+      if (is_head(p)) {
+        if (owned) {
+          bool k2;
+          const uint64_t bits = cur.finish(emax, k2);
+          emit(hp, p, bits, k2, SUM ? 0u : cur.idx);
+        }
+        cur.clear();
+        owned = true;
+        hp = p;
+      }
+      if (owned) {
+        const uint32_t q = S.perm[p];
+        cur.add(recs[ridx_of(q)], ridx_of(q), c, seg_start, emax);
+      }
+    }
   }
   if (owned) {
     uint32_t end_p = p1;
@@ -1235,19 +1427,16 @@ template <bool F64, bool SUM, bool SEQ, bool POS>
 __device__ uint32_t resolve_single_key(const Ctx& c, const MatMeta& mm, uint64_t key, uint32_t lkey, int64_t start,
                                        uint32_t n, const RSmem& S, BlockShared& B, int64_t base) {
   using VT = typename std::conditional<F64, uint64_t, uint32_t>::type;
-  using R = Red<F64, SUM, SEQ, POS>;
+  using R = Red<F64, SUM, SEQ>;
   const int tid = threadIdx.x, NT = blockDim.x;
   const uint4* recs = reinterpret_cast<const uint4*>(c.rec + start);
-  auto val_of = [&](const uint4& r) -> uint64_t {
-    const uint64_t v = ((uint64_t)r.w << 32) | r.z;
-    return F64 ? v : f32_bits_to_f64_bits(v);
-  };
   int emax = 1;
   if (SUM) {
     int el = 0;
     for (uint32_t k = tid; k < n; k += NT) {
       const uint4 r = recs[k];
-      if (r.x == lkey) el = max(el, f64_align_exponent(val_of(r)));
+      const uint64_t v = rec_val(r);
+      if (r.x == lkey) el = max(el, f64_align_exponent(F64 ? v : f32_bits_to_f64_bits(v)));
     }
     emax = max(1, block_max_int(el, B));
   }
@@ -1255,34 +1444,22 @@ __device__ uint32_t resolve_single_key(const Ctx& c, const MatMeta& mm, uint64_t
   st.clear();
   for (uint32_t k = tid; k < n; k += NT) {
     const uint4 r = recs[k];
-    if (r.x != lkey) continue;
-    if (SUM) {
-      acc_add_bits(st.acc, val_of(r), emax);
-    } else {
-      const uint64_t s2 = SEQ ? c.rs[start + k] : 0ull;
-      if (st.better(s2, r.y)) { st.seq = s2; st.pos = r.y; st.idx = k; }
-    }
+    if (r.x == lkey) st.add(r, k, c, start, emax);
   }
-  S.slots[tid] = st.to_slot(0u);
+  S.slots[tid] = st.to_slot(0u, emax);
   __syncthreads();
   __shared__ uint64_t s_bits;
   __shared__ uint32_t s_keep, s_win;
   if (tid == 0) {
     R all;
     all.clear();
-    for (int t2 = 0; t2 < NT; ++t2) all.merge(S.slots[t2]);
+    if (SUM) all.cnt = 3;
+    for (int t2 = 0; t2 < NT; ++t2) all.merge(S.slots[t2], recs);
     bool keep;
-    uint64_t bits;
-    if (SUM) {
-      bits = acc_round(all.acc, emax, !F64, &keep);
-    } else {
-      const uint4 r = recs[all.idx];
-      bits = ((uint64_t)r.w << 32) | r.z;
-      keep = F64 ? (__longlong_as_double((long long)bits) != 0.0) : (__uint_as_float((uint32_t)bits) != 0.0f);
-    }
+    const uint64_t bits = all.finish(emax, keep);
     s_bits = bits;
     s_keep = keep ? 1u : 0u;
-    s_win = all.idx;
+    s_win = SUM ? 0u : all.idx;
     const uint64_t nr = (uint64_t)mm.n_rows;
     const uint64_t col = key / nr;
     if (col * nr == key) c.col_ptr[mm.col_base + col] = base;
@@ -1293,7 +1470,7 @@ __device__ uint32_t resolve_single_key(const Ctx& c, const MatMeta& mm, uint64_t
   }
   __syncthreads();
   const bool keep = s_keep != 0;
-  if (c.keep_map) {
+  if (POS && c.keep_map) {
     for (uint32_t k = tid; k < n; k += NT) {
       const uint4 r = recs[k];
       if (r.x != lkey) continue;
@@ -1310,29 +1487,27 @@ __global__ void __launch_bounds__(1024) k_resolve(Ctx c) {
   __shared__ BlockShared B;
   __shared__ MatMeta mm;
   const int tid = threadIdx.x, NT = blockDim.x;
-  const RLayout RL = resolve_layout(c.cap, POS, SEQ, NT, c.sub_bits);
+  const RLayout RL = resolve_layout(c.cap, NT, c.sub_bits);
   RSmem S;
   S.keys = reinterpret_cast<uint32_t*>(smraw + RL.keys);
-  S.vals = reinterpret_cast<uint64_t*>(smraw + RL.vals);
-  S.pos = reinterpret_cast<uint32_t*>(smraw + RL.pos);
   S.perm = reinterpret_cast<uint16_t*>(smraw + RL.perm);
   S.orig = nullptr;
   S.sub_a = reinterpret_cast<uint32_t*>(smraw + RL.sub_a);
   S.sub_b = reinterpret_cast<uint32_t*>(smraw + RL.sub_b);
   S.slots = reinterpret_cast<Slot*>(smraw + RL.slots);
-  uint32_t* orig_store = reinterpret_cast<uint32_t*>(smraw + RL.orig);
   const uint32_t NB = c.scal->NB;
   const uint32_t cap = (uint32_t)c.cap;
-  if (tid == 0) B.next = is_aborted(c) ? ~0u : atomicAdd(&c.scal->ticket, 1u);
-  __syncthreads();
+  const uint32_t capw = cap / 2;  // window mode: keys in the first half, record indices in the second
   while (true) {
     if (tid == 0) {
-      // hold the next bucket's ticket too, and warm L2 with its records
-      B.ticket = B.next;
-      B.next = (B.ticket < NB && !is_aborted(c)) ? atomicAdd(&c.scal->ticket, 1u) : ~0u;
-      if (B.next < NB) {
-        const uint32_t nn = c.bk_count[B.next];
-        if (nn <= cap) prefetch_l2(c.rec + c.bk_start[B.next], nn * 16u);
+      // take a bucket when ready for it (tickets follow readiness, so a block
+      // waits only on buckets already being worked on); warm L2 with the
+      // bucket that will be taken about one round later
+      B.ticket = is_aborted(c) ? ~0u : atomicAdd(&c.scal->ticket, 1u);
+      const uint32_t ahead = B.ticket + gridDim.x;
+      if (B.ticket < NB && ahead < NB) {
+        const uint32_t nn = c.bk_count[ahead];
+        if (nn <= cap) prefetch_l2(c.rec + c.bk_start[ahead], nn * 16u);
       }
     }
     __syncthreads();
@@ -1360,13 +1535,21 @@ __global__ void __launch_bounds__(1024) k_resolve(Ctx c) {
     int64_t total;
     if (n <= cap) {
       int el = 0;
-      for (uint32_t k = tid; k < n; k += NT) {
+      uint32_t k = tid;
+      for (; k + 3 * NT < n; k += 4 * NT) {  // four record loads in flight per thread
+        uint4 r[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) r[u] = __ldcg(recs + k + u * NT);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          S.keys[k + u * NT] = r[u].x;
+          if (SUM) el = max(el, f64_align_exponent(F64 ? rec_val(r[u]) : f32_bits_to_f64_bits(rec_val(r[u]))));
+        }
+      }
+      for (; k < n; k += NT) {
         const uint4 r = __ldcg(recs + k);
         S.keys[k] = r.x;
-        if (POS) S.pos[k] = r.y;
-        const uint64_t v = ((uint64_t)r.w << 32) | r.z;
-        S.vals[k] = v;
-        if (SUM) el = max(el, f64_align_exponent(F64 ? v : f32_bits_to_f64_bits(v)));
+        if (SUM) el = max(el, f64_align_exponent(F64 ? rec_val(r) : f32_bits_to_f64_bits(rec_val(r))));
       }
       S.orig = nullptr;
       const int emax = SUM ? max(1, block_max_int(el, B)) : 1;
@@ -1375,12 +1558,15 @@ __global__ void __launch_bounds__(1024) k_resolve(Ctx c) {
       total = B.excl + nnz;
     } else {
       // more writes than fit: windows of the key range, each sorted in shared memory
-      if (tid == 0) B.excl = (klo == 0 || b == c.withhold) ? 0 : lookback_wait(c, b);
+      if (tid < 32) {
+        const int64_t ex = (klo == 0 || b == c.withhold) ? 0 : lookback_wait_warp(c, b);
+        if (tid == 0) B.excl = ex;
+      }
       __syncthreads();
       int64_t base = B.excl;
       __syncthreads();
       uint64_t wlo = 0;
-      S.orig = SEQ ? orig_store : nullptr;
+      S.orig = S.keys + capw;
       while (wlo < span) {
         int hs = (span - wlo <= 1) ? 0 : max(0, ceil_log2_u64(span - wlo) - c.sub_bits);
         uint64_t wend = span;
@@ -1397,7 +1583,7 @@ __global__ void __launch_bounds__(1024) k_resolve(Ctx c) {
           __syncthreads();
           if (tid == 0) {
             uint32_t cum = 0, taken = 0;
-            while (taken < nbins && cum + S.sub_a[taken] <= cap) cum += S.sub_a[taken++];
+            while (taken < nbins && cum + S.sub_a[taken] <= capw) cum += S.sub_a[taken++];
             B.taken = taken;
             B.cum = cum;
           }
@@ -1425,11 +1611,8 @@ __global__ void __launch_bounds__(1024) k_resolve(Ctx c) {
             if (l >= wlo && l < whi) {
               const uint32_t q = atomicAdd(&B.n_w, 1u);
               S.keys[q] = (uint32_t)(l - wlo);
-              if (POS) S.pos[q] = r.y;
-              const uint64_t v = ((uint64_t)r.w << 32) | r.z;
-              S.vals[q] = v;
-              if (SEQ) S.orig[q] = k;
-              if (SUM) el = max(el, f64_align_exponent(F64 ? v : f32_bits_to_f64_bits(v)));
+              S.orig[q] = k;
+              if (SUM) el = max(el, f64_align_exponent(F64 ? rec_val(r) : f32_bits_to_f64_bits(rec_val(r))));
             }
           }
           const int emax = SUM ? max(1, block_max_int(el, B)) : 1;
@@ -1453,6 +1636,16 @@ __global__ void __launch_bounds__(1024) k_resolve(Ctx c) {
       c.d_nnz[mi] = total;
     }
     __syncthreads();
+    // the bucket's records are dead now: drop the L2 lines that hold only
+    // this bucket's records, so that the results stored in them are never
+    // written back to HBM
+    {
+      const uint64_t a0 = reinterpret_cast<uint64_t>(c.rec + start);
+      const uint64_t a1 = reinterpret_cast<uint64_t>(c.rec + start + n);
+      const uint64_t l0 = (a0 + 127) & ~127ull, l1 = a1 & ~127ull;
+      for (uint64_t a = l0 + (uint64_t)tid * 128; a < l1; a += (uint64_t)NT * 128)
+        asm volatile("discard.global.L2 [%0], 128;" ::"l"(a) : "memory");
+    }
   }
 }
 
@@ -1461,7 +1654,7 @@ __global__ void __launch_bounds__(1024) k_resolve(Ctx c) {
 // ===========================================================================
 namespace {
 
-spm_tuning g_tuning = {6144, 11, 1024, 1024};
+spm_tuning g_tuning = {14336, 11, 1024, 1024};
 int64_t g_withhold = -1;
 std::mutex g_mutex;
 
@@ -1506,13 +1699,13 @@ ModeParams mode_params(spm_mode mode, uint32_t flags, const spm_tuning& tun) {
   const bool sum = mode == SPM_MODE_SUM;
   p.pos = !sum || (flags & SPM_KEEP_MAP) != 0;
   p.seq = !sum && (flags & SPM_SEQ_EXPLICIT) != 0;
-  p.cap = !p.pos ? kCapSum : (p.seq ? 7680 : kCapSet);
-  p.tgt = std::max<int64_t>(256, (int64_t)tun.bucket_target * p.cap / kCapSum);
+  p.cap = kCapResolve;
+  p.tgt = std::max<int64_t>(256, (int64_t)tun.bucket_target);
   return p;
 }
 
 size_t resolve_smem_bytes(const ModeParams& mp, int threads, int sub_bits) {
-  return resolve_layout(mp.cap, mp.pos, mp.seq, threads, sub_bits).total;
+  return resolve_layout(mp.cap, threads, sub_bits).total;
 }
 
 size_t partition_smem_bytes() { return (size_t)(kHistCapSmem + kLutCapSmem) * 4; }
@@ -1546,18 +1739,16 @@ spm_status device_init(int& dev, DevState*& ds) {
   SPM_SET_SCATTER(true, true)
 #undef SPM_SET_SCATTER
   {
-    // the largest layout of each instantiation (1024 threads, the widest digit)
-    const size_t r_sum = resolve_layout(kCapSum, false, false, 1024, kSubBitsMax).total;
-    const size_t r_pos = resolve_layout(kCapSet, true, false, 1024, kSubBitsMax).total;
-    const size_t r_seq = resolve_layout(7680, true, true, 1024, kSubBitsMax).total;
-    set_smem_attr(k_resolve<false, true, false, false>, r_sum);
-    set_smem_attr(k_resolve<true, true, false, false>, r_sum);
-    set_smem_attr(k_resolve<false, true, false, true>, r_pos);
-    set_smem_attr(k_resolve<true, true, false, true>, r_pos);
-    set_smem_attr(k_resolve<false, false, false, true>, r_pos);
-    set_smem_attr(k_resolve<true, false, false, true>, r_pos);
-    set_smem_attr(k_resolve<false, false, true, true>, r_seq);
-    set_smem_attr(k_resolve<true, false, true, true>, r_seq);
+    // the largest layout (1024 threads, the widest digit)
+    const size_t r = resolve_layout(kCapResolve, 1024, kSubBitsMax).total;
+    set_smem_attr(k_resolve<false, true, false, false>, r);
+    set_smem_attr(k_resolve<true, true, false, false>, r);
+    set_smem_attr(k_resolve<false, true, false, true>, r);
+    set_smem_attr(k_resolve<true, true, false, true>, r);
+    set_smem_attr(k_resolve<false, false, false, true>, r);
+    set_smem_attr(k_resolve<true, false, false, true>, r);
+    set_smem_attr(k_resolve<false, false, true, true>, r);
+    set_smem_attr(k_resolve<true, false, true, true>, r);
     set_smem_attr(k_plan, kPlanSmem);
   }
   if (cudaGetLastError() != cudaSuccess) return SPM_ERR_CUDA;
@@ -1863,10 +2054,10 @@ int32_t spm_version(void) { return 10000; }
 spm_status spm_set_tuning(const spm_tuning* t) {
   std::lock_guard<std::mutex> lk(g_mutex);
   if (!t) {
-    g_tuning = spm_tuning{6144, 11, 1024, 1024};
+    g_tuning = spm_tuning{14336, 11, 1024, 1024};
     return SPM_OK;
   }
-  if (t->bucket_target < 256 || t->bucket_target > kCapSum) return SPM_ERR_INVALID_ARG;
+  if (t->bucket_target < 256 || t->bucket_target > kCapResolve) return SPM_ERR_INVALID_ARG;
   if (t->sub_bits < 8 || t->sub_bits > kSubBitsMax) return SPM_ERR_INVALID_ARG;
   if (t->partition_threads != 256 && t->partition_threads != 512 && t->partition_threads != 1024)
     return SPM_ERR_INVALID_ARG;

@@ -29,8 +29,7 @@ constexpr int kL2Bits = 8;                // a level-2 table refines one cell in
 constexpr int kL2Size = 1 << kL2Bits;
 constexpr int kMaxL2Tables = 32;          // level-2 tables per matrix
 constexpr int kMaxKeyBits = 52;           // n_rows * n_cols <= 2^52
-constexpr int kCapSum = 12288;            // writes of one bucket held in shared memory (add mode)
-constexpr int kCapSet = 9216;             // ... (last-write mode or with the map: positions kept too)
+constexpr int kCapResolve = 28672;        // writes of one bucket sorted in shared memory (keys + order)
 constexpr int kSubBitsMax = 11;           // counting-sort digit inside a bucket: up to 2048 sub-bins
 constexpr int64_t kSampleTotal = 1 << 19; // samples drawn per call (spread over the matrices)
 constexpr int64_t kSampleMin = 256;       // at least this many per matrix (or all of its writes)
