@@ -313,7 +313,8 @@ def main():
     stage_ms = {k: statistics.mean(v) for k, v in stages.items()}
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": profiled_traffic(args.workload), "peak_kind": peak_kind,
-                "kernel": "spm_assemble_csc: the whole sync step (12 kernels), CUDA events around each call",
+                "kernel": f"spm_assemble_csc: the whole sync step ({launches // max(args.steps, 1)} kernel launches), "
+                          "CUDA events around each call",
                 "algorithmic_bytes_per_call": alg_bytes,
                 "bytes_formula": "m*(4+4+sv) + nnz*(4+sv) + (n_cols+1)*8",
                 "call_ms_mean": 1000 * mean_call_s, "stage_ms_mean": stage_ms}

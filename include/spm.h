@@ -234,19 +234,35 @@ spm_status spm_triplet_dvals(int64_t m, const int32_t* rows, const int32_t* cols
  * Tuning parameters of the assembly kernels (process-wide; the autotuner
  * sets them).  A call with NULL restores the defaults.  Changing them changes
  * the workspace size, so query the workspace after setting them.
- *   bucket_target      expected writes per bucket the planner aims for
- *                      (256 .. 8192)
- *   sub_bits           log2 of the counting-sort digit used inside a bucket
- *                      (8 .. 12)
- *   partition_threads  threads per block of the histogram/scatter kernels
- *                      (256, 512 or 1024)
- *   resolve_threads    threads per block of the per-bucket kernel (256 or 512)
+ *   bucket_target        expected writes per bucket the planner aims for
+ *                        (256 .. 114688); a bucket may hold up to twice the
+ *                        target, at most 28672, in shared memory -- larger
+ *                        buckets take a slower windowed path
+ *   sub_bits             log2 of the counting-sort digit used inside a bucket
+ *                        (8 .. 11)
+ *   partition_threads    threads per block of the histogram/scatter kernels
+ *                        (256, 512 or 1024)
+ *   resolve_threads      threads per block of the per-bucket kernel
+ *                        (256, 512 or 1024)
+ *   two_pass_min_writes  calls with at least this many writes (and no seq)
+ *                        move the writes to their buckets in two passes --
+ *                        first to about four groups of buckets per SM, then
+ *                        within each group -- which keeps the set of partly
+ *                        written cache lines small; the workspace then holds
+ *                        18 more bytes per write (>= 0)
+ *   two_pass_min_fronts  ... and only when the one-pass scatter would write
+ *                        to more than this many (partition block, bucket)
+ *                        pairs, counted on the device after the histogram;
+ *                        0 with two_pass_min_writes = 0 forces two passes
+ *                        (>= 0)
  */
 typedef struct {
   int32_t bucket_target;
   int32_t sub_bits;
   int32_t partition_threads;
   int32_t resolve_threads;
+  int32_t two_pass_min_writes;
+  int32_t two_pass_min_fronts;
 } spm_tuning;
 
 spm_status spm_set_tuning(const spm_tuning* t);

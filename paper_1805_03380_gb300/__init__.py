@@ -49,7 +49,8 @@ class SpmError(RuntimeError):
 
 class _Tuning(ctypes.Structure):
     _fields_ = [("bucket_target", ctypes.c_int32), ("sub_bits", ctypes.c_int32),
-                ("partition_threads", ctypes.c_int32), ("resolve_threads", ctypes.c_int32)]
+                ("partition_threads", ctypes.c_int32), ("resolve_threads", ctypes.c_int32),
+                ("two_pass_min_writes", ctypes.c_int32), ("two_pass_min_fronts", ctypes.c_int32)]
 
 
 _lib = None
@@ -193,13 +194,17 @@ def spm_triplet_dvals(rows, cols, map, dY, X, dvals, stream=None):
     _check(code, "spm_triplet_dvals")
 
 
-def spm_set_tuning(bucket_target=None, sub_bits=None, partition_threads=None, resolve_threads=None, reset=False):
+def spm_set_tuning(bucket_target=None, sub_bits=None, partition_threads=None, resolve_threads=None,
+                   two_pass_min_writes=None, two_pass_min_fronts=None, reset=False):
+    """Set the process-wide tuning (fields left as None keep their value); returns the new tuning."""
     if reset:
         _check(lib().spm_set_tuning(None), "spm_set_tuning")
         return spm_get_tuning()
     cur = spm_get_tuning()
-    t = _Tuning(bucket_target or cur["bucket_target"], sub_bits or cur["sub_bits"],
-                partition_threads or cur["partition_threads"], resolve_threads or cur["resolve_threads"])
+    new = dict(bucket_target=bucket_target, sub_bits=sub_bits, partition_threads=partition_threads,
+               resolve_threads=resolve_threads, two_pass_min_writes=two_pass_min_writes,
+               two_pass_min_fronts=two_pass_min_fronts)
+    t = _Tuning(*[cur[f] if new[f] is None else int(new[f]) for f, _ in _Tuning._fields_])
     _check(lib().spm_set_tuning(ctypes.byref(t)), "spm_set_tuning")
     return spm_get_tuning()
 

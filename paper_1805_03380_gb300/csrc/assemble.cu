@@ -129,6 +129,30 @@ __device__ __forceinline__ uint32_t isqrt_u32(uint32_t x) {
   return r;
 }
 
+// Division of 32-bit integers by an invariant divisor with a multiply and
+// shifts (Granlund and Montgomery, "Division by invariant integers using
+// multiplication", 1994, the round-up method of their Fig. 4.1): for
+// 1 <= d < 2^32 and l = ceil(log2 d), m = floor(2^32 (2^l - d) / d) + 1 and
+// n / d = (t + ((n - t) >> min(l, 1))) >> max(l - 1, 0), t = mulhi(m, n).
+struct Div32 {
+  uint32_t m, s1, s2;
+};
+
+__host__ __device__ inline Div32 div32_make(uint32_t d) {
+  int l = 0;
+  while ((uint64_t{1} << l) < (uint64_t)d) ++l;
+  Div32 r;
+  r.m = (uint32_t)(((uint64_t{1} << 32) * ((uint64_t{1} << l) - d)) / d + 1);
+  r.s1 = l < 1 ? (uint32_t)l : 1u;
+  r.s2 = l > 1 ? (uint32_t)(l - 1) : 0u;
+  return r;
+}
+
+__device__ __forceinline__ uint32_t div32(uint32_t n, const Div32& D) {
+  const uint32_t t = __umulhi(D.m, n);
+  return (t + ((n - t) >> D.s1)) >> D.s2;
+}
+
 // ===========================================================================
 // Setup: per-matrix metadata
 // ===========================================================================
@@ -548,6 +572,8 @@ __global__ void k_bucket_scan(Ctx c) {
   if (threadIdx.x == 0) {
     if (carry > (unsigned long long)c.nbcap_total) record_fatal(c, SPM_ERR_UNSUPPORTED);
     c.scal->NB = (uint32_t)carry;
+    const unsigned long long grp = (unsigned long long)max(c.groups, 1);
+    c.scal->G = (uint32_t)max(1ull, (carry + grp - 1) / grp);
   }
   __syncthreads();
   const MatMeta* meta = c.meta;
@@ -703,14 +729,13 @@ __device__ __forceinline__ void advance_view(const Ctx& c, const CtaInfo& ci, co
   }
 }
 
-// Shared-memory layout of the partition kernels: [counters | LUT slice].
-__device__ __forceinline__ void partition_prologue(const Ctx& c, const CtaInfo& ci, uint32_t* sm, bool& hist_smem,
+// Shared-memory layout of the partition kernels: [counters | LUT slice];
+// `counters` words (at most kHistCapSmem) precede the LUT slice.
+__device__ __forceinline__ void partition_prologue(const Ctx& c, const CtaInfo& ci, uint32_t* sm, int64_t counters,
                                                    bool& lut_smem, uint32_t*& lut_base) {
-  const int64_t range = (int64_t)ci.cb1 - (int64_t)ci.cb0;
   const int64_t lutn = ci.l1 - ci.l0;
-  hist_smem = range <= kHistCapSmem;
   lut_smem = lutn <= kLutCapSmem;
-  const int64_t hwords = hist_smem ? ((range + 3) & ~3ll) : 0;
+  const int64_t hwords = (counters + 3) & ~3ll;
   lut_base = sm + hwords;
   if (lut_smem) {
     // per matrix: its level-1 table and the level-2 tables it uses, packed
@@ -729,10 +754,11 @@ __global__ void __launch_bounds__(1024) k_hist(Ctx c) {
   extern __shared__ __align__(16) uint32_t sm[];
   const CtaInfo ci = c.cta[blockIdx.x];
   if (is_aborted(c) || ci.e0 >= ci.e1) return;
-  bool hist_smem, lut_smem;
+  bool lut_smem;
   uint32_t* lut_base;
-  partition_prologue(c, ci, sm, hist_smem, lut_smem, lut_base);
   const int64_t range = (int64_t)ci.cb1 - (int64_t)ci.cb0;
+  const bool hist_smem = range <= kHistCapSmem;
+  partition_prologue(c, ci, sm, hist_smem ? range : 0, lut_smem, lut_base);
   uint32_t* hist = hist_smem ? sm : (c.hist + ci.hoff);
   for (int64_t k = threadIdx.x; k < range; k += blockDim.x) hist[k] = 0u;
   __syncthreads();
@@ -803,7 +829,7 @@ __global__ void __launch_bounds__(256) k_colscan(Ctx c) {
     c.bk_count[b] = 0u;
     return;
   }
-  uint32_t running = 0;
+  uint32_t running = 0, fronts = 0;
   for (int c0 = 0; c0 < C; c0 += 8) {  // eight independent loads in flight
     uint32_t v[8];
     uint32_t* ptr[8];
@@ -825,10 +851,14 @@ __global__ void __launch_bounds__(256) k_colscan(Ctx c) {
       if (ptr[u]) {
         *ptr[u] = running;
         running += v[u];
+        fronts += v[u] != 0u ? 1u : 0u;
       }
     }
   }
   c.bk_count[b] = running;
+  const unsigned act = __activemask();
+  const uint32_t wsum = __reduce_add_sync(act, fronts);
+  if ((threadIdx.x & 31) == __ffs(act) - 1 && wsum) atomicAdd(&c.scal->fronts, (unsigned long long)wsum);
 }
 
 // Device-wide exclusive scan of bk_count into bk_start (three kernels).
@@ -863,15 +893,22 @@ __global__ void k_scan_down(Ctx c) {
   if (i < c.nbcap_total) c.bk_start[i] = off;
 }
 
+// The two-pass partition runs when the workspace has room for it and the
+// one-pass scatter would keep more write fronts open than L2 can hold.
+__device__ __forceinline__ bool two_pass_on(const Ctx& c) {
+  return c.two_pass != 0 && (int64_t)c.scal->fronts > c.min_fronts;
+}
+
 template <bool BATCHED, bool VEC, bool F64, bool SEQ>
 __global__ void __launch_bounds__(1024) k_scatter(Ctx c) {
   extern __shared__ __align__(16) uint32_t sm[];
   const CtaInfo ci = c.cta[blockIdx.x];
-  if (is_aborted(c) || ci.e0 >= ci.e1) return;
-  bool hist_smem, lut_smem;
+  if (is_aborted(c) || ci.e0 >= ci.e1 || two_pass_on(c)) return;
+  bool lut_smem;
   uint32_t* lut_base;
-  partition_prologue(c, ci, sm, hist_smem, lut_smem, lut_base);
   const int64_t range = (int64_t)ci.cb1 - (int64_t)ci.cb0;
+  const bool hist_smem = range <= kHistCapSmem;
+  partition_prologue(c, ci, sm, hist_smem ? range : 0, lut_smem, lut_base);
   uint32_t* cur = hist_smem ? sm : (c.hist + ci.hoff);
   for (int64_t k = threadIdx.x; k < range; k += blockDim.x)
     cur[k] = c.bk_start[ci.cb0 + k] + c.hist[ci.hoff + k];
@@ -886,8 +923,8 @@ __global__ void __launch_bounds__(1024) k_scatter(Ctx c) {
     advance_view<BATCHED>(c, ci, lut_base, lut_smem, t, v);
     uint32_t b, lk;
     if (classify(v, r, col, b, lk)) {
-      const uint32_t slot = atomicAdd(&cur[b], 1u);
       const uint64_t vb = (uint64_t)val;
+      const uint32_t slot = atomicAdd(&cur[b], 1u);
       // records are written a few at a time per bucket: ask L2 to keep the
       // partially written lines rather than the streamed inputs
       asm volatile("st.global.L2::cache_hint.v4.u32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(c.rec + slot), "r"(lk),
@@ -945,6 +982,263 @@ __global__ void __launch_bounds__(1024) k_scatter(Ctx c) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Two-pass partition.  Buckets are taken in groups of G consecutive buckets
+// (group g = buckets [g*G, (g+1)*G), about one group per SM); a group spans
+// the same slots of the temporary record array as of the final one.  Pass A
+// moves every write to its group, pass B moves the records of one group to
+// their buckets.  Both passes first sort each tile of kTileItems x blockDim
+// writes by destination in shared memory and then write the tile out in that
+// order, so that consecutive threads store to consecutive addresses and the
+// records leave as whole cache lines rather than one 16-byte piece per write.
+// The loads of the next tile are issued before the current one is sorted.
+// ---------------------------------------------------------------------------
+constexpr int kTileItems = 4;      // writes per thread per tile
+constexpr int kMaxGroupsA = 2048;  // groups one pass-A block may write to
+constexpr int kGroupMax = 1024;    // buckets per group, at most
+
+__host__ __device__ inline size_t part_a_smem_bytes(int threads) {
+  const size_t T = (size_t)kTileItems * threads;
+  return 16 * T + 2 * T + 2 * T + 4 * (3 * (size_t)kMaxGroupsA + 4) + 4 * (size_t)kLutCapSmem;
+}
+
+__host__ __device__ inline size_t part_b_smem_bytes(int threads) {
+  const size_t T = (size_t)kTileItems * threads;
+  return 16 * T + 2 * T + 4 * (3 * (size_t)kGroupMax + 4);
+}
+
+// start[0, nd] = exclusive prefix sums of cnt[0, nd) (start[nd] = total); ends
+// with a barrier.
+__device__ void tile_scan(const uint32_t* cnt, uint32_t* start, uint32_t nd, uint32_t* buf, uint32_t* tot) {
+  const uint32_t per = (nd + blockDim.x - 1) / blockDim.x;
+  const uint32_t a = min(nd, threadIdx.x * per), e = min(nd, a + per);
+  uint32_t local = 0;
+  for (uint32_t q = a; q < e; ++q) local += cnt[q];
+  uint32_t run = block_scan_excl<uint32_t>(local, tot, buf);
+  for (uint32_t q = a; q < e; ++q) {
+    start[q] = run;
+    run += cnt[q];
+  }
+  if (threadIdx.x == 0) start[nd] = *tot;
+  __syncthreads();
+}
+
+constexpr uint32_t kNoItem = 0xffffffffu;
+
+template <bool BATCHED, bool VEC, bool F64>
+__global__ void __launch_bounds__(1024) k_part_a(Ctx c) {
+  extern __shared__ __align__(16) uint32_t sm[];
+  __shared__ uint32_t s_buf[32], s_tot;
+  using VT = typename std::conditional<F64, uint64_t, uint32_t>::type;
+  const CtaInfo ci = c.cta[blockIdx.x];
+  if (is_aborted(c) || ci.e0 >= ci.e1 || !two_pass_on(c)) return;
+  const int tid = threadIdx.x, NT = blockDim.x;
+  const uint32_t T = kTileItems * NT;
+  const int64_t range = (int64_t)ci.cb1 - (int64_t)ci.cb0;
+  const uint32_t G = c.scal->G;
+  const Div32 dG = div32_make(G);
+  const uint32_t g0 = div32(ci.cb0, dG);
+  const uint32_t ngrp = div32(ci.cb1 - 1, dG) - g0 + 1;
+  if (ngrp > (uint32_t)kMaxGroupsA) {  // the host keeps the group count below this
+    if (tid == 0) record_fatal(c, SPM_ERR_UNSUPPORTED);
+    return;
+  }
+  uint4* stage = reinterpret_cast<uint4*>(sm);
+  uint16_t* dig = reinterpret_cast<uint16_t*>(stage + T);
+  uint16_t* sub = dig + T;
+  uint32_t* cnt = reinterpret_cast<uint32_t*>(sub + T);
+  uint32_t* start = cnt + kMaxGroupsA;
+  uint32_t* cur = start + kMaxGroupsA + 1;
+  bool lut_smem;
+  uint32_t* lut_base;
+  partition_prologue(c, ci, cur + kMaxGroupsA + 3, 0, lut_smem, lut_base);
+  // this block's first slot in each group: the writes of the group's buckets
+  // that come before its own (earlier matrices, earlier blocks)
+  for (uint32_t q = tid; q < ngrp; q += NT) cnt[q] = 0u;
+  __syncthreads();
+  for (int64_t k = tid; k < range; k += NT) atomicAdd(&cnt[div32(ci.cb0 + (uint32_t)k, dG) - g0], c.hist[ci.hoff + k]);
+  __syncthreads();
+  for (uint32_t q = tid; q < ngrp; q += NT) {
+    cur[q] = cnt[q] + c.bk_start[max((g0 + q) * G, ci.cb0)];
+    cnt[q] = 0u;
+  }
+  __syncthreads();
+  MatView v;
+  load_view(c, ci, lut_base, lut_smem, ci.i0, v);
+  const VT* vin = reinterpret_cast<const VT*>(c.vals);
+  auto tpos = [&](int64_t tb, int u) -> int64_t { return VEC ? tb + 4 * tid + u : tb + tid + (int64_t)u * NT; };
+  struct Raw {
+    int32_t r[kTileItems], cl[kTileItems];
+    VT x[kTileItems];
+  };
+  auto load_raw = [&](int64_t tb, Raw& R) {
+    const int64_t t0 = tb + 4 * tid;
+    if (VEC && t0 + 4 <= ci.e1) {
+      const int4 a = __ldcs(reinterpret_cast<const int4*>(c.rows + t0));
+      const int4 b = __ldcs(reinterpret_cast<const int4*>(c.cols + t0));
+      R.r[0] = a.x, R.r[1] = a.y, R.r[2] = a.z, R.r[3] = a.w;
+      R.cl[0] = b.x, R.cl[1] = b.y, R.cl[2] = b.z, R.cl[3] = b.w;
+      if (F64) {
+        const ulonglong2* vp = reinterpret_cast<const ulonglong2*>(vin + t0);
+        const ulonglong2 p = __ldcs(vp), q = __ldcs(vp + 1);
+        R.x[0] = (VT)p.x, R.x[1] = (VT)p.y, R.x[2] = (VT)q.x, R.x[3] = (VT)q.y;
+      } else {
+        const uint4 p = __ldcs(reinterpret_cast<const uint4*>(vin + t0));
+        R.x[0] = (VT)p.x, R.x[1] = (VT)p.y, R.x[2] = (VT)p.z, R.x[3] = (VT)p.w;
+      }
+    } else {
+#pragma unroll
+      for (int u = 0; u < kTileItems; ++u) {
+        const int64_t t = tpos(tb, u);
+        if (t < ci.e1) {
+          R.r[u] = __ldcs(c.rows + t);
+          R.cl[u] = __ldcs(c.cols + t);
+          R.x[u] = __ldcs(vin + t);
+        }
+      }
+    }
+  };
+  bool bad = false;
+  Raw R;
+  load_raw(ci.e0, R);
+  for (int64_t tb = ci.e0; tb < ci.e1; tb += T) {
+    uint32_t lk[kTileItems], sb[kTileItems], dr[kTileItems];
+    uint64_t vv[kTileItems];
+#pragma unroll
+    for (int u = 0; u < kTileItems; ++u) {
+      const int64_t t = tpos(tb, u);
+      dr[u] = kNoItem;
+      if (t < ci.e1) {
+        advance_view<BATCHED>(c, ci, lut_base, lut_smem, t, v);
+        uint32_t b;
+        if (classify(v, R.r[u], R.cl[u], b, lk[u])) {
+          const uint32_t bg = ci.cb0 + b;
+          const uint32_t grp = div32(bg, dG);
+          const uint32_t d = grp - g0;
+          dr[u] = (d << 16) | atomicAdd(&cnt[d], 1u);
+          sb[u] = bg - grp * G;
+          vv[u] = (uint64_t)R.x[u];
+        } else {
+          bad = true;
+        }
+      }
+    }
+    if (tb + T < ci.e1) load_raw(tb + T, R);  // next tile's loads overlap this tile's sort and stores
+    __syncthreads();
+    tile_scan(cnt, start, ngrp, s_buf, &s_tot);
+#pragma unroll
+    for (int u = 0; u < kTileItems; ++u) {
+      if (dr[u] != kNoItem) {
+        const uint32_t d = dr[u] >> 16;
+        const uint32_t p = start[d] + (dr[u] & 0xffffu);
+        stage[p] = make_uint4(lk[u], (uint32_t)tpos(tb, u), (uint32_t)vv[u], (uint32_t)(vv[u] >> 32));
+        dig[p] = (uint16_t)d;
+        sub[p] = (uint16_t)sb[u];
+      }
+    }
+    __syncthreads();
+    const uint32_t nt = start[ngrp];
+    uint4* tmp = reinterpret_cast<uint4*>(c.tmp);
+    for (uint32_t i = tid; i < nt; i += NT) {
+      const uint32_t d = dig[i];
+      const uint32_t g = cur[d] + (i - start[d]);
+      tmp[g] = stage[i];
+      c.rsub[g] = sub[i];
+    }
+    __syncthreads();
+    for (uint32_t q = tid; q < ngrp; q += NT) {
+      cur[q] += cnt[q];
+      cnt[q] = 0u;
+    }
+    __syncthreads();
+  }
+  if (bad) record_error(c, SPM_ERR_INDEX_OUT_OF_RANGE);
+}
+
+// Pass B: block g moves the records of bucket group g from tmp to their
+// buckets in rec.
+__global__ void __launch_bounds__(1024) k_part_b(Ctx c) {
+  extern __shared__ __align__(16) uint32_t sm[];
+  __shared__ uint32_t s_buf[32], s_tot;
+  if (is_aborted(c) || !two_pass_on(c)) return;
+  const int tid = threadIdx.x, NT = blockDim.x;
+  const uint32_t T = kTileItems * NT;
+  const uint32_t NB = c.scal->NB, G = c.scal->G;
+  const uint64_t b0 = (uint64_t)blockIdx.x * G;
+  if (G == 0 || b0 >= NB) return;
+  const uint32_t gn = (uint32_t)((uint64_t)G < (uint64_t)NB - b0 ? (uint64_t)G : (uint64_t)NB - b0);
+  if (gn > (uint32_t)kGroupMax) {
+    if (tid == 0) record_fatal(c, SPM_ERR_UNSUPPORTED);
+    return;
+  }
+  uint4* stage = reinterpret_cast<uint4*>(sm);
+  uint16_t* dig = reinterpret_cast<uint16_t*>(stage + T);
+  uint32_t* cnt = reinterpret_cast<uint32_t*>(dig + T);
+  uint32_t* start = cnt + kGroupMax;
+  uint32_t* cur = start + kGroupMax + 1;
+  for (uint32_t g = tid; g < gn; g += NT) {
+    cur[g] = c.bk_start[b0 + g];
+    cnt[g] = 0u;
+  }
+  const uint32_t lo = c.bk_start[b0];
+  const uint32_t hi = c.bk_start[b0 + gn - 1] + c.bk_count[b0 + gn - 1];
+  __syncthreads();
+  const uint4* src = reinterpret_cast<const uint4*>(c.tmp);
+  uint4* dst = reinterpret_cast<uint4*>(c.rec);
+  bool bad = false;
+  uint4 r[kTileItems];
+  uint32_t g[kTileItems];
+  auto load = [&](uint32_t tb) {
+#pragma unroll
+    for (int u = 0; u < kTileItems; ++u) {
+      const uint32_t k = tb + (uint32_t)u * NT + tid;
+      if (k < hi) {
+        r[u] = __ldcs(src + k);
+        g[u] = __ldcs(c.rsub + k);
+      }
+    }
+  };
+  load(lo);
+  for (uint32_t tb = lo; tb < hi; tb += T) {
+    uint4 rr[kTileItems];
+    uint32_t dr[kTileItems];
+#pragma unroll
+    for (int u = 0; u < kTileItems; ++u) {
+      dr[u] = kNoItem;
+      rr[u] = r[u];
+      if (tb + (uint32_t)u * NT + tid < hi) {
+        if (g[u] < gn) dr[u] = (g[u] << 16) | atomicAdd(&cnt[g[u]], 1u);
+        else bad = true;
+      }
+    }
+    if (tb + T < hi) load(tb + T);
+    __syncthreads();
+    tile_scan(cnt, start, gn, s_buf, &s_tot);
+#pragma unroll
+    for (int u = 0; u < kTileItems; ++u) {
+      if (dr[u] != kNoItem) {
+        const uint32_t d = dr[u] >> 16;
+        const uint32_t p = start[d] + (dr[u] & 0xffffu);
+        stage[p] = rr[u];
+        dig[p] = (uint16_t)d;
+      }
+    }
+    __syncthreads();
+    const uint32_t nt = start[gn];
+    for (uint32_t i = tid; i < nt; i += NT) {
+      const uint32_t d = dig[i];
+      dst[cur[d] + (i - start[d])] = stage[i];
+    }
+    __syncthreads();
+    for (uint32_t q = tid; q < gn; q += NT) {
+      cur[q] += cnt[q];
+      cnt[q] = 0u;
+    }
+    __syncthreads();
+  }
+  if (bad) record_fatal(c, SPM_ERR_CUDA);
+}
+
 // ===========================================================================
 // Resolve: one bucket at a time per block (persistent)
 // ===========================================================================
@@ -953,16 +1247,10 @@ __global__ void __launch_bounds__(1024) k_scatter(Ctx c) {
 // positions and results stay in the bucket's records (L2).  In window mode
 // the second half of the key array holds the record index of each key.
 struct RLayout {
-  size_t keys, perm, sub_a, sub_b, slots, total;
+  size_t keys, perm, sub_a, sub_b, total;
 };
 
-struct __align__(8) Slot {
-  uint64_t a, b;      // add mode: accumulator (lo, hi); last-write mode: seq, pos | idx << 32
-  uint32_t flags;     // add mode: NaN/Inf flags; last-write mode: 1 if a write is present
-  uint32_t has_head;  // the thread's range contains the start of a run (or is past the end)
-};
-
-__host__ __device__ inline RLayout resolve_layout(int cap, int nt, int sub_bits) {
+__host__ __device__ inline RLayout resolve_layout(int cap, int sub_bits) {
   RLayout L;
   size_t o = 0;
   auto take = [&](size_t bytes) {
@@ -974,7 +1262,6 @@ __host__ __device__ inline RLayout resolve_layout(int cap, int nt, int sub_bits)
   L.perm = take(2ull * cap);
   L.sub_a = take(4ull * ((size_t{1} << sub_bits) + 4));
   L.sub_b = take(4ull * (size_t{1} << sub_bits));
-  L.slots = take(sizeof(Slot) * (size_t)nt);
   L.total = o;
   return L;
 }
@@ -985,17 +1272,35 @@ struct RSmem {
   uint32_t* orig;   // window mode: record index of each key (else null: index = position)
   uint32_t* sub_a;
   uint32_t* sub_b;
-  Slot* slots;
+};
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kMaxWarps = 32;
+constexpr int kPartBytes = 80;
+
+// Per-warp exchange area of the reduction: a warp whose range of sorted
+// positions starts inside a run that began in an earlier warp's range parks
+// its part of that run here; the warp that holds the run's head merges it.
+struct WarpPart {
+  alignas(16) unsigned char part[kPartBytes];  // reduction state (Red<...>)
+  uint32_t ends;  // the run ends inside this warp's range (or there is no such run)
+  uint32_t fhp;   // sorted position of that run's head (set by the warp that owns it)
 };
 
 struct BlockShared {
-  uint64_t col0;
   uint32_t buf[32];
   uint32_t tot;
   uint32_t ticket;
   int64_t excl;
   uint32_t taken, cum, n_w;
   int32_t red_i[32];
+  // column arithmetic of the current bucket or window
+  uint64_t col0, r0;  // first key = col0 * n_rows + r0
+  Div32 dv;
+  uint32_t fastdiv;   // keys relative to col0 * n_rows fit 32 bits
+  uint32_t wkept[kMaxWarps];
+  int64_t wbase[kMaxWarps];
+  WarpPart wp[kMaxWarps];
 };
 
 // Wait (bounded) for the look-back chain of bucket b to provide its exclusive
@@ -1014,13 +1319,13 @@ __device__ int64_t lookback_wait_warp(const Ctx& c, int64_t b) {
     const int64_t bb = top - lane;
     const uint64_t s = bb >= 0 ? ld_acquire_u64(&c.bk_state[bb]) : kStIncl;
     const uint64_t flag = s & ~kStMask;
-    const unsigned incl = __ballot_sync(0xffffffffu, flag == kStIncl);
-    const unsigned none = __ballot_sync(0xffffffffu, flag == 0);
+    const unsigned incl = __ballot_sync(kFull, flag == kStIncl);
+    const unsigned none = __ballot_sync(kFull, flag == 0);
     const int first_incl = incl ? __ffs(incl) - 1 : 32;
-    const unsigned upto = first_incl >= 31 ? 0xffffffffu : ((2u << first_incl) - 1u);
+    const unsigned upto = first_incl >= 31 ? kFull : ((2u << first_incl) - 1u);
     if ((none & upto) == 0) {
       uint64_t v = (lane <= first_incl) ? (s & kStMask) : 0ull;
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
       excl += (int64_t)v;
       if (first_incl < 32) break;
       top -= 32;
@@ -1036,7 +1341,7 @@ __device__ int64_t lookback_wait_warp(const Ctx& c, int64_t b) {
         stop = 1;
       }
     }
-    if (__shfl_sync(0xffffffffu, stop, 0)) break;
+    if (__shfl_sync(kFull, stop, 0)) break;
   }
   return excl;
 }
@@ -1060,12 +1365,12 @@ __device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
 }
 
 __device__ __forceinline__ int block_max_int(int v, BlockShared& B) {
-  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(kFull, v, o));
   if ((threadIdx.x & 31) == 0) B.red_i[threadIdx.x >> 5] = v;
   __syncthreads();
   if (threadIdx.x < 32) {
     int x = threadIdx.x < (blockDim.x >> 5) ? B.red_i[threadIdx.x] : INT_MIN;
-    for (int o = 16; o > 0; o >>= 1) x = max(x, __shfl_xor_sync(0xffffffffu, x, o));
+    for (int o = 16; o > 0; o >>= 1) x = max(x, __shfl_xor_sync(kFull, x, o));
     if (threadIdx.x == 0) B.red_i[0] = x;
   }
   __syncthreads();
@@ -1081,32 +1386,49 @@ __device__ __forceinline__ bool bits_nonzero(uint64_t bits) {
   return F64 ? (bits & 0x7FFFFFFFFFFFFFFFull) != 0 : (bits & 0x7FFFFFFFull) != 0;
 }
 
-// Reduction state of one run (equal keys).  Add mode: the exact sum rounded
-// once -- a single write is its own value, two writes are one IEEE addition
-// (which rounds their exact sum), more writes go through the exact integer
-// accumulator.  Last-write mode: the write with the largest (seq, position).
+// Value field of a record: the write's value before the reduction, the
+// element's value (at the run's first record) after it.
+template <bool F64>
+__device__ __forceinline__ void store_val(uint4* recs, uint32_t r, uint64_t bits) {
+  uint32_t* p = reinterpret_cast<uint32_t*>(recs + r) + 2;
+  if (F64) {
+    *reinterpret_cast<uint64_t*>(p) = bits;
+  } else {
+    *p = (uint32_t)bits;
+  }
+}
+
+template <bool F64>
+__device__ __forceinline__ uint64_t load_val(const uint4* recs, uint32_t r) {
+  const uint32_t* p = reinterpret_cast<const uint32_t*>(recs + r) + 2;
+  if (F64) return __ldcg(reinterpret_cast<const unsigned long long*>(p));
+  return __ldcg(p);
+}
+
+// Reduction state of (part of) one run of equal keys.  Add mode: the exact
+// sum rounded once -- a single write is its own value, two writes are one
+// IEEE addition (which rounds their exact sum), more writes go through the
+// exact integer accumulator (acc is zero while cnt <= 2).  Last-write mode:
+// the write with the largest (seq, position).
 template <bool F64, bool SUM, bool SEQ>
 struct Red {
   Acc acc;
-  uint32_t cnt;
+  uint32_t cnt;       // add mode: writes so far, 3 = three or more
   uint64_t one, two;  // add mode: the first two values while cnt <= 2
   uint64_t seq, wval;
   uint32_t pos, idx;  // last-write mode: best write (idx = record index), ~0u = none
 
   __device__ __forceinline__ void clear() {
-    if (SUM) {
-      acc = acc_zero();
-      cnt = 0;
-      one = two = 0;
-    } else {
-      seq = 0;
-      wval = 0;
-      pos = 0;
-      idx = ~0u;
-    }
+    acc = acc_zero();
+    cnt = 0;
+    one = two = 0;
+    seq = 0;
+    wval = 0;
+    pos = 0;
+    idx = ~0u;
   }
   __device__ __forceinline__ static uint64_t wide(uint64_t v) { return F64 ? v : f32_bits_to_f64_bits(v); }
-  // Move the values held aside into the accumulator (cnt becomes >= 3).
+  // Move the values held aside into the accumulator (cnt becomes 3).
   __device__ __forceinline__ void spill(int emax) {
     if (cnt >= 1 && cnt <= 2) {
       acc_add_bits(acc, wide(one), emax);
@@ -1117,19 +1439,10 @@ struct Red {
   __device__ __forceinline__ bool better(uint64_t s2, uint32_t p2) const {
     return idx == ~0u || s2 > seq || (s2 == seq && p2 > pos);
   }
+  // One more write (add mode: only used with cnt == 3).
   __device__ __forceinline__ void add(const uint4& r, uint32_t ridx, const Ctx& c, int64_t seg_start, int emax) {
     if (SUM) {
-      const uint64_t v = rec_val(r);
-      if (cnt == 0) {
-        one = v;
-        cnt = 1;
-      } else if (cnt == 1) {
-        two = v;
-        cnt = 2;
-      } else {
-        spill(emax);
-        acc_add_bits(acc, wide(v), emax);
-      }
+      acc_add_bits(acc, wide(rec_val(r)), emax);
     } else {
       const uint64_t s2 = SEQ ? c.rs[seg_start + ridx] : 0ull;
       if (better(s2, r.y)) {
@@ -1140,37 +1453,52 @@ struct Red {
       }
     }
   }
-  // (the caller spills an add-mode state before merging)
-  __device__ __forceinline__ void merge(const Slot& o, const uint4* recs) {
+  __device__ __forceinline__ void merge(const Red& o, int emax) {
     if (SUM) {
-      Acc b{o.a, (int64_t)o.b, o.flags};
-      acc_merge(acc, b);
-      cnt = 3;
-    } else if (o.flags) {
-      const uint32_t p2 = (uint32_t)o.b, k2 = (uint32_t)(o.b >> 32);
-      if (better(o.a, p2)) {
-        seq = o.a;
-        pos = p2;
-        idx = k2;
-        wval = rec_val(recs[k2]);
+      if (o.cnt == 0) return;
+      if (cnt == 0) {
+        *this = o;
+        return;
       }
+      if (cnt == 1 && o.cnt == 1) {
+        two = o.one;
+        cnt = 2;
+        return;
+      }
+      Red t = o;
+      t.spill(emax);
+      spill(emax);
+      acc_merge(acc, t.acc);
+    } else if (o.idx != ~0u && better(o.seq, o.pos)) {
+      seq = o.seq;
+      pos = o.pos;
+      idx = o.idx;
+      wval = o.wval;
     }
   }
-  // Publishable state (add mode: everything in the accumulator).
-  __device__ __forceinline__ Slot to_slot(uint32_t has_head, int emax) {
-    Slot s;
+  template <class F>
+  __device__ __forceinline__ Red shuffled(F sh) const {
+    Red o;
     if (SUM) {
-      spill(emax);
-      s.a = acc.lo;
-      s.b = (uint64_t)acc.hi;
-      s.flags = acc.flags;
+      o.acc.lo = sh(acc.lo);
+      o.acc.hi = sh(acc.hi);
+      o.acc.flags = sh(acc.flags);
+      o.cnt = sh(cnt);
+      o.one = sh(one);
+      o.two = sh(two);
+      o.seq = o.wval = 0;
+      o.pos = 0;
+      o.idx = ~0u;
     } else {
-      s.a = seq;
-      s.b = (uint64_t)pos | ((uint64_t)idx << 32);
-      s.flags = idx != ~0u ? 1u : 0u;
+      o.acc = acc_zero();
+      o.cnt = 0;
+      o.one = o.two = 0;
+      o.seq = SEQ ? sh(seq) : 0ull;
+      o.wval = sh(wval);
+      o.pos = sh(pos);
+      o.idx = sh(idx);
     }
-    s.has_head = has_head;
-    return s;
+    return o;
   }
   // Final value bits of the element and whether it is stored.
   __device__ __forceinline__ uint64_t finish(int emax, bool& keep) const {
@@ -1197,28 +1525,55 @@ struct Red {
   }
 };
 
+// Column arithmetic of a bucket (or window) whose first key is klo; written
+// by thread 0, read after the next barrier.
+__device__ __forceinline__ void column_setup(BlockShared& B, const MatMeta& mm, uint64_t klo, uint64_t span) {
+  const uint64_t nr = (uint64_t)mm.n_rows;
+  B.col0 = klo / nr;
+  B.r0 = klo - B.col0 * nr;
+  B.fastdiv = (B.r0 + span + nr) < (uint64_t{1} << 32) ? 1u : 0u;
+  B.dv = div32_make((uint32_t)nr);
+}
+
+// floor(x / n_rows) for an offset x from col0 * n_rows
+__device__ __forceinline__ uint64_t col_div(const BlockShared& B, uint64_t x, uint64_t nr) {
+  return B.fastdiv ? (uint64_t)div32((uint32_t)x, B.dv) : x / nr;
+}
+
 // Process the n keys in shared memory (relative to klo, in [0, span)): sort
 // them, reduce each run of equal keys (values from the bucket's records),
 // drop zeros, and write the stored elements, the column offsets of every
 // column that starts inside [klo, klo + span) and the map.  The output
 // position of the first element comes from the look-back (bucket mode) or is
 // base_in (window mode).  Returns the number of stored elements.
+//
+// The reduction is warp-centric: each warp takes an equal range of sorted
+// positions and walks it 32 positions at a time, one per lane; run
+// boundaries come from neighbouring keys, sums and winners from segmented
+// warp scans.  A run that crosses a warp boundary is finished by the warp
+// holding its head, from the parts the following warps park.  Each result
+// is kept in the value field of its run's first record until the output
+// positions are known.
 template <bool F64, bool SUM, bool SEQ, bool POS>
 __device__ uint32_t resolve_records(const Ctx& c, const MatMeta& mm, int64_t b, uint64_t klo, uint64_t span,
                                     uint32_t n, const RSmem& S, BlockShared& B, bool window, int64_t base_in,
                                     int64_t seg_start, int emax) {
   using VT = typename std::conditional<F64, uint64_t, uint32_t>::type;
   using R = Red<F64, SUM, SEQ>;
-  const int tid = threadIdx.x, NT = blockDim.x;
+  static_assert(sizeof(R) <= kPartBytes, "reduction state too large");
+  const int tid = threadIdx.x, NT = blockDim.x, lane = tid & 31, w = tid >> 5, NW = NT >> 5;
   uint4* recs = reinterpret_cast<uint4*>(c.rec + seg_start);
-  if (tid == 0) B.col0 = klo / (uint64_t)mm.n_rows;  // visible after the next barrier
+  uint32_t* const keys = S.keys;
+  uint16_t* const perm = S.perm;
+  const uint32_t* const orig = S.orig;
+  if (tid == 0) column_setup(B, mm, klo, span);  // visible after the next barrier
   // ---- counting sort on the top key bits
   const int sbits = span <= 1 ? 0 : ceil_log2_u64(span);
   const int sshift = sbits > c.sub_bits ? sbits - c.sub_bits : 0;
   const uint32_t nsub = (uint32_t)(((span - 1) >> sshift) + 1);
   for (uint32_t q = tid; q <= nsub; q += NT) S.sub_a[q] = 0u;
   __syncthreads();
-  for (uint32_t k = tid; k < n; k += NT) atomicAdd(&S.sub_a[S.keys[k] >> sshift], 1u);
+  for (uint32_t k = tid; k < n; k += NT) atomicAdd(&S.sub_a[keys[k] >> sshift], 1u);
   __syncthreads();
   {
     const uint32_t per = (nsub + NT - 1) / NT;
@@ -1235,188 +1590,380 @@ __device__ uint32_t resolve_records(const Ctx& c, const MatMeta& mm, int64_t b, 
     if (tid == 0) S.sub_a[nsub] = n;
   }
   __syncthreads();
-  for (uint32_t k = tid; k < n; k += NT) S.perm[atomicAdd(&S.sub_b[S.keys[k] >> sshift], 1u)] = (uint16_t)k;
+  for (uint32_t k = tid; k < n; k += NT) perm[atomicAdd(&S.sub_b[keys[k] >> sshift], 1u)] = (uint16_t)k;
   __syncthreads();
   if (sshift > 0) {  // sub-bins hold several keys: order them by key
     const uint32_t sa = (uint32_t)(((uint64_t)tid * nsub) / NT), sb = (uint32_t)(((uint64_t)(tid + 1) * nsub) / NT);
     const uint32_t ea = S.sub_a[sa], eb = S.sub_a[sb];
     for (uint32_t x = ea + 1; x < eb; ++x) {
-      const uint16_t v = S.perm[x];
-      const uint32_t kv = S.keys[v];
+      const uint16_t v = perm[x];
+      const uint32_t kv = keys[v];
       uint32_t y = x;
-      while (y > ea && S.keys[S.perm[y - 1]] > kv) {
-        S.perm[y] = S.perm[y - 1];
+      while (y > ea && keys[perm[y - 1]] > kv) {
+        perm[y] = perm[y - 1];
         --y;
       }
-      S.perm[y] = v;
+      perm[y] = v;
     }
     __syncthreads();
   }
-  // ---- balanced ranges of sorted positions; runs may cross range boundaries
-  const uint32_t E = (n + NT - 1) / NT;
-  const uint32_t p0 = min(n, (uint32_t)tid * E), p1 = min(n, p0 + E);
-  auto key_at = [&](uint32_t p) -> uint32_t { return S.keys[S.perm[p]]; };
-  auto is_head = [&](uint32_t p) -> bool { return p == 0 || key_at(p) != key_at(p - 1); };
-  auto ridx_of = [&](uint32_t q) -> uint32_t { return S.orig ? S.orig[q] : q; };
-  R first, cur;
-  first.clear();
-  cur.clear();
-  bool owned = false, seen = false;
+  auto key_at = [&](uint32_t p) -> uint32_t { return keys[perm[p]]; };
+  auto ridx_of = [&](uint32_t q) -> uint32_t { return orig ? orig[q] : q; };
+
+  // ---- pass 1: reduce every run; results go to the runs' first records
+  const uint32_t E = ((n + NW - 1) / NW + 31) & ~31u;
+  const uint32_t s = min(n, (uint32_t)w * E), e = min(n, s + E);
+  const bool fstart = s > 0 && s < e && key_at(s) == key_at(s - 1);
+  R carry;  // the run open at the end of the previous chunk (identical in all lanes)
+  carry.clear();
+  R lred;   // this lane's share of the open run from chunks that lie entirely inside it
+  lred.clear();
+  if (SUM) lred.cnt = 3;
+  bool lred_used = false;
+  auto fold = [&]() {  // move the lanes' shares into the carry (uniform again)
+    if (!lred_used) return;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) lred.merge(lred.shuffled([&](auto x) { return __shfl_xor_sync(kFull, x, o); }), emax);
+    carry.merge(lred, emax);
+    lred.clear();
+    if (SUM) lred.cnt = 3;
+    lred_used = false;
+  };
+  bool open = fstart, foreign = fstart, parked = false;
+  uint32_t ckey = fstart ? key_at(s) : 0u;
+  uint32_t chp = 0, chr = 0;  // sorted position and record index of the open run's head
   uint32_t kept = 0;
-  uint32_t hp1 = 0;
-  uint32_t prev_key = p0 > 0 && p0 < n ? key_at(p0 - 1) : ~0u;
-  for (uint32_t pb = p0; pb < p1; pb += 4) {
-    // four records in flight per thread
-    uint4 rr[4];
-    uint32_t qq[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      if (pb + u < p1) {
-        qq[u] = S.perm[pb + u];
-        rr[u] = recs[ridx_of(qq[u])];
-      }
+  const bool map_lw = POS && !SUM && c.keep_map;
+
+  auto finish_run = [&](const R& r, uint32_t hr, uint32_t hp, bool multi) -> bool {
+    bool keep;
+    const uint64_t bits = r.finish(emax, keep);
+    if (multi) store_val<F64>(recs, hr, bits);  // a single write's record already holds it
+    // last-write map: the winner's stream position goes to the run's second record
+    if (map_lw && multi) reinterpret_cast<uint32_t*>(recs + ridx_of(perm[hp + 1]))[2] = r.pos;
+    return keep;
+  };
+
+  auto chunk = [&](uint32_t base, uint32_t key, uint32_t ridx, const uint4& rec, uint64_t sq) {
+    const uint32_t p = base + lane;
+    const bool valid = p < e;
+    const uint32_t pk = __shfl_up_sync(kFull, key, 1);
+    const bool head = valid && (lane == 0 ? !(open && key == ckey) : key != pk);
+    uint32_t nk = __shfl_down_sync(kFull, key, 1);
+    const bool more = p + 1 < n;
+    if (valid && (lane == 31 || p + 1 == e) && more) nk = key_at(p + 1);
+    const bool tail = valid && (!more || nk != key);
+    const unsigned vm = __ballot_sync(kFull, valid), hm = __ballot_sync(kFull, head), tm = __ballot_sync(kFull, tail);
+    if (hm == vm && tm == vm) {
+      // every write is an element of its own: its record already holds the result
+      kept += __popc(__ballot_sync(kFull, valid && bits_nonzero<F64>(F64 ? rec_val(rec) : (uint64_t)rec.z)));
+      open = foreign = false;
+      return;
     }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const uint32_t p = pb + u;
-      if (p >= p1) break;
-      const uint32_t kk = S.keys[qq[u]];
-      if (p == 0 || kk != prev_key) {
-        if (owned) {
-          // a complete run (head and end in this range): its result goes to
-          // the head's record for the write pass (only this thread touches it)
-          bool k2;
-          const uint64_t bits = cur.finish(emax, k2);
-          kept += k2 ? 1u : 0u;
-          if (!c.keep_map) recs[ridx_of(S.perm[hp1])].z = (uint32_t)bits, recs[ridx_of(S.perm[hp1])].w = (uint32_t)(bits >> 32);
-        } else if (p > p0) {
-          first = cur;
+    if (hm == 0 && tm == 0) {
+      // the whole chunk lies inside the open run: accumulate per lane
+      if (SUM && !lred_used) {
+        carry.spill(emax);
+        carry.cnt = 3;
+      }
+      if (valid) lred.add(rec, ridx, c, seg_start, emax);
+      lred_used = true;
+      return;
+    }
+    fold();
+    const int Lv = 31 - __clz(vm);
+    const unsigned hle = hm & (kFull >> (31 - lane));
+    const int hl = hle ? 31 - __clz(hle) : -1;  // head lane of my run, -1: it began before this chunk
+    const int seg0 = hl >= 0 ? hl : 0;
+    R r;
+    if (SUM) {
+      const uint64_t v = F64 ? rec_val(rec) : (uint64_t)rec.z;
+      uint64_t vp = __shfl_up_sync(kFull, v, 1);
+      if (lane == 0) vp = carry.one;
+      const uint32_t tot = hl >= 0 ? (uint32_t)(lane - hl + 1) : (uint32_t)lane + 1u + carry.cnt;
+      r.clear();
+      r.cnt = min(tot, 3u);
+      r.one = tot == 1 ? v : vp;
+      r.two = v;
+      if (__any_sync(kFull, valid && (tail || lane == Lv) && tot >= 3)) {
+        Acc a = acc_zero();
+        if (valid) acc_add_bits(a, R::wide(v), emax);
+        if (lane == 0 && hl < 0) {
+          R t = carry;
+          t.spill(emax);
+          acc_merge(a, t.acc);
         }
-        cur.clear();
-        owned = seen = true;
-        hp1 = p;
-      }
-      prev_key = kk;
-      cur.add(rr[u], ridx_of(qq[u]), c, seg_start, emax);
-    }
-  }
-  if (!seen) first = cur;
-  S.slots[tid] = first.to_slot((seen || p0 >= n) ? 1u : 0u, emax);
-  __syncthreads();
-  uint64_t open_bits = 0;
-  bool open_keep = false;
-  uint32_t open_win = ~0u;
-  if (seen) {  // the last run starting here may continue into the following ranges
-    for (int t2 = tid + 1; t2 < NT; ++t2) {
-      const Slot sl = S.slots[t2];
-      if (sl.has_head && !(sl.flags | sl.a | sl.b)) break;  // next range starts a run: nothing to add
-      if (SUM) cur.spill(emax);
-      cur.merge(sl, recs);
-      if (sl.has_head) break;
-    }
-    open_bits = cur.finish(emax, open_keep);
-    open_win = SUM ? 0u : cur.idx;
-    kept += open_keep ? 1u : 0u;
-  }
-  const uint32_t off = block_scan_excl<uint32_t>(kept, &B.tot, B.buf);
-  const uint32_t nnz = B.tot;
-  if (tid < 32) {
-    if (window) {
-      if (tid == 0) B.excl = base_in;
-    } else if (b == c.withhold) {
-      if (tid == 0) B.excl = 0;  // fault injection: publish nothing, wait for nothing
-    } else if (klo == 0) {
-      if (tid == 0) {
-        st_release_u64(&c.bk_state[b], kStIncl | (uint64_t)nnz);
-        B.excl = 0;
+        // segmented scan: as many steps as the longest run piece in the chunk needs
+        const uint32_t span_max = __reduce_max_sync(kFull, valid ? (uint32_t)(lane - seg0 + 1) : 0u);
+        if (__any_sync(kFull, a.flags != 0)) {
+          for (uint32_t o = 1; o < span_max; o <<= 1) {
+            const Acc y{__shfl_up_sync(kFull, a.lo, o), __shfl_up_sync(kFull, a.hi, o),
+                        __shfl_up_sync(kFull, a.flags, o)};
+            if (lane - (int)o >= seg0) acc_merge(a, y);
+          }
+        } else {
+          for (uint32_t o = 1; o < span_max; o <<= 1) {
+            const uint64_t lo2 = __shfl_up_sync(kFull, a.lo, o);
+            const int64_t hi2 = __shfl_up_sync(kFull, a.hi, o);
+            if (lane - (int)o >= seg0) acc_merge(a, Acc{lo2, hi2, 0u});
+          }
+        }
+        if (tot >= 3) r.acc = a;
       }
     } else {
-      const int64_t ex = lookback_warp(c, b, nnz);
-      if (tid == 0) B.excl = ex;
+      uint64_t bs = SEQ ? sq : 0ull;
+      uint32_t bp = rec.y;
+      int wl = lane;
+      if (lane == 0 && hl < 0 && carry.idx != ~0u && !(bs > carry.seq || (bs == carry.seq && bp > carry.pos))) {
+        bs = carry.seq;
+        bp = carry.pos;
+        wl = 32;
+      }
+      if (!(hm == vm && tm == vm)) {  // some run has more than one write
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint64_t bs2 = SEQ ? __shfl_up_sync(kFull, bs, o) : 0ull;
+          const uint32_t bp2 = __shfl_up_sync(kFull, bp, o);
+          const int wl2 = __shfl_up_sync(kFull, wl, o);
+          if (lane - o >= seg0 && (bs2 > bs || (bs2 == bs && bp2 > bp))) {
+            bs = bs2;
+            bp = bp2;
+            wl = wl2;
+          }
+        }
+      }
+      const uint64_t wv = __shfl_sync(kFull, rec_val(rec), wl & 31);
+      const uint32_t wr = __shfl_sync(kFull, ridx, wl & 31);
+      r.clear();
+      r.seq = bs;
+      r.pos = bp;
+      r.idx = wl == 32 ? carry.idx : wr;
+      r.wval = wl == 32 ? carry.wval : wv;
+    }
+    const uint32_t hr = __shfl_sync(kFull, ridx, seg0);
+    const bool fpark = tail && hl < 0 && foreign;
+    bool keep = false;
+    if (fpark) {
+      // the run began in an earlier warp's range: park this part of it
+      *reinterpret_cast<R*>(B.wp[w].part) = r;
+      B.wp[w].ends = 1u;
+    } else if (tail) {
+      keep = finish_run(r, hl >= 0 ? hr : chr, hl >= 0 ? base + hl : chp, hl != lane);
+    }
+    kept += __popc(__ballot_sync(kFull, keep));
+    if (__any_sync(kFull, fpark)) parked = true;
+    if ((tm >> Lv) & 1u) {
+      open = foreign = false;
+    } else {  // the last run continues: carry its state
+      carry = r.shuffled([&](auto x) { return __shfl_sync(kFull, x, Lv); });
+      ckey = __shfl_sync(kFull, key, Lv);
+      const int hlv = __shfl_sync(kFull, hl, Lv);
+      if (hlv >= 0) {
+        foreign = false;
+        chp = base + hlv;
+        chr = __shfl_sync(kFull, ridx, hlv);
+      }
+      open = true;
+    }
+  };
+
+  auto load = [&](uint32_t base, uint32_t& key, uint32_t& ridx, uint4& rec, uint64_t& sq) {
+    const uint32_t p = base + lane;
+    key = 0;
+    ridx = 0;
+    rec = make_uint4(0u, 0u, 0u, 0u);
+    sq = 0;
+    if (p < e) {
+      const uint32_t q = perm[p];
+      key = keys[q];
+      ridx = ridx_of(q);
+      rec = __ldcg(recs + ridx);
+      if (SEQ) sq = __ldcg(reinterpret_cast<const unsigned long long*>(c.rs + seg_start + ridx));
+    }
+  };
+
+  for (uint32_t base = s; base < e; base += 64) {  // two chunks in flight
+    uint32_t k0, k1, i0, i1;
+    uint4 r0, r1;
+    uint64_t q0, q1;
+    load(base, k0, i0, r0, q0);
+    const bool second = base + 32 < e;
+    if (second) load(base + 32, k1, i1, r1, q1);
+    chunk(base, k0, i0, r0, q0);
+    if (second) chunk(base + 32, k1, i1, r1, q1);
+  }
+  fold();
+  if (lane == 0 && !parked) {
+    R* pp = reinterpret_cast<R*>(B.wp[w].part);
+    if (open && foreign) {  // the whole range lies inside one run of an earlier warp
+      *pp = carry;
+      B.wp[w].ends = 0u;
+    } else {
+      pp->clear();
+      B.wp[w].ends = 1u;
     }
   }
   __syncthreads();
-  // ---- write, walking the runs this thread owns (those starting in its range)
-  int64_t idx = B.excl + off;
+  if (open && !foreign) {  // my last run continues into the following ranges
+    bool keep = false;
+    if (lane == 0) {
+      R r = carry;
+      for (int w2 = w + 1; w2 < NW; ++w2) {
+        WarpPart& wp = B.wp[w2];
+        r.merge(*reinterpret_cast<const R*>(wp.part), emax);
+        wp.fhp = chp;
+        if (wp.ends) break;
+      }
+      keep = finish_run(r, chr, chp, true);
+    }
+    kept += __shfl_sync(kFull, keep ? 1u : 0u, 0);
+  }
+  if (lane == 0) B.wkept[w] = kept;
+  __syncthreads();
+  if (w == 0) {
+    const uint32_t x = lane < NW ? B.wkept[lane] : 0u;
+    uint32_t inc = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(kFull, inc, o);
+      if (lane >= o) inc += y;
+    }
+    const uint32_t nnz = __shfl_sync(kFull, inc, 31);
+    int64_t ex;
+    if (window) {
+      ex = base_in;
+    } else if (b == c.withhold) {
+      ex = 0;  // fault injection: publish nothing, wait for nothing
+    } else if (klo == 0) {
+      if (lane == 0) st_release_u64(&c.bk_state[b], kStIncl | (uint64_t)nnz);
+      ex = 0;
+    } else {
+      ex = lookback_warp(c, b, nnz);
+    }
+    if (lane < NW) B.wbase[lane] = ex + (int64_t)(inc - x);
+    if (lane == 0) {
+      B.tot = nnz;
+      B.excl = ex;
+    }
+  }
+  __syncthreads();
+  const uint32_t nnz = B.tot;
+
+  // ---- pass 2: write the elements of the runs whose heads lie in my range,
+  // and the offsets of the columns that start in my range of keys
+  int64_t idx = B.wbase[w];
   const uint64_t nr = (uint64_t)mm.n_rows;
-  auto range_start = [&](uint32_t p) -> uint64_t {  // first key owned by the range starting at p
+  const uint64_t col0 = B.col0, r0 = B.r0;
+  auto own_from = [&](uint32_t p) -> uint64_t {  // first key owned by the range starting at position p
     if (p >= n) return span;
-    return (uint64_t)key_at(p) + (is_head(p) ? 0u : 1u);
+    const uint32_t k = key_at(p);
+    return (p > 0 && key_at(p - 1) == k) ? (uint64_t)k + 1 : (uint64_t)k;
   };
-  const uint64_t gstart = klo + (tid == 0 ? 0ull : range_start(p0));
-  const uint64_t gend = klo + range_start(p1);
-  // first column whose start key lies in this thread's range; the bucket's
-  // first column c0 is computed once per bucket
-  const uint64_t c0 = B.col0, d0 = gstart - c0 * nr;
-  uint64_t j = c0 + ((d0 >> 32) == 0 && (nr >> 32) == 0 ? (uint64_t)(((uint32_t)d0 + (uint32_t)nr - 1u) / (uint32_t)nr)
-                                                        : (d0 + nr - 1) / nr);
-  uint64_t next_start = j * nr;
+  const uint64_t ks = w == 0 ? 0ull : own_from(s);
+  const uint64_t ke = own_from(e);
+  uint64_t jn = col0 + col_div(B, r0 + ks + nr - 1, nr);  // first column starting at or after klo + ks
+  const uint64_t je = col0 + col_div(B, r0 + ke + nr - 1, nr);
   int64_t* colp = c.col_ptr + mm.col_base;
   int32_t* rowp = c.row_idx + mm.t0;
   VT* outp = reinterpret_cast<VT*>(c.out_vals) + mm.t0;
-  auto emit = [&](uint32_t hp, uint32_t end_p, uint64_t bits, bool keep, uint32_t win) {
-    const uint64_t key = klo + key_at(hp);
-    int32_t slot = -2;
-    if (keep) {
-      while (next_start <= key) {
-        colp[j] = idx;
-        ++j;
-        next_start += nr;
+  const bool mapping = POS && c.keep_map;
+  int64_t mout = -2;  // map: output index of the run continuing from the previous chunk (-2: not stored)
+  uint32_t mwin = 0;  // map, last-write mode: stream position of that run's winner
+  if (mapping && fstart) {
+    const uint32_t hp = B.wp[w].fhp;
+    const uint64_t hb = load_val<F64>(recs, ridx_of(perm[hp]));
+    mout = bits_nonzero<F64>(hb) ? idx - 1 : -2;
+    if (!SUM) mwin = __ldcg(reinterpret_cast<const uint32_t*>(recs + ridx_of(perm[hp + 1])) + 2);
+  }
+  uint32_t pkey = fstart ? key_at(s) : 0u;
+  bool popen = fstart;
+  for (uint32_t base0 = s; base0 < e; base0 += 64) {
+    // two chunks at a time: both chunks' shared-memory and L2 loads are in
+    // flight before either is written out
+    uint32_t keyv[2], ridxv[2], posv[2];
+    bool validv[2], headv[2];
+    uint64_t bitsv[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const uint32_t p = base0 + 32 * h + lane;
+      validv[h] = p < e;
+      keyv[h] = 0;
+      ridxv[h] = 0;
+      if (validv[h]) {
+        const uint32_t q = perm[p];
+        keyv[h] = keys[q];
+        ridxv[h] = ridx_of(q);
       }
-      rowp[idx] = (int32_t)(key - (j - 1) * nr);
-      outp[idx] = (VT)bits;
-      slot = (int32_t)idx;
-      ++idx;
     }
-    if (POS && c.keep_map) {
-      for (uint32_t x = hp; x < end_p; ++x) {
-        const uint32_t rk = ridx_of(S.perm[x]);
-        c.map[recs[rk].y] = (!SUM && rk != win) ? -1 : slot;
-      }
-    }
-  };
-  owned = false;
-  uint32_t hp = 0;
-  if (!c.keep_map) {
-    // results of complete runs were stored in pass 1
-    for (uint32_t p = p0; p < p1; ++p) {
-      if (is_head(p)) {
-        if (owned) {
-          const uint64_t r = rec_val(recs[ridx_of(S.perm[hp])]);
-          emit(hp, p, r, bits_nonzero<F64>(r), 0u);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const uint32_t pk = __shfl_up_sync(kFull, keyv[h], 1);
+      const uint32_t prev_last = h == 0 ? pkey : __shfl_sync(kFull, keyv[0], 31);
+      const bool prev_open = h == 0 ? popen : true;
+      headv[h] = validv[h] && (lane == 0 ? !(prev_open && keyv[h] == prev_last) : keyv[h] != pk);
+      bitsv[h] = 0;
+      posv[h] = 0;
+      if (mapping) {
+        if (validv[h]) {
+          const uint4 rr = __ldcg(recs + ridxv[h]);
+          posv[h] = rr.y;
+          bitsv[h] = F64 ? rec_val(rr) : (uint64_t)rr.z;
         }
-        owned = true;
-        hp = p;
+      } else if (headv[h]) {
+        bitsv[h] = load_val<F64>(recs, ridxv[h]);
       }
     }
-  } else {
-    for (uint32_t p = p0; p < p1; ++p) {
-      if (is_head(p)) {
-        if (owned) {
-          bool k2;
-          const uint64_t bits = cur.finish(emax, k2);
-          emit(hp, p, bits, k2, SUM ? 0u : cur.idx);
-        }
-        cur.clear();
-        owned = true;
-        hp = p;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const uint32_t base = base0 + 32 * h;
+      if (base >= e) break;
+      const uint32_t p = base + lane;
+      const bool valid = validv[h], head = headv[h];
+      const uint32_t key = keyv[h], mypos = posv[h];
+      const uint64_t bits = bitsv[h];
+      const bool keep = head && bits_nonzero<F64>(bits);
+      const unsigned km = __ballot_sync(kFull, keep);
+      const unsigned lt = km & ((1u << lane) - 1u);
+      const int64_t i = idx + __popc(lt);
+      uint64_t col = 0;
+      if (keep) {
+        const uint64_t x = r0 + key;
+        const uint64_t cr = col_div(B, x, nr);
+        col = col0 + cr;
+        rowp[i] = (int32_t)(x - cr * nr);
+        outp[i] = (VT)bits;
       }
-      if (owned) {
-        const uint32_t q = S.perm[p];
-        cur.add(recs[ridx_of(q)], ridx_of(q), c, seg_start, emax);
+      const uint64_t pc = __shfl_sync(kFull, col, lt ? 31 - __clz(lt) : 0);
+      if (keep)
+        for (uint64_t j = lt ? pc + 1 : jn; j <= col; ++j) colp[j] = i;
+      if (mapping) {
+        uint32_t nk = __shfl_down_sync(kFull, key, 1);
+        if (valid && (lane == 31 || p + 1 == e) && p + 1 < n) nk = key_at(p + 1);
+        const bool multi = p + 1 < n && nk == key;
+        int64_t hout = keep ? i : -2;
+        uint32_t hwin = mypos;
+        if (!SUM && head && multi) hwin = __ldcg(reinterpret_cast<const uint32_t*>(recs + ridx_of(perm[p + 1])) + 2);
+        const unsigned hm = __ballot_sync(kFull, head);
+        const unsigned hle = hm & (kFull >> (31 - lane));
+        const int hl = hle ? 31 - __clz(hle) : -1;
+        const int64_t o2 = __shfl_sync(kFull, hout, hl >= 0 ? hl : 0);
+        const uint32_t w2 = __shfl_sync(kFull, hwin, hl >= 0 ? hl : 0);
+        const int64_t out = hl >= 0 ? o2 : mout;
+        const uint32_t win = hl >= 0 ? w2 : mwin;
+        if (valid) c.map[mypos] = (!SUM && mypos != win) ? -1 : (int32_t)out;
+        const int Lv = 31 - __clz(__ballot_sync(kFull, valid));
+        mout = __shfl_sync(kFull, out, Lv);
+        mwin = __shfl_sync(kFull, win, Lv);
+      }
+      if (km) {
+        jn = __shfl_sync(kFull, col, 31 - __clz(km)) + 1;
+        idx += __popc(km);
       }
     }
+    pkey = __shfl_sync(kFull, keyv[1], 31);  // only read when a later pair exists (then chunk 1 is full)
+    popen = true;
   }
-  if (owned) {
-    uint32_t end_p = p1;
-    if (c.keep_map) while (end_p < n && !is_head(end_p)) ++end_p;
-    emit(hp, end_p, open_bits, open_keep, open_win);
-  }
-  while (next_start < gend) {
-    colp[j] = idx;
-    ++j;
-    next_start += nr;
-  }
+  for (uint64_t j = jn + lane; j < je; j += 32) colp[j] = idx;
   __syncthreads();
   return nnz;
 }
@@ -1425,10 +1972,10 @@ __device__ uint32_t resolve_records(const Ctx& c, const MatMeta& mm, int64_t b, 
 // reduction over its records in global memory.
 template <bool F64, bool SUM, bool SEQ, bool POS>
 __device__ uint32_t resolve_single_key(const Ctx& c, const MatMeta& mm, uint64_t key, uint32_t lkey, int64_t start,
-                                       uint32_t n, const RSmem& S, BlockShared& B, int64_t base) {
+                                       uint32_t n, BlockShared& B, int64_t base) {
   using VT = typename std::conditional<F64, uint64_t, uint32_t>::type;
   using R = Red<F64, SUM, SEQ>;
-  const int tid = threadIdx.x, NT = blockDim.x;
+  const int tid = threadIdx.x, NT = blockDim.x, lane = tid & 31, w = tid >> 5, NW = NT >> 5;
   const uint4* recs = reinterpret_cast<const uint4*>(c.rec + start);
   int emax = 1;
   if (SUM) {
@@ -1442,19 +1989,20 @@ __device__ uint32_t resolve_single_key(const Ctx& c, const MatMeta& mm, uint64_t
   }
   R st;
   st.clear();
+  if (SUM) st.cnt = 3;  // everything goes to the accumulator
   for (uint32_t k = tid; k < n; k += NT) {
     const uint4 r = recs[k];
     if (r.x == lkey) st.add(r, k, c, start, emax);
   }
-  S.slots[tid] = st.to_slot(0u, emax);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) st.merge(st.shuffled([&](auto x) { return __shfl_xor_sync(kFull, x, o); }), emax);
+  if (lane == 0) *reinterpret_cast<R*>(B.wp[w].part) = st;
   __syncthreads();
   __shared__ uint64_t s_bits;
   __shared__ uint32_t s_keep, s_win;
   if (tid == 0) {
-    R all;
-    all.clear();
-    if (SUM) all.cnt = 3;
-    for (int t2 = 0; t2 < NT; ++t2) all.merge(S.slots[t2], recs);
+    R all = *reinterpret_cast<const R*>(B.wp[0].part);
+    for (int w2 = 1; w2 < NW; ++w2) all.merge(*reinterpret_cast<const R*>(B.wp[w2].part), emax);
     bool keep;
     const uint64_t bits = all.finish(emax, keep);
     s_bits = bits;
@@ -1487,14 +2035,13 @@ __global__ void __launch_bounds__(1024) k_resolve(Ctx c) {
   __shared__ BlockShared B;
   __shared__ MatMeta mm;
   const int tid = threadIdx.x, NT = blockDim.x;
-  const RLayout RL = resolve_layout(c.cap, NT, c.sub_bits);
+  const RLayout RL = resolve_layout(c.cap, c.sub_bits);
   RSmem S;
   S.keys = reinterpret_cast<uint32_t*>(smraw + RL.keys);
   S.perm = reinterpret_cast<uint16_t*>(smraw + RL.perm);
   S.orig = nullptr;
   S.sub_a = reinterpret_cast<uint32_t*>(smraw + RL.sub_a);
   S.sub_b = reinterpret_cast<uint32_t*>(smraw + RL.sub_b);
-  S.slots = reinterpret_cast<Slot*>(smraw + RL.slots);
   const uint32_t NB = c.scal->NB;
   const uint32_t cap = (uint32_t)c.cap;
   const uint32_t capw = cap / 2;  // window mode: keys in the first half, record indices in the second
@@ -1622,7 +2169,7 @@ __global__ void __launch_bounds__(1024) k_resolve(Ctx c) {
                                                       emax);
           wlo = whi;
         } else {
-          base += resolve_single_key<F64, SUM, SEQ, POS>(c, mm, klo + wlo, (uint32_t)wlo, start, n, S, B, base);
+          base += resolve_single_key<F64, SUM, SEQ, POS>(c, mm, klo + wlo, (uint32_t)wlo, start, n, B, base);
           wlo = wlo + 1;
         }
         __syncthreads();
@@ -1654,7 +2201,8 @@ __global__ void __launch_bounds__(1024) k_resolve(Ctx c) {
 // ===========================================================================
 namespace {
 
-spm_tuning g_tuning = {14336, 11, 1024, 1024};
+constexpr spm_tuning kDefaultTuning = {6144, 11, 1024, 512, 1 << 22, 1 << 19};
+spm_tuning g_tuning = kDefaultTuning;
 int64_t g_withhold = -1;
 std::mutex g_mutex;
 
@@ -1699,16 +2247,25 @@ ModeParams mode_params(spm_mode mode, uint32_t flags, const spm_tuning& tun) {
   const bool sum = mode == SPM_MODE_SUM;
   p.pos = !sum || (flags & SPM_KEEP_MAP) != 0;
   p.seq = !sum && (flags & SPM_SEQ_EXPLICIT) != 0;
-  p.cap = kCapResolve;
   p.tgt = std::max<int64_t>(256, (int64_t)tun.bucket_target);
+  // room for twice the target (the planner's estimates are sampled), at
+  // most what fits in shared memory
+  p.cap = (int)std::min<int64_t>(kCapResolve, std::max<int64_t>(1024, 2 * p.tgt) & ~int64_t{15});
   return p;
 }
 
 size_t resolve_smem_bytes(const ModeParams& mp, int threads, int sub_bits) {
-  return resolve_layout(mp.cap, threads, sub_bits).total;
+  (void)threads;
+  return resolve_layout(mp.cap, sub_bits).total;
 }
 
 size_t partition_smem_bytes() { return (size_t)(kHistCapSmem + kLutCapSmem) * 4; }
+
+// Bucket groups of the two-pass partition: one per SM, or more when needed
+// to keep at most kGroupMax buckets in a group.
+int64_t two_pass_groups(int sms, int64_t nbcap_total) {
+  return std::max<int64_t>((int64_t)sms, (nbcap_total + kGroupMax - 1) / kGroupMax);
+}
 
 template <typename K>
 void set_smem_attr(K kernel, size_t bytes) {
@@ -1740,7 +2297,7 @@ spm_status device_init(int& dev, DevState*& ds) {
 #undef SPM_SET_SCATTER
   {
     // the largest layout (1024 threads, the widest digit)
-    const size_t r = resolve_layout(kCapResolve, 1024, kSubBitsMax).total;
+    const size_t r = resolve_layout(kCapResolve, kSubBitsMax).total;
     set_smem_attr(k_resolve<false, true, false, false>, r);
     set_smem_attr(k_resolve<true, true, false, false>, r);
     set_smem_attr(k_resolve<false, true, false, true>, r);
@@ -1750,6 +2307,15 @@ spm_status device_init(int& dev, DevState*& ds) {
     set_smem_attr(k_resolve<false, false, true, true>, r);
     set_smem_attr(k_resolve<true, false, true, true>, r);
     set_smem_attr(k_plan, kPlanSmem);
+    set_smem_attr(k_part_b, part_b_smem_bytes(1024));
+    set_smem_attr(k_part_a<false, false, false>, part_a_smem_bytes(1024));
+    set_smem_attr(k_part_a<false, false, true>, part_a_smem_bytes(1024));
+    set_smem_attr(k_part_a<false, true, false>, part_a_smem_bytes(1024));
+    set_smem_attr(k_part_a<false, true, true>, part_a_smem_bytes(1024));
+    set_smem_attr(k_part_a<true, false, false>, part_a_smem_bytes(1024));
+    set_smem_attr(k_part_a<true, false, true>, part_a_smem_bytes(1024));
+    set_smem_attr(k_part_a<true, true, false>, part_a_smem_bytes(1024));
+    set_smem_attr(k_part_a<true, true, true>, part_a_smem_bytes(1024));
   }
   if (cudaGetLastError() != cudaSuccess) return SPM_ERR_CUDA;
   ds->sms = sms;
@@ -1776,7 +2342,7 @@ struct HostPlan {
 
 // Validate the sizes and compute the workspace layout.
 spm_status host_plan(int64_t B, const int64_t* h_nr, const int64_t* h_nc, const int64_t* h_tp, int sv, bool seq,
-                     int64_t tgt, int C, HostPlan& hp) {
+                     int64_t tgt, int C, int64_t two_pass_min, HostPlan& hp) {
   if (B < 0 || (B > 0 && (!h_nr || !h_nc || !h_tp))) return SPM_ERR_INVALID_ARG;
   if (B >= (int64_t{1} << 26)) return SPM_ERR_UNSUPPORTED;
   if (B > 0 && h_tp[0] != 0) return SPM_ERR_INVALID_ARG;
@@ -1865,6 +2431,9 @@ spm_status host_plan(int64_t B, const int64_t* h_nr, const int64_t* h_nc, const 
   L.hist = take(4 * (size_t)std::max<int64_t>(hist, 1));
   L.rec = take(sizeof(Rec) * (size_t)(m_total + 4));
   L.rs = seq ? take(8 * (size_t)(m_total + 4)) : o;
+  L.two_pass = !seq && m_total > 0 && m_total >= two_pass_min && two_pass_groups(C, nbcap) <= kMaxGroupsA;
+  L.tmp = L.two_pass ? take(sizeof(Rec) * (size_t)(m_total + 4)) : o;
+  L.rsub = L.two_pass ? take(2 * (size_t)(m_total + 4)) : o;
   L.total = o;
   return SPM_OK;
 }
@@ -1881,8 +2450,19 @@ void launch_partition(const Ctx& ctx, const Layout& L, bool vec, cudaStream_t st
   k_scan_top<<<1, 1024, 0, st>>>(ctx, L.scan_blocks);
   k_scan_down<<<(unsigned)L.scan_blocks, kScanBlock, 0, st>>>(ctx);
   stage_mark(st, call, 3);
-#define SPM_SCATTER(VE, F6, SQ) k_scatter<BATCHED, VE, F6, SQ><<<C, threads, ps, st>>>(ctx)
   const bool f64 = ctx.f64 != 0, sq = ctx.has_seq != 0;
+  if (ctx.two_pass) {  // (the device picks one of the two paths; the other's blocks return at once)
+    const size_t pa = part_a_smem_bytes(threads);
+    if (vec) {
+      if (f64) k_part_a<BATCHED, true, true><<<C, threads, pa, st>>>(ctx);
+      else k_part_a<BATCHED, true, false><<<C, threads, pa, st>>>(ctx);
+    } else {
+      if (f64) k_part_a<BATCHED, false, true><<<C, threads, pa, st>>>(ctx);
+      else k_part_a<BATCHED, false, false><<<C, threads, pa, st>>>(ctx);
+    }
+    k_part_b<<<(unsigned)ctx.groups, threads, part_b_smem_bytes(threads), st>>>(ctx);
+  }
+#define SPM_SCATTER(VE, F6, SQ) k_scatter<BATCHED, VE, F6, SQ><<<C, threads, ps, st>>>(ctx)
   if (vec) {
     if (f64) { if (sq) SPM_SCATTER(true, true, true); else SPM_SCATTER(true, true, false); }
     else { if (sq) SPM_SCATTER(true, false, true); else SPM_SCATTER(true, false, false); }
@@ -1894,10 +2474,21 @@ void launch_partition(const Ctx& ctx, const Layout& L, bool vec, cudaStream_t st
   stage_mark(st, call, 4);
 }
 
+// Persistent grid: as many blocks as fit on the SMs at once.
+template <typename K>
+int resident_grid(K kernel, int sms, int threads, size_t smem) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess || per_sm < 1) {
+    cudaGetLastError();
+    per_sm = 1;
+  }
+  return sms * per_sm;
+}
+
 void launch_resolve(const Ctx& ctx, const ModeParams& mp, int sms, cudaStream_t st, int threads) {
   const size_t rs = resolve_smem_bytes(mp, threads, ctx.sub_bits);
-  const int grid = sms * (rs <= 110 * 1024 ? 2 : 1);
-#define SPM_RES(F6, SU, SQ, PO) k_resolve<F6, SU, SQ, PO><<<grid, threads, rs, st>>>(ctx)
+#define SPM_RES(F6, SU, SQ, PO) \
+  k_resolve<F6, SU, SQ, PO><<<resident_grid(k_resolve<F6, SU, SQ, PO>, sms, threads, rs), threads, rs, st>>>(ctx)
   if (ctx.f64) {
     if (ctx.sum_mode) { if (mp.pos) SPM_RES(true, true, false, true); else SPM_RES(true, true, false, false); }
     else { if (mp.seq) SPM_RES(true, false, true, true); else SPM_RES(true, false, false, true); }
@@ -1935,7 +2526,7 @@ spm_status run_assembly(int64_t B, const int64_t* h_nr, const int64_t* h_nc, con
   const int sv = dtype == SPM_F64 ? 8 : 4;
   const ModeParams mp = mode_params(mode, flags, tun);
   HostPlan hp;
-  s = host_plan(B, h_nr, h_nc, h_tp, sv, mp.seq, mp.tgt, ds->sms, hp);
+  s = host_plan(B, h_nr, h_nc, h_tp, sv, mp.seq, mp.tgt, ds->sms, tun.two_pass_min_writes, hp);
   if (s != SPM_OK) return s;
   const Layout& L = hp.L;
   if (L.m_total > 0 && (!rows || !cols || !vals || !row_idx || !out_vals)) return SPM_ERR_INVALID_ARG;
@@ -1971,6 +2562,11 @@ spm_status run_assembly(int64_t B, const int64_t* h_nr, const int64_t* h_nc, con
   ctx.hist = reinterpret_cast<uint32_t*>(ws + L.hist);
   ctx.rec = reinterpret_cast<Rec*>(ws + L.rec);
   ctx.rs = mp.seq ? reinterpret_cast<uint64_t*>(ws + L.rs) : nullptr;
+  ctx.two_pass = L.two_pass ? 1 : 0;
+  ctx.tmp = L.two_pass ? reinterpret_cast<Rec*>(ws + L.tmp) : nullptr;
+  ctx.rsub = L.two_pass ? reinterpret_cast<uint16_t*>(ws + L.rsub) : nullptr;
+  ctx.groups = (int32_t)two_pass_groups(ds->sms, L.nbcap_total);
+  ctx.min_fronts = tun.two_pass_min_fronts;
   ctx.B = L.B;
   ctx.m_total = L.m_total;
   ctx.S_total = L.S_total;
@@ -2021,7 +2617,8 @@ spm_status run_assembly(int64_t B, const int64_t* h_nr, const int64_t* h_nc, con
   else launch_partition<false>(ctx, L, vec, st, tun.partition_threads, call);
   launch_resolve(ctx, mp, ds->sms, st, tun.resolve_threads);
   stage_mark(st, call, 5);
-  g_launches += 11 + (L.S_total > 0 ? 1 : 0);  // setup, plan, 2 bucket kernels, 6 partition, resolve
+  // setup, plan, 2 bucket kernels, 6 partition (with room for two passes: 8), resolve
+  g_launches += 11 + (L.S_total > 0 ? 1 : 0) + (L.two_pass ? 2 : 0);
   if (cudaGetLastError() != cudaSuccess) return SPM_ERR_CUDA;
   return SPM_OK;
 }
@@ -2054,15 +2651,16 @@ int32_t spm_version(void) { return 10000; }
 spm_status spm_set_tuning(const spm_tuning* t) {
   std::lock_guard<std::mutex> lk(g_mutex);
   if (!t) {
-    g_tuning = spm_tuning{14336, 11, 1024, 1024};
+    g_tuning = kDefaultTuning;
     return SPM_OK;
   }
-  if (t->bucket_target < 256 || t->bucket_target > kCapResolve) return SPM_ERR_INVALID_ARG;
+  if (t->bucket_target < 256 || t->bucket_target > 4 * kCapResolve) return SPM_ERR_INVALID_ARG;
   if (t->sub_bits < 8 || t->sub_bits > kSubBitsMax) return SPM_ERR_INVALID_ARG;
   if (t->partition_threads != 256 && t->partition_threads != 512 && t->partition_threads != 1024)
     return SPM_ERR_INVALID_ARG;
   if (t->resolve_threads != 256 && t->resolve_threads != 512 && t->resolve_threads != 1024)
     return SPM_ERR_INVALID_ARG;
+  if (t->two_pass_min_writes < 0 || t->two_pass_min_fronts < 0) return SPM_ERR_INVALID_ARG;
   g_tuning = *t;
   return SPM_OK;
 }
@@ -2123,7 +2721,8 @@ spm_status spm_debug_plan_stats(const void* workspace, size_t ws_bytes, int64_t 
   const int64_t tp[2] = {0, m};
   HostPlan hp;
   const ModeParams mp = mode_params(mode, flags, tun);
-  s = host_plan(1, &n_rows, &n_cols, tp, dtype == SPM_F64 ? 8 : 4, mp.seq, mp.tgt, ds->sms, hp);
+  s = host_plan(1, &n_rows, &n_cols, tp, dtype == SPM_F64 ? 8 : 4, mp.seq, mp.tgt, ds->sms, tun.two_pass_min_writes,
+                hp);
   if (s != SPM_OK) return s;
   if (ws_bytes < hp.L.total) return SPM_ERR_WORKSPACE_TOO_SMALL;
   const char* ws = static_cast<const char*>(workspace);
@@ -2169,7 +2768,7 @@ spm_status spm_assemble_csc_batched_workspace(int64_t batch, const int64_t* h_n_
   HostPlan hp;
   const ModeParams mp = mode_params(mode, flags, tun);
   const spm_status s = host_plan(batch, h_n_rows, h_n_cols, h_trip_ptr, dtype == SPM_F64 ? 8 : 4, mp.seq, mp.tgt,
-                                 num_sms_for_sizing(), hp);
+                                 num_sms_for_sizing(), tun.two_pass_min_writes, hp);
   if (s != SPM_OK) return s;
   *bytes = hp.L.total;
   return SPM_OK;

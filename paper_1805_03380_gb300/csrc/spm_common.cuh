@@ -159,7 +159,8 @@ struct Layout {
   bool seq;
   // byte offsets
   size_t meta, scal, cta, samp, cellcnt, lut, l2cell, bk_lo, bk_info, bk_count, bk_start, bk_state,
-      scanpart, hist, rec, rs, total;
+      scanpart, hist, rec, rs, tmp, rsub, total;
+  bool two_pass;   // writes reach their buckets in two passes (through tmp/rsub)
 };
 
 // Device-side scalars block (in the workspace).
@@ -167,7 +168,8 @@ struct Scalars {
   uint32_t NB;        // total buckets
   uint32_t ticket;    // persistent-kernel work counter
   uint32_t abort;     // set when a fatal device error was recorded
-  uint32_t pad;
+  uint32_t G;         // two-pass partition: buckets per group (group g = buckets [g*G, (g+1)*G))
+  unsigned long long fronts;  // (partition block, bucket) pairs with writes: the scatter's write fronts
 };
 
 // Per partition block (chunk of writes) information.
@@ -208,6 +210,8 @@ struct Ctx {
   uint32_t* hist;
   Rec* rec;
   uint64_t* rs;
+  Rec* tmp;           // two-pass partition: records grouped by bucket group
+  uint16_t* rsub;     // two-pass partition: bucket within the group of each tmp record
   // sizes
   int64_t B, m_total, S_total, lut_total, nbcap_total, hist_bound, C;
   int32_t sum_mode, f64, keep_map, has_seq;
@@ -215,6 +219,9 @@ struct Ctx {
   int32_t cap;       // writes a bucket may hold for the in-shared-memory path
   int32_t sub_bits;
   int64_t withhold;   // bucket whose look-back publication is withheld (tests), -1 = none
+  int32_t two_pass;   // partition in two passes
+  int32_t groups;     // two-pass partition: number of bucket groups aimed at (>= 1)
+  int64_t min_fronts; // two-pass partition: used only above this many write fronts
 };
 
 }  // namespace spm

@@ -46,13 +46,26 @@ def test_status_strings_and_version(spm):
 
 def test_workspace_query_and_limits(spm):
     import torch
-    ws = spm.spm_assemble_csc_workspace(100_000, 100_000, 100_000_000, torch.float64, "sum")
-    # records (8 + 8 bytes per write) dominate; planner tables are small next to them
-    assert 16 * 100_000_000 < ws < 22 * 100_000_000
+    m = 100_000_000
+    ws = spm.spm_assemble_csc_workspace(100_000, 100_000, m, torch.float64, "sum")
+    # records (8 + 8 bytes per write) and, above the two-pass threshold, the
+    # first pass's copy (16 bytes) and bucket-in-group index (2 bytes)
+    # dominate; planner tables are small next to them
+    assert 34 * m < ws < 40 * m
+    t0 = spm.spm_get_tuning()
+    try:
+        spm.spm_set_tuning(two_pass_min_writes=2**31 - 1)
+        ws1 = spm.spm_assemble_csc_workspace(100_000, 100_000, m, torch.float64, "sum")
+        assert 16 * m < ws1 < 22 * m
+        assert ws - ws1 >= 18 * m
+    finally:
+        spm.spm_set_tuning(reset=True)
+    assert spm.spm_get_tuning() == t0
     # seq orders the writes in last-write mode (sums do not depend on the order)
-    ws_set = spm.spm_assemble_csc_workspace(100_000, 100_000, 100_000_000, torch.float64, "set")
-    ws_seq = spm.spm_assemble_csc_workspace(100_000, 100_000, 100_000_000, torch.float64, "set", spm.SEQ_EXPLICIT)
-    assert ws_seq >= ws_set + 8 * 100_000_000
+    m = 1_000_000  # below the two-pass threshold
+    ws_set = spm.spm_assemble_csc_workspace(100_000, 100_000, m, torch.float64, "set")
+    ws_seq = spm.spm_assemble_csc_workspace(100_000, 100_000, m, torch.float64, "set", spm.SEQ_EXPLICIT)
+    assert ws_seq >= ws_set + 8 * m
     assert spm.spm_assemble_csc_workspace(1000, 1000, 0, torch.float32, "set") > 0
     with pytest.raises(spm.SpmError) as e:
         spm.spm_assemble_csc_workspace(1 << 30, 1 << 30, 10, torch.float64, "sum")  # 2^60 > 2^52 key space
@@ -101,10 +114,14 @@ def test_host_argument_validation_launches_nothing(spm):
 def test_tuning_roundtrip(spm):
     t0 = spm.spm_get_tuning()
     try:
-        t = spm.spm_set_tuning(bucket_target=2048, sub_bits=10, partition_threads=512, resolve_threads=256)
-        assert t == {"bucket_target": 2048, "sub_bits": 10, "partition_threads": 512, "resolve_threads": 256}
+        t = spm.spm_set_tuning(bucket_target=2048, sub_bits=10, partition_threads=512, resolve_threads=256,
+                               two_pass_min_writes=0, two_pass_min_fronts=7)
+        assert t == {"bucket_target": 2048, "sub_bits": 10, "partition_threads": 512, "resolve_threads": 256,
+                     "two_pass_min_writes": 0, "two_pass_min_fronts": 7}
         with pytest.raises(spm.SpmError):
             spm.spm_set_tuning(bucket_target=100)
+        with pytest.raises(spm.SpmError):
+            spm.spm_set_tuning(two_pass_min_writes=-1)
         with pytest.raises(spm.SpmError):
             spm.spm_set_tuning(resolve_threads=768)
     finally:

@@ -273,13 +273,18 @@ def test_cuda_graph_capture_and_replay():
 
 
 def test_oversize_buckets_window_path():
-    # a bucket target equal to the shared-memory capacity makes many buckets
+    # a bucket target above the shared-memory capacity makes many buckets
     # overflow it, which exercises the windowed path
     import paper_1805_03380_gb300 as spm
-    spm.spm_set_tuning(bucket_target=8192)
+    spm.spm_set_tuning(bucket_target=65536)
     try:
         d = workloads.density_sweep(3e-3, n=10_000)
         d["vals"][::7] = 0.0
+        a = spm.Assembler(d["shape"], len(d["rows"]), torch.float64, "set")
+        a.run(to_dev(d["rows"]), to_dev(d["cols"]), to_dev(d["vals"]))
+        a.result()
+        st = spm.spm_debug_plan_stats(a)
+        assert st["over_capacity"] > 0 and st["largest"] > st["capacity"]
         _check(d, "set")
         d2 = workloads.zipf_batch(m=400_000, n=2000, seed=workloads.SEED_BASE + 25)
         _check(d2, "sum", rounded=True)
