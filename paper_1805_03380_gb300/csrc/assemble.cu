@@ -997,38 +997,87 @@ constexpr int kTileItems = 4;      // writes per thread per tile
 constexpr int kMaxGroupsA = 2048;  // groups one pass-A block may write to
 constexpr int kGroupMax = 1024;    // buckets per group, at most
 
+// Shared memory of a tile: T records and their digits (and, in pass A, the
+// bucket within the group), then per digit two count buffers (tiles
+// alternate between them), the tile's first slot, the tile's first global
+// slot and the running global cursor.
+__host__ __device__ inline size_t tile_smem_words(int threads, int ndig, bool with_sub) {
+  const size_t T = (size_t)kTileItems * threads;
+  return 4 * T + T / 2 + (with_sub ? T / 2 : 0) + 5 * (size_t)ndig + 4;
+}
+
 __host__ __device__ inline size_t part_a_smem_bytes(int threads) {
-  const size_t T = (size_t)kTileItems * threads;
-  return 16 * T + 2 * T + 2 * T + 4 * (3 * (size_t)kMaxGroupsA + 4) + 4 * (size_t)kLutCapSmem;
+  return 4 * (tile_smem_words(threads, kMaxGroupsA, true) + (size_t)kLutCapSmem);
 }
 
-__host__ __device__ inline size_t part_b_smem_bytes(int threads) {
-  const size_t T = (size_t)kTileItems * threads;
-  return 16 * T + 2 * T + 4 * (3 * (size_t)kGroupMax + 4);
+__host__ __device__ inline size_t part_b_smem_bytes(int threads) { return 4 * tile_smem_words(threads, kGroupMax, false); }
+
+struct TileSmem {
+  uint4* stage;
+  uint16_t* dig;
+  uint16_t* sub;
+  uint32_t* cnt0;   // count buffer 0; buffer 1 follows it at cnt0 + ndig
+  uint32_t ndig;
+  uint32_t* start;  // [ndig + 1]
+  uint32_t* gbase;  // first global slot of each digit for the tile being written
+  uint32_t* cur;    // next global slot of each digit
+  uint32_t* end;    // first word after the tile area
+};
+
+__device__ __forceinline__ TileSmem tile_smem(uint32_t* sm, int ndig, bool with_sub) {
+  const uint32_t T = kTileItems * blockDim.x;
+  TileSmem S;
+  S.stage = reinterpret_cast<uint4*>(sm);
+  S.dig = reinterpret_cast<uint16_t*>(S.stage + T);
+  S.sub = S.dig + T;
+  uint32_t* w = reinterpret_cast<uint32_t*>(S.sub + (with_sub ? T : 0));
+  S.cnt0 = w;
+  S.ndig = (uint32_t)ndig;
+  S.start = w + 2 * ndig;
+  S.gbase = w + 3 * ndig + 1;
+  S.cur = w + 4 * ndig + 1;
+  S.end = w + 5 * ndig + 4;
+  return S;
 }
 
-// start[0, nd] = exclusive prefix sums of cnt[0, nd) (start[nd] = total); ends
-// with a barrier.
-__device__ void tile_scan(const uint32_t* cnt, uint32_t* start, uint32_t nd, uint32_t* buf, uint32_t* tot) {
-  const uint32_t per = (nd + blockDim.x - 1) / blockDim.x;
-  const uint32_t a = min(nd, threadIdx.x * per), e = min(nd, a + per);
+// One warp: start[] = exclusive prefix sums of this tile's counts,
+// gbase[] = cur[], cur[] += counts, and the other count buffer is cleared
+// for the next tile.
+__device__ __forceinline__ void tile_scan_warp(TileSmem& S, int buf, uint32_t nd) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t per = (nd + 31) / 32;
+  const uint32_t a = min(nd, lane * per), e = min(nd, a + per);
+  const uint32_t* cnt = S.cnt0 + (buf ? S.ndig : 0u);
+  uint32_t* other = S.cnt0 + (buf ? 0u : S.ndig);
   uint32_t local = 0;
   for (uint32_t q = a; q < e; ++q) local += cnt[q];
-  uint32_t run = block_scan_excl<uint32_t>(local, tot, buf);
-  for (uint32_t q = a; q < e; ++q) {
-    start[q] = run;
-    run += cnt[q];
+  uint32_t inc = local;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += y;
   }
-  if (threadIdx.x == 0) start[nd] = *tot;
-  __syncthreads();
+  uint32_t run = inc - local;
+  for (uint32_t q = a; q < e; ++q) {
+    const uint32_t x = cnt[q];
+    S.start[q] = run;
+    run += x;
+    S.gbase[q] = S.cur[q];
+    S.cur[q] += x;
+    other[q] = 0u;
+  }
+  if (lane == 31) S.start[nd] = inc;
 }
 
 constexpr uint32_t kNoItem = 0xffffffffu;
 
+// Per tile: count (shared-memory atomics give each item its rank within its
+// digit), barrier, one warp scans, barrier, items go to their sorted slots,
+// barrier, the sorted tile is written out; the next tile's first barrier
+// also ends this write-out.
 template <bool BATCHED, bool VEC, bool F64>
 __global__ void __launch_bounds__(1024) k_part_a(Ctx c) {
   extern __shared__ __align__(16) uint32_t sm[];
-  __shared__ uint32_t s_buf[32], s_tot;
   using VT = typename std::conditional<F64, uint64_t, uint32_t>::type;
   const CtaInfo ci = c.cta[blockIdx.x];
   if (is_aborted(c) || ci.e0 >= ci.e1 || !two_pass_on(c)) return;
@@ -1043,24 +1092,22 @@ __global__ void __launch_bounds__(1024) k_part_a(Ctx c) {
     if (tid == 0) record_fatal(c, SPM_ERR_UNSUPPORTED);
     return;
   }
-  uint4* stage = reinterpret_cast<uint4*>(sm);
-  uint16_t* dig = reinterpret_cast<uint16_t*>(stage + T);
-  uint16_t* sub = dig + T;
-  uint32_t* cnt = reinterpret_cast<uint32_t*>(sub + T);
-  uint32_t* start = cnt + kMaxGroupsA;
-  uint32_t* cur = start + kMaxGroupsA + 1;
+  TileSmem S = tile_smem(sm, kMaxGroupsA, true);
   bool lut_smem;
   uint32_t* lut_base;
-  partition_prologue(c, ci, cur + kMaxGroupsA + 3, 0, lut_smem, lut_base);
+  partition_prologue(c, ci, S.end, 0, lut_smem, lut_base);
   // this block's first slot in each group: the writes of the group's buckets
   // that come before its own (earlier matrices, earlier blocks)
-  for (uint32_t q = tid; q < ngrp; q += NT) cnt[q] = 0u;
+  uint32_t* const cnt0 = S.cnt0;
+  uint32_t* const cnt1 = S.cnt0 + S.ndig;
+  for (uint32_t q = tid; q < ngrp; q += NT) cnt0[q] = cnt1[q] = 0u;
   __syncthreads();
-  for (int64_t k = tid; k < range; k += NT) atomicAdd(&cnt[div32(ci.cb0 + (uint32_t)k, dG) - g0], c.hist[ci.hoff + k]);
+  for (int64_t k = tid; k < range; k += NT)
+    atomicAdd(&cnt0[div32(ci.cb0 + (uint32_t)k, dG) - g0], c.hist[ci.hoff + k]);
   __syncthreads();
   for (uint32_t q = tid; q < ngrp; q += NT) {
-    cur[q] = cnt[q] + c.bk_start[max((g0 + q) * G, ci.cb0)];
-    cnt[q] = 0u;
+    S.cur[q] = cnt0[q] + c.bk_start[max((g0 + q) * G, ci.cb0)];
+    cnt0[q] = 0u;
   }
   __syncthreads();
   MatView v;
@@ -1101,7 +1148,9 @@ __global__ void __launch_bounds__(1024) k_part_a(Ctx c) {
   bool bad = false;
   Raw R;
   load_raw(ci.e0, R);
-  for (int64_t tb = ci.e0; tb < ci.e1; tb += T) {
+  uint4* tmp = reinterpret_cast<uint4*>(c.tmp);
+  int buf = 0;
+  for (int64_t tb = ci.e0; tb < ci.e1; tb += T, buf ^= 1) {
     uint32_t lk[kTileItems], sb[kTileItems], dr[kTileItems];
     uint64_t vv[kTileItems];
 #pragma unroll
@@ -1115,7 +1164,7 @@ __global__ void __launch_bounds__(1024) k_part_a(Ctx c) {
           const uint32_t bg = ci.cb0 + b;
           const uint32_t grp = div32(bg, dG);
           const uint32_t d = grp - g0;
-          dr[u] = (d << 16) | atomicAdd(&cnt[d], 1u);
+          dr[u] = (d << 16) | atomicAdd(&(buf ? cnt1 : cnt0)[d], 1u);
           sb[u] = bg - grp * G;
           vv[u] = (uint64_t)R.x[u];
         } else {
@@ -1125,41 +1174,34 @@ __global__ void __launch_bounds__(1024) k_part_a(Ctx c) {
     }
     if (tb + T < ci.e1) load_raw(tb + T, R);  // next tile's loads overlap this tile's sort and stores
     __syncthreads();
-    tile_scan(cnt, start, ngrp, s_buf, &s_tot);
+    if (tid < 32) tile_scan_warp(S, buf, ngrp);
+    __syncthreads();
 #pragma unroll
     for (int u = 0; u < kTileItems; ++u) {
       if (dr[u] != kNoItem) {
         const uint32_t d = dr[u] >> 16;
-        const uint32_t p = start[d] + (dr[u] & 0xffffu);
-        stage[p] = make_uint4(lk[u], (uint32_t)tpos(tb, u), (uint32_t)vv[u], (uint32_t)(vv[u] >> 32));
-        dig[p] = (uint16_t)d;
-        sub[p] = (uint16_t)sb[u];
+        const uint32_t p = S.start[d] + (dr[u] & 0xffffu);
+        S.stage[p] = make_uint4(lk[u], (uint32_t)tpos(tb, u), (uint32_t)vv[u], (uint32_t)(vv[u] >> 32));
+        S.dig[p] = (uint16_t)d;
+        S.sub[p] = (uint16_t)sb[u];
       }
     }
     __syncthreads();
-    const uint32_t nt = start[ngrp];
-    uint4* tmp = reinterpret_cast<uint4*>(c.tmp);
+    const uint32_t nt = S.start[ngrp];
     for (uint32_t i = tid; i < nt; i += NT) {
-      const uint32_t d = dig[i];
-      const uint32_t g = cur[d] + (i - start[d]);
-      tmp[g] = stage[i];
-      c.rsub[g] = sub[i];
+      const uint32_t d = S.dig[i];
+      const uint32_t g = S.gbase[d] + (i - S.start[d]);
+      tmp[g] = S.stage[i];
+      c.rsub[g] = S.sub[i];
     }
-    __syncthreads();
-    for (uint32_t q = tid; q < ngrp; q += NT) {
-      cur[q] += cnt[q];
-      cnt[q] = 0u;
-    }
-    __syncthreads();
   }
   if (bad) record_error(c, SPM_ERR_INDEX_OUT_OF_RANGE);
 }
 
 // Pass B: block g moves the records of bucket group g from tmp to their
-// buckets in rec.
+// buckets in rec (same tile scheme).
 __global__ void __launch_bounds__(1024) k_part_b(Ctx c) {
   extern __shared__ __align__(16) uint32_t sm[];
-  __shared__ uint32_t s_buf[32], s_tot;
   if (is_aborted(c) || !two_pass_on(c)) return;
   const int tid = threadIdx.x, NT = blockDim.x;
   const uint32_t T = kTileItems * NT;
@@ -1171,14 +1213,12 @@ __global__ void __launch_bounds__(1024) k_part_b(Ctx c) {
     if (tid == 0) record_fatal(c, SPM_ERR_UNSUPPORTED);
     return;
   }
-  uint4* stage = reinterpret_cast<uint4*>(sm);
-  uint16_t* dig = reinterpret_cast<uint16_t*>(stage + T);
-  uint32_t* cnt = reinterpret_cast<uint32_t*>(dig + T);
-  uint32_t* start = cnt + kGroupMax;
-  uint32_t* cur = start + kGroupMax + 1;
+  TileSmem S = tile_smem(sm, kGroupMax, false);
+  uint32_t* const cnt0 = S.cnt0;
+  uint32_t* const cnt1 = S.cnt0 + S.ndig;
   for (uint32_t g = tid; g < gn; g += NT) {
-    cur[g] = c.bk_start[b0 + g];
-    cnt[g] = 0u;
+    S.cur[g] = c.bk_start[b0 + g];
+    cnt0[g] = cnt1[g] = 0u;
   }
   const uint32_t lo = c.bk_start[b0];
   const uint32_t hi = c.bk_start[b0 + gn - 1] + c.bk_count[b0 + gn - 1];
@@ -1199,7 +1239,8 @@ __global__ void __launch_bounds__(1024) k_part_b(Ctx c) {
     }
   };
   load(lo);
-  for (uint32_t tb = lo; tb < hi; tb += T) {
+  int buf = 0;
+  for (uint32_t tb = lo; tb < hi; tb += T, buf ^= 1) {
     uint4 rr[kTileItems];
     uint32_t dr[kTileItems];
 #pragma unroll
@@ -1207,34 +1248,29 @@ __global__ void __launch_bounds__(1024) k_part_b(Ctx c) {
       dr[u] = kNoItem;
       rr[u] = r[u];
       if (tb + (uint32_t)u * NT + tid < hi) {
-        if (g[u] < gn) dr[u] = (g[u] << 16) | atomicAdd(&cnt[g[u]], 1u);
+        if (g[u] < gn) dr[u] = (g[u] << 16) | atomicAdd(&(buf ? cnt1 : cnt0)[g[u]], 1u);
         else bad = true;
       }
     }
     if (tb + T < hi) load(tb + T);
     __syncthreads();
-    tile_scan(cnt, start, gn, s_buf, &s_tot);
+    if (tid < 32) tile_scan_warp(S, buf, gn);
+    __syncthreads();
 #pragma unroll
     for (int u = 0; u < kTileItems; ++u) {
       if (dr[u] != kNoItem) {
         const uint32_t d = dr[u] >> 16;
-        const uint32_t p = start[d] + (dr[u] & 0xffffu);
-        stage[p] = rr[u];
-        dig[p] = (uint16_t)d;
+        const uint32_t p = S.start[d] + (dr[u] & 0xffffu);
+        S.stage[p] = rr[u];
+        S.dig[p] = (uint16_t)d;
       }
     }
     __syncthreads();
-    const uint32_t nt = start[gn];
+    const uint32_t nt = S.start[gn];
     for (uint32_t i = tid; i < nt; i += NT) {
-      const uint32_t d = dig[i];
-      dst[cur[d] + (i - start[d])] = stage[i];
+      const uint32_t d = S.dig[i];
+      dst[S.gbase[d] + (i - S.start[d])] = S.stage[i];
     }
-    __syncthreads();
-    for (uint32_t q = tid; q < gn; q += NT) {
-      cur[q] += cnt[q];
-      cnt[q] = 0u;
-    }
-    __syncthreads();
   }
   if (bad) record_fatal(c, SPM_ERR_CUDA);
 }
@@ -1331,12 +1367,13 @@ __device__ int64_t lookback_wait_warp(const Ctx& c, int64_t b) {
       top -= 32;
       continue;
     }
+    __nanosleep(256);  // leave the issue slots to the other block on this SM meanwhile
     // leave the wait together: lane 0 decides for the warp
     int stop = 0;
     if (lane == 0) {
       if (is_aborted(c)) {
         stop = 1;
-      } else if ((++spins & 63) == 0 && global_timer_ns() - t_start > 2000000000ull) {
+      } else if ((++spins & 7) == 0 && global_timer_ns() - t_start > 2000000000ull) {
         record_fatal(c, SPM_ERR_TIMEOUT);
         stop = 1;
       }
@@ -1635,13 +1672,26 @@ __device__ uint32_t resolve_records(const Ctx& c, const MatMeta& mm, int64_t b, 
   uint32_t kept = 0;
   const bool map_lw = POS && !SUM && c.keep_map;
 
-  auto finish_run = [&](const R& r, uint32_t hr, uint32_t hp, bool multi) -> bool {
+  // The stored elements of this warp's runs, in key order: (key, -, value)
+  // at seg[0, kept).  (With the map, results stay in the runs' first records
+  // for the positional write pass.)
+  const bool mapping = POS && c.keep_map;
+  uint4* const seg = reinterpret_cast<uint4*>(c.tmp + seg_start) + s;
+  auto finish_run = [&](const R& r, uint32_t hr, uint32_t hp, bool multi, uint64_t& bits) -> bool {
     bool keep;
-    const uint64_t bits = r.finish(emax, keep);
-    if (multi) store_val<F64>(recs, hr, bits);  // a single write's record already holds it
-    // last-write map: the winner's stream position goes to the run's second record
-    if (map_lw && multi) reinterpret_cast<uint32_t*>(recs + ridx_of(perm[hp + 1]))[2] = r.pos;
+    bits = r.finish(emax, keep);
+    if (mapping) {
+      if (multi) store_val<F64>(recs, hr, bits);  // a single write's record already holds it
+      // last-write map: the winner's stream position goes to the run's second record
+      if (map_lw && multi) reinterpret_cast<uint32_t*>(recs + ridx_of(perm[hp + 1]))[2] = r.pos;
+    }
     return keep;
+  };
+  auto append = [&](bool keep, uint32_t key, uint64_t bits) {  // warp-wide
+    const unsigned km = __ballot_sync(kFull, keep);
+    if (!mapping && keep)
+      seg[kept + __popc(km & ((1u << lane) - 1u))] = make_uint4(key, 0u, (uint32_t)bits, (uint32_t)(bits >> 32));
+    kept += __popc(km);
   };
 
   auto chunk = [&](uint32_t base, uint32_t key, uint32_t ridx, const uint4& rec, uint64_t sq) {
@@ -1655,8 +1705,9 @@ __device__ uint32_t resolve_records(const Ctx& c, const MatMeta& mm, int64_t b, 
     const bool tail = valid && (!more || nk != key);
     const unsigned vm = __ballot_sync(kFull, valid), hm = __ballot_sync(kFull, head), tm = __ballot_sync(kFull, tail);
     if (hm == vm && tm == vm) {
-      // every write is an element of its own: its record already holds the result
-      kept += __popc(__ballot_sync(kFull, valid && bits_nonzero<F64>(F64 ? rec_val(rec) : (uint64_t)rec.z)));
+      // every write is an element of its own: its value is the result
+      const uint64_t v1 = F64 ? rec_val(rec) : (uint64_t)rec.z;
+      append(valid && bits_nonzero<F64>(v1), key, v1);
       open = foreign = false;
       return;
     }
@@ -1743,14 +1794,15 @@ __device__ uint32_t resolve_records(const Ctx& c, const MatMeta& mm, int64_t b, 
     const uint32_t hr = __shfl_sync(kFull, ridx, seg0);
     const bool fpark = tail && hl < 0 && foreign;
     bool keep = false;
+    uint64_t rbits = 0;
     if (fpark) {
       // the run began in an earlier warp's range: park this part of it
       *reinterpret_cast<R*>(B.wp[w].part) = r;
       B.wp[w].ends = 1u;
     } else if (tail) {
-      keep = finish_run(r, hl >= 0 ? hr : chr, hl >= 0 ? base + hl : chp, hl != lane);
+      keep = finish_run(r, hl >= 0 ? hr : chr, hl >= 0 ? base + hl : chp, hl != lane, rbits);
     }
-    kept += __popc(__ballot_sync(kFull, keep));
+    append(keep, key, rbits);
     if (__any_sync(kFull, fpark)) parked = true;
     if ((tm >> Lv) & 1u) {
       open = foreign = false;
@@ -1806,6 +1858,7 @@ __device__ uint32_t resolve_records(const Ctx& c, const MatMeta& mm, int64_t b, 
   __syncthreads();
   if (open && !foreign) {  // my last run continues into the following ranges
     bool keep = false;
+    uint64_t rbits = 0;
     if (lane == 0) {
       R r = carry;
       for (int w2 = w + 1; w2 < NW; ++w2) {
@@ -1814,9 +1867,9 @@ __device__ uint32_t resolve_records(const Ctx& c, const MatMeta& mm, int64_t b, 
         wp.fhp = chp;
         if (wp.ends) break;
       }
-      keep = finish_run(r, chr, chp, true);
+      keep = finish_run(r, chr, chp, true, rbits);
     }
-    kept += __shfl_sync(kFull, keep ? 1u : 0u, 0);
+    append(lane == 0 && keep, ckey, rbits);
   }
   if (lane == 0) B.wkept[w] = kept;
   __syncthreads();
@@ -1866,7 +1919,6 @@ __device__ uint32_t resolve_records(const Ctx& c, const MatMeta& mm, int64_t b, 
   int64_t* colp = c.col_ptr + mm.col_base;
   int32_t* rowp = c.row_idx + mm.t0;
   VT* outp = reinterpret_cast<VT*>(c.out_vals) + mm.t0;
-  const bool mapping = POS && c.keep_map;
   int64_t mout = -2;  // map: output index of the run continuing from the previous chunk (-2: not stored)
   uint32_t mwin = 0;  // map, last-write mode: stream position of that run's winner
   if (mapping && fstart) {
@@ -1875,9 +1927,35 @@ __device__ uint32_t resolve_records(const Ctx& c, const MatMeta& mm, int64_t b, 
     mout = bits_nonzero<F64>(hb) ? idx - 1 : -2;
     if (!SUM) mwin = __ldcg(reinterpret_cast<const uint32_t*>(recs + ridx_of(perm[hp + 1])) + 2);
   }
+  if (!mapping) {
+    // this warp's stored elements, from its segment, 32 at a time
+    for (uint32_t i0 = 0; i0 < kept; i0 += 32) {
+      const uint32_t i = i0 + lane;
+      const bool keep = i < kept;
+      uint4 rr = make_uint4(0u, 0u, 0u, 0u);
+      if (keep) rr = __ldcg(seg + i);
+      const uint32_t key = rr.x;
+      const uint64_t bits = ((uint64_t)rr.w << 32) | rr.z;
+      const unsigned km = __ballot_sync(kFull, keep);
+      uint64_t col = 0;
+      const int64_t o = idx + i0 + lane;
+      if (keep) {
+        const uint64_t x = r0 + key;
+        const uint64_t cr = col_div(B, x, nr);
+        col = col0 + cr;
+        rowp[o] = (int32_t)(x - cr * nr);
+        outp[o] = (VT)bits;
+      }
+      const uint64_t pc = __shfl_up_sync(kFull, col, 1);
+      if (keep)
+        for (uint64_t j = lane ? pc + 1 : jn; j <= col; ++j) colp[j] = o;
+      jn = __shfl_sync(kFull, col, 31 - __clz(km)) + 1;
+    }
+    idx += kept;
+  }
   uint32_t pkey = fstart ? key_at(s) : 0u;
   bool popen = fstart;
-  for (uint32_t base0 = s; base0 < e; base0 += 64) {
+  for (uint32_t base0 = s; mapping && base0 < e; base0 += 64) {
     // two chunks at a time: both chunks' shared-memory and L2 loads are in
     // flight before either is written out
     uint32_t keyv[2], ridxv[2], posv[2];
@@ -2432,7 +2510,7 @@ spm_status host_plan(int64_t B, const int64_t* h_nr, const int64_t* h_nc, const 
   L.rec = take(sizeof(Rec) * (size_t)(m_total + 4));
   L.rs = seq ? take(8 * (size_t)(m_total + 4)) : o;
   L.two_pass = !seq && m_total > 0 && m_total >= two_pass_min && two_pass_groups(C, nbcap) <= kMaxGroupsA;
-  L.tmp = L.two_pass ? take(sizeof(Rec) * (size_t)(m_total + 4)) : o;
+  L.tmp = take(sizeof(Rec) * (size_t)(m_total + 4));
   L.rsub = L.two_pass ? take(2 * (size_t)(m_total + 4)) : o;
   L.total = o;
   return SPM_OK;
@@ -2563,7 +2641,7 @@ spm_status run_assembly(int64_t B, const int64_t* h_nr, const int64_t* h_nc, con
   ctx.rec = reinterpret_cast<Rec*>(ws + L.rec);
   ctx.rs = mp.seq ? reinterpret_cast<uint64_t*>(ws + L.rs) : nullptr;
   ctx.two_pass = L.two_pass ? 1 : 0;
-  ctx.tmp = L.two_pass ? reinterpret_cast<Rec*>(ws + L.tmp) : nullptr;
+  ctx.tmp = reinterpret_cast<Rec*>(ws + L.tmp);
   ctx.rsub = L.two_pass ? reinterpret_cast<uint16_t*>(ws + L.rsub) : nullptr;
   ctx.groups = (int32_t)two_pass_groups(ds->sms, L.nbcap_total);
   ctx.min_fronts = tun.two_pass_min_fronts;
