@@ -283,13 +283,15 @@ spm_status spm_debug_withhold_publication(int64_t bucket);
  *
  * spm_debug_stage_timing(1) makes every later assembly call on the current
  * device record CUDA events, on the call's stream, at the boundaries of its
- * five stages: 0 planning (sampling, lookup tables, bucket descriptors),
- * 1 histogram pass, 2 bucket offsets, 3 scatter pass, 4 per-bucket resolve.
+ * six stages: 0 planning (sampling, lookup tables, bucket descriptors),
+ * 1 histogram pass, 2 bucket offsets, 3 scatter pass (one or two kernels),
+ * 4 per-bucket resolve (the k_resolve kernel alone), 5 placement of the
+ * stored elements (calls without the map; empty otherwise).
  * Events of the last 64 calls are kept.  spm_debug_stage_timing(0) stops
  * recording.  Not capturable in a CUDA graph while enabled.
  *
  * spm_debug_stage_times(back, ms, n): after the stream has completed, writes
- * the durations in milliseconds of the first n (<= 5) stages of the call made
+ * the durations in milliseconds of the first n (<= 6) stages of the call made
  * `back` calls ago (0 = the latest).
  *
  * spm_debug_launch_count(): number of kernels this library has launched so

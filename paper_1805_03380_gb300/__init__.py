@@ -214,7 +214,7 @@ def spm_debug_withhold_publication(bucket):
     _check(lib().spm_debug_withhold_publication(int(bucket)), "spm_debug_withhold_publication")
 
 
-STAGES = ("plan", "hist", "offsets", "scatter", "resolve")
+STAGES = ("plan", "hist", "offsets", "scatter", "resolve", "emit")
 
 
 def spm_debug_stage_timing(enable):

@@ -139,8 +139,12 @@ struct Div32 {
 };
 
 __host__ __device__ inline Div32 div32_make(uint32_t d) {
+#ifdef __CUDA_ARCH__
+  const int l = d > 1 ? 32 - __clz((int)(d - 1)) : 0;
+#else
   int l = 0;
   while ((uint64_t{1} << l) < (uint64_t)d) ++l;
+#endif
   Div32 r;
   r.m = (uint32_t)(((uint64_t{1} << 32) * ((uint64_t{1} << l) - d)) / d + 1);
   r.s1 = l < 1 ? (uint32_t)l : 1u;
@@ -861,12 +865,13 @@ __global__ void __launch_bounds__(256) k_colscan(Ctx c) {
   if ((threadIdx.x & 31) == __ffs(act) - 1 && wsum) atomicAdd(&c.scal->fronts, (unsigned long long)wsum);
 }
 
-// Device-wide exclusive scan of bk_count into bk_start (three kernels).
-__global__ void k_scan_reduce(Ctx c) {
+// Device-wide exclusive scan of a per-bucket count array (bk_count into
+// bk_start; bk_nnz into bk_out) in three kernels.
+__global__ void k_scan_reduce(Ctx c, const uint32_t* __restrict__ in) {
   __shared__ uint32_t buf[32];
   __shared__ uint32_t tot;
   const int64_t i = (int64_t)blockIdx.x * kScanBlock + threadIdx.x;
-  const uint32_t v = i < c.nbcap_total ? c.bk_count[i] : 0u;
+  const uint32_t v = i < c.nbcap_total && i < (int64_t)c.scal->NB ? in[i] : 0u;
   block_scan_excl<uint32_t>(v, &tot, buf);
   if (threadIdx.x == 0) c.scanpart[blockIdx.x] = tot;
 }
@@ -884,13 +889,13 @@ __global__ void k_scan_top(Ctx c, int64_t nblk) {
   }
 }
 
-__global__ void k_scan_down(Ctx c) {
+__global__ void k_scan_down(Ctx c, const uint32_t* __restrict__ in, uint32_t* __restrict__ out) {
   __shared__ uint32_t buf[32];
   __shared__ uint32_t tot;
   const int64_t i = (int64_t)blockIdx.x * kScanBlock + threadIdx.x;
-  const uint32_t v = i < c.nbcap_total ? c.bk_count[i] : 0u;
+  const uint32_t v = i < c.nbcap_total && i < (int64_t)c.scal->NB ? in[i] : 0u;
   const uint32_t off = block_scan_excl<uint32_t>(v, &tot, buf) + c.scanpart[blockIdx.x];
-  if (i < c.nbcap_total) c.bk_start[i] = off;
+  if (i < c.nbcap_total) out[i] = off;
 }
 
 // The two-pass partition runs when the workspace has room for it and the
@@ -1335,6 +1340,7 @@ struct BlockShared {
   Div32 dv;
   uint32_t fastdiv;   // keys relative to col0 * n_rows fit 32 bits
   uint32_t wkept[kMaxWarps];
+  uint32_t wstart[kMaxWarps];
   int64_t wbase[kMaxWarps];
   WarpPart wp[kMaxWarps];
 };
@@ -1594,7 +1600,7 @@ __device__ __forceinline__ uint64_t col_div(const BlockShared& B, uint64_t x, ui
 template <bool F64, bool SUM, bool SEQ, bool POS>
 __device__ uint32_t resolve_records(const Ctx& c, const MatMeta& mm, int64_t b, uint64_t klo, uint64_t span,
                                     uint32_t n, const RSmem& S, BlockShared& B, bool window, int64_t base_in,
-                                    int64_t seg_start, int emax) {
+                                    int64_t seg_start, int emax, uint32_t key_off, int64_t seg_base) {
   using VT = typename std::conditional<F64, uint64_t, uint32_t>::type;
   using R = Red<F64, SUM, SEQ>;
   static_assert(sizeof(R) <= kPartBytes, "reduction state too large");
@@ -1676,7 +1682,9 @@ __device__ uint32_t resolve_records(const Ctx& c, const MatMeta& mm, int64_t b, 
   // at seg[0, kept).  (With the map, results stay in the runs' first records
   // for the positional write pass.)
   const bool mapping = POS && c.keep_map;
-  uint4* const seg = reinterpret_cast<uint4*>(c.tmp + seg_start) + s;
+  const bool deferred = c.deferred != 0;
+  uint4* const seg = reinterpret_cast<uint4*>(c.tmp + seg_base) + s;
+  if (lane == 0) B.wstart[w] = s;
   auto finish_run = [&](const R& r, uint32_t hr, uint32_t hp, bool multi, uint64_t& bits) -> bool {
     bool keep;
     bits = r.finish(emax, keep);
@@ -1690,7 +1698,8 @@ __device__ uint32_t resolve_records(const Ctx& c, const MatMeta& mm, int64_t b, 
   auto append = [&](bool keep, uint32_t key, uint64_t bits) {  // warp-wide
     const unsigned km = __ballot_sync(kFull, keep);
     if (!mapping && keep)
-      seg[kept + __popc(km & ((1u << lane) - 1u))] = make_uint4(key, 0u, (uint32_t)bits, (uint32_t)(bits >> 32));
+      seg[kept + __popc(km & ((1u << lane) - 1u))] =
+          make_uint4(key + key_off, 0u, (uint32_t)bits, (uint32_t)(bits >> 32));
     kept += __popc(km);
   };
 
@@ -1885,6 +1894,8 @@ __device__ uint32_t resolve_records(const Ctx& c, const MatMeta& mm, int64_t b, 
     int64_t ex;
     if (window) {
       ex = base_in;
+    } else if (deferred) {
+      ex = 0;  // placed later by k_emit
     } else if (b == c.withhold) {
       ex = 0;  // fault injection: publish nothing, wait for nothing
     } else if (klo == 0) {
@@ -1901,18 +1912,29 @@ __device__ uint32_t resolve_records(const Ctx& c, const MatMeta& mm, int64_t b, 
   }
   __syncthreads();
   const uint32_t nnz = B.tot;
-
-  // ---- pass 2: write the elements of the runs whose heads lie in my range,
-  // and the offsets of the columns that start in my range of keys
-  int64_t idx = B.wbase[w];
-  const uint64_t nr = (uint64_t)mm.n_rows;
-  const uint64_t col0 = B.col0, r0 = B.r0;
   auto own_from = [&](uint32_t p) -> uint64_t {  // first key owned by the range starting at position p
     if (p >= n) return span;
     const uint32_t k = key_at(p);
     return (p > 0 && key_at(p - 1) == k) ? (uint64_t)k + 1 : (uint64_t)k;
   };
   const uint64_t ks = w == 0 ? 0ull : own_from(s);
+  if (deferred && !mapping) {
+    // k_emit places this warp's segment; window calls are compacted by the caller
+    if (!window && lane == 0) {
+      SegDesc d;  // (warp 0's also carries the bucket's first key as col0 * n_rows + r0)
+      d.count = kept;
+      d.pad = w == 0 ? (uint32_t)B.r0 : 0u;
+      d.ks = w == 0 ? B.col0 : 0ull;
+      c.seg_desc[b * c.res_warps + w] = d;
+    }
+    return nnz;
+  }
+
+  // ---- pass 2: write the elements of the runs whose heads lie in my range,
+  // and the offsets of the columns that start in my range of keys
+  int64_t idx = B.wbase[w];
+  const uint64_t nr = (uint64_t)mm.n_rows;
+  const uint64_t col0 = B.col0, r0 = B.r0;
   const uint64_t ke = own_from(e);
   uint64_t jn = col0 + col_div(B, r0 + ks + nr - 1, nr);  // first column starting at or after klo + ks
   const uint64_t je = col0 + col_div(B, r0 + ke + nr - 1, nr);
@@ -2086,12 +2108,17 @@ __device__ uint32_t resolve_single_key(const Ctx& c, const MatMeta& mm, uint64_t
     s_bits = bits;
     s_keep = keep ? 1u : 0u;
     s_win = SUM ? 0u : all.idx;
-    const uint64_t nr = (uint64_t)mm.n_rows;
-    const uint64_t col = key / nr;
-    if (col * nr == key) c.col_ptr[mm.col_base + col] = base;
-    if (keep) {
-      c.row_idx[mm.t0 + base] = (int32_t)(key - col * nr);
-      reinterpret_cast<VT*>(c.out_vals)[mm.t0 + base] = (VT)bits;
+    if (c.deferred) {
+      // the element joins the bucket's results (key within the bucket) for k_emit
+      if (keep) reinterpret_cast<uint4*>(c.tmp + start)[base] = make_uint4(lkey, 0u, (uint32_t)bits, (uint32_t)(bits >> 32));
+    } else {
+      const uint64_t nr = (uint64_t)mm.n_rows;
+      const uint64_t col = key / nr;
+      if (col * nr == key) c.col_ptr[mm.col_base + col] = base;
+      if (keep) {
+        c.row_idx[mm.t0 + base] = (int32_t)(key - col * nr);
+        reinterpret_cast<VT*>(c.out_vals)[mm.t0 + base] = (VT)bits;
+      }
     }
   }
   __syncthreads();
@@ -2149,7 +2176,9 @@ __global__ void __launch_bounds__(1024) k_resolve(Ctx c) {
       if (tid == 0) {
         c.d_nnz[mi] = 0;
         st_release_u64(&c.bk_state[b], kStIncl);
+        if (c.deferred) c.bk_nnz[b] = 0u;
       }
+      if (c.deferred && tid < c.res_warps) c.seg_desc[(int64_t)b * c.res_warps + tid] = SegDesc{0u, 0u, 0ull};
       __syncthreads();
       continue;
     }
@@ -2179,16 +2208,19 @@ __global__ void __launch_bounds__(1024) k_resolve(Ctx c) {
       S.orig = nullptr;
       const int emax = SUM ? max(1, block_max_int(el, B)) : 1;
       __syncthreads();
-      const uint32_t nnz = resolve_records<F64, SUM, SEQ, POS>(c, mm, b, klo, span, n, S, B, false, 0, start, emax);
+      const uint32_t nnz =
+          resolve_records<F64, SUM, SEQ, POS>(c, mm, b, klo, span, n, S, B, false, 0, start, emax, 0u, start);
       total = B.excl + nnz;
+      if (c.deferred && tid == 0) c.bk_nnz[b] = nnz;
     } else {
       // more writes than fit: windows of the key range, each sorted in shared memory
       if (tid < 32) {
-        const int64_t ex = (klo == 0 || b == c.withhold) ? 0 : lookback_wait_warp(c, b);
+        const int64_t ex = (klo == 0 || b == c.withhold || c.deferred) ? 0 : lookback_wait_warp(c, b);
         if (tid == 0) B.excl = ex;
       }
       __syncthreads();
-      int64_t base = B.excl;
+      int64_t base = B.excl;  // deferred: results of this bucket so far
+      int64_t pbase = 0;      // deferred: scratch slots used by the windows so far (>= base)
       __syncthreads();
       uint64_t wlo = 0;
       S.orig = S.keys + capw;
@@ -2243,20 +2275,51 @@ __global__ void __launch_bounds__(1024) k_resolve(Ctx c) {
           const int emax = SUM ? max(1, block_max_int(el, B)) : 1;
           __syncthreads();
           const uint32_t nw = B.n_w;
-          base += resolve_records<F64, SUM, SEQ, POS>(c, mm, b, klo + wlo, whi - wlo, nw, S, B, true, base, start,
-                                                      emax);
+          const uint32_t got = resolve_records<F64, SUM, SEQ, POS>(c, mm, b, klo + wlo, whi - wlo, nw, S, B, true,
+                                                                   base, start, emax, (uint32_t)wlo, start + pbase);
+          if (c.deferred) {
+            // move the warps' segments (in order) behind the bucket's earlier
+            // results; every destination lies at or below its source
+            uint4* t4 = reinterpret_cast<uint4*>(c.tmp);
+            for (int w2 = 0; w2 < (NT >> 5); ++w2) {
+              const uint32_t cnt = B.wkept[w2];
+              const int64_t src = start + pbase + B.wstart[w2], dst = start + B.wbase[w2];
+              for (uint32_t i0 = 0; i0 < cnt; i0 += NT) {
+                uint4 v = make_uint4(0u, 0u, 0u, 0u);
+                const bool in = i0 + tid < cnt;
+                if (in) v = t4[src + i0 + tid];
+                __syncthreads();
+                if (in) t4[dst + i0 + tid] = v;
+                __syncthreads();
+              }
+            }
+          }
+          base += got;
+          pbase += nw;
           wlo = whi;
         } else {
           base += resolve_single_key<F64, SUM, SEQ, POS>(c, mm, klo + wlo, (uint32_t)wlo, start, n, B, base);
+          pbase += 1;
           wlo = wlo + 1;
         }
         __syncthreads();
       }
       total = base;
-      // the inclusive value of a bucket is the matrix-relative end of its output
-      if (tid == 0 && b != c.withhold) st_release_u64(&c.bk_state[b], kStIncl | (uint64_t)total);
+      if (c.deferred) {
+        // one segment: all of the bucket's results, from its first slot
+        if (tid == 0) c.bk_nnz[b] = (uint32_t)total;
+        if (tid < c.res_warps) {
+          const uint64_t col0 = tid == 0 ? klo / (uint64_t)mm.n_rows : 0ull;
+          c.seg_desc[(int64_t)b * c.res_warps + tid] =
+              SegDesc{tid == 0 ? (uint32_t)total : 0u, tid == 0 ? (uint32_t)(klo - col0 * (uint64_t)mm.n_rows) : 0u,
+                      col0};
+        }
+      } else if (tid == 0 && b != c.withhold) {
+        // the inclusive value of a bucket is the matrix-relative end of its output
+        st_release_u64(&c.bk_state[b], kStIncl | (uint64_t)total);
+      }
     }
-    if (tid == 0 && klo + span == mm.K) {
+    if (!c.deferred && tid == 0 && klo + span == mm.K) {
       c.col_ptr[mm.col_base + mm.n_cols] = total;
       c.d_nnz[mi] = total;
     }
@@ -2275,6 +2338,125 @@ __global__ void __launch_bounds__(1024) k_resolve(Ctx c) {
 }
 
 // ===========================================================================
+// Deferred placement: one block per bucket writes the bucket's stored
+// elements (the concatenation of its resolve warps' segments, in key order)
+// to their final positions, and the offsets of the columns that start in the
+// bucket's key range.  Every element is handled independently: element i
+// fills the offsets of the columns after the previous element's column up to
+// its own.
+// ===========================================================================
+template <bool F64>
+__global__ void __launch_bounds__(256, 8) k_emit(Ctx c) {
+  using VT = typename std::conditional<F64, uint64_t, uint32_t>::type;
+  __shared__ uint32_t pre[kMaxWarps + 1];  // exclusive prefix of the segment counts
+  __shared__ uint32_t sst[kMaxWarps];      // first slot of each segment (from the bucket's first)
+  __shared__ uint64_t s_col0, s_nr, s_jn, s_je, s_last;
+  __shared__ uint32_t s_r0, s_fast, s_skip, s_last_bucket;
+  __shared__ int64_t s_out, s_total, s_t0, s_col_base, s_ncols;
+  __shared__ Div32 s_dv;
+  const int tid = threadIdx.x, NT = blockDim.x, NW = c.res_warps;
+  const int64_t b = blockIdx.x;
+  if (b >= (int64_t)c.scal->NB || is_aborted(c)) return;
+  const uint32_t info = c.bk_info[b];
+  const int64_t mi = info >> 6;
+  if (tid < 32) {
+    const uint32_t n = c.bk_count[b];
+    const SegDesc d = tid < NW ? c.seg_desc[b * NW + tid] : SegDesc{0u, 0u, 0ull};
+    uint32_t inc = d.count;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+      if (tid >= o) inc += y;
+    }
+    const uint32_t E = ((n + NW - 1) / NW + 31) & ~31u;
+    if (tid < NW) {
+      pre[tid] = inc - d.count;
+      sst[tid] = min(n, (uint32_t)tid * E);
+    }
+    if (tid == 31) pre[NW] = inc;
+    if (tid == 0) {
+      const MatMeta& mm = c.meta[mi];
+      const uint64_t K = mm.K;
+      s_skip = K == 0 ? 1u : 0u;
+      if (K != 0) {
+        const uint64_t klo = c.bk_lo[b];
+        const uint64_t span = min(uint64_t{1} << (info & 63), K - klo);
+        const uint64_t nr = (uint64_t)mm.n_rows;
+        const uint64_t col0 = d.ks, r0 = d.pad;  // the bucket's first key = col0 * nr + r0
+        const bool fast = (r0 + span + nr) < (uint64_t{1} << 32);
+        const Div32 dv = div32_make((uint32_t)nr);
+        s_col0 = col0;
+        s_r0 = (uint32_t)r0;
+        s_nr = nr;
+        s_fast = fast ? 1u : 0u;
+        s_dv = dv;
+        s_jn = col0 + (r0 ? 1u : 0u);  // first column starting at or after the first key
+        const uint64_t xe = r0 + span + nr - 1;
+        s_je = col0 + (fast ? (uint64_t)div32((uint32_t)xe, dv) : xe / nr);
+        const uint32_t mfirst = c.bk_out[mm.bucket_off];
+        const uint32_t ob = c.bk_out[b];
+        s_out = (int64_t)(ob - mfirst);
+        s_total = (int64_t)(ob + c.bk_nnz[b] - mfirst);
+        s_t0 = mm.t0;
+        s_col_base = mm.col_base;
+        s_ncols = mm.n_cols;
+        s_last_bucket = b == mm.bucket_off + mm.nb - 1 ? 1u : 0u;
+      }
+    }
+  }
+  __syncthreads();
+  if (s_skip) return;  // (resolve wrote the empty matrix's offsets)
+  const uint32_t nres = pre[NW];
+  const uint64_t col0 = s_col0, r0 = s_r0, nr = s_nr;
+  const bool fast = s_fast != 0;
+  const Div32 dv = s_dv;
+  const int64_t out = s_out;
+  auto cdiv = [&](uint64_t x) -> uint64_t { return fast ? (uint64_t)div32((uint32_t)x, dv) : x / nr; };
+  const uint4* base = reinterpret_cast<const uint4*>(c.tmp + c.bk_start[b]);
+  auto slot_of = [&](uint32_t i) -> uint32_t {  // scratch slot of the bucket's i-th element
+    int lo = 0, hi = NW - 1;                     // the last segment w with pre[w] <= i
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (pre[mid] <= i) lo = mid; else hi = mid - 1;
+    }
+    return sst[lo] + (i - pre[lo]);
+  };
+  int64_t* colp = c.col_ptr + s_col_base;
+  int32_t* rowp = c.row_idx + s_t0;
+  VT* outp = reinterpret_cast<VT*>(c.out_vals) + s_t0;
+  const int lane = tid & 31;
+  for (uint32_t i0 = 0; i0 < nres; i0 += NT) {
+    const uint32_t i = i0 + tid;
+    const bool have = i < nres;
+    uint64_t col = 0;
+    uint32_t pkey = 0;
+    if (have) {
+      const uint4 rr = __ldcs(base + slot_of(i));
+      if (lane == 0 && i > 0) pkey = __ldcg(base + slot_of(i - 1)).x;
+      const uint64_t x = r0 + rr.x;
+      const uint64_t cr = cdiv(x);
+      col = col0 + cr;
+      rowp[out + i] = (int32_t)(x - cr * nr);
+      outp[out + i] = (VT)(((uint64_t)rr.w << 32) | rr.z);
+    }
+    // the previous element's column: from the neighbouring lane, or from its key
+    uint64_t pc = __shfl_up_sync(0xffffffffu, col, 1);
+    if (have && lane == 0) pc = i == 0 ? s_jn - 1 : col0 + cdiv(r0 + pkey);
+    if (have)
+      for (uint64_t j = pc + 1; j <= col; ++j) colp[j] = out + i;
+    if (have && i == nres - 1) s_last = col;
+  }
+  __syncthreads();
+  // columns that start after the bucket's last element (all of them if it has none)
+  const uint64_t from = nres ? s_last + 1 : s_jn;
+  for (uint64_t j = from + tid; j < s_je; j += NT) colp[j] = out + nres;
+  if (tid == 0 && s_last_bucket) {
+    colp[s_ncols] = s_total;
+    c.d_nnz[mi] = s_total;
+  }
+}
+
+// ===========================================================================
 // Host side
 // ===========================================================================
 namespace {
@@ -2285,7 +2467,7 @@ int64_t g_withhold = -1;
 std::mutex g_mutex;
 
 // measurement hooks
-constexpr int kStages = 5;
+constexpr int kStages = 6;
 constexpr int kRing = 64;
 struct StageRing {
   bool on = false;
@@ -2420,7 +2602,7 @@ struct HostPlan {
 
 // Validate the sizes and compute the workspace layout.
 spm_status host_plan(int64_t B, const int64_t* h_nr, const int64_t* h_nc, const int64_t* h_tp, int sv, bool seq,
-                     int64_t tgt, int C, int64_t two_pass_min, HostPlan& hp) {
+                     int64_t tgt, int C, int64_t two_pass_min, int res_warps, HostPlan& hp) {
   if (B < 0 || (B > 0 && (!h_nr || !h_nc || !h_tp))) return SPM_ERR_INVALID_ARG;
   if (B >= (int64_t{1} << 26)) return SPM_ERR_UNSUPPORTED;
   if (B > 0 && h_tp[0] != 0) return SPM_ERR_INVALID_ARG;
@@ -2512,6 +2694,9 @@ spm_status host_plan(int64_t B, const int64_t* h_nr, const int64_t* h_nc, const 
   L.two_pass = !seq && m_total > 0 && m_total >= two_pass_min && two_pass_groups(C, nbcap) <= kMaxGroupsA;
   L.tmp = take(sizeof(Rec) * (size_t)(m_total + 4));
   L.rsub = L.two_pass ? take(2 * (size_t)(m_total + 4)) : o;
+  L.bk_nnz = take(4 * (size_t)std::max<int64_t>(nbcap, 1));
+  L.bk_out = take(4 * (size_t)std::max<int64_t>(nbcap, 1));
+  L.seg_desc = take(sizeof(SegDesc) * (size_t)std::max<int64_t>(nbcap, 1) * (size_t)res_warps);
   L.total = o;
   return SPM_OK;
 }
@@ -2524,9 +2709,9 @@ void launch_partition(const Ctx& ctx, const Layout& L, bool vec, cudaStream_t st
   else k_hist<BATCHED, false><<<C, threads, ps, st>>>(ctx);
   stage_mark(st, call, 2);
   k_colscan<<<(unsigned)((L.nbcap_total + 255) / 256), 256, 0, st>>>(ctx);
-  k_scan_reduce<<<(unsigned)L.scan_blocks, kScanBlock, 0, st>>>(ctx);
+  k_scan_reduce<<<(unsigned)L.scan_blocks, kScanBlock, 0, st>>>(ctx, ctx.bk_count);
   k_scan_top<<<1, 1024, 0, st>>>(ctx, L.scan_blocks);
-  k_scan_down<<<(unsigned)L.scan_blocks, kScanBlock, 0, st>>>(ctx);
+  k_scan_down<<<(unsigned)L.scan_blocks, kScanBlock, 0, st>>>(ctx, ctx.bk_count, ctx.bk_start);
   stage_mark(st, call, 3);
   const bool f64 = ctx.f64 != 0, sq = ctx.has_seq != 0;
   if (ctx.two_pass) {  // (the device picks one of the two paths; the other's blocks return at once)
@@ -2604,7 +2789,7 @@ spm_status run_assembly(int64_t B, const int64_t* h_nr, const int64_t* h_nc, con
   const int sv = dtype == SPM_F64 ? 8 : 4;
   const ModeParams mp = mode_params(mode, flags, tun);
   HostPlan hp;
-  s = host_plan(B, h_nr, h_nc, h_tp, sv, mp.seq, mp.tgt, ds->sms, tun.two_pass_min_writes, hp);
+  s = host_plan(B, h_nr, h_nc, h_tp, sv, mp.seq, mp.tgt, ds->sms, tun.two_pass_min_writes, tun.resolve_threads / 32, hp);
   if (s != SPM_OK) return s;
   const Layout& L = hp.L;
   if (L.m_total > 0 && (!rows || !cols || !vals || !row_idx || !out_vals)) return SPM_ERR_INVALID_ARG;
@@ -2645,6 +2830,11 @@ spm_status run_assembly(int64_t B, const int64_t* h_nr, const int64_t* h_nc, con
   ctx.rsub = L.two_pass ? reinterpret_cast<uint16_t*>(ws + L.rsub) : nullptr;
   ctx.groups = (int32_t)two_pass_groups(ds->sms, L.nbcap_total);
   ctx.min_fronts = tun.two_pass_min_fronts;
+  ctx.deferred = keep_map ? 0 : 1;
+  ctx.res_warps = tun.resolve_threads / 32;
+  ctx.bk_nnz = reinterpret_cast<uint32_t*>(ws + L.bk_nnz);
+  ctx.bk_out = reinterpret_cast<uint32_t*>(ws + L.bk_out);
+  ctx.seg_desc = reinterpret_cast<SegDesc*>(ws + L.seg_desc);
   ctx.B = L.B;
   ctx.m_total = L.m_total;
   ctx.S_total = L.S_total;
@@ -2695,8 +2885,18 @@ spm_status run_assembly(int64_t B, const int64_t* h_nr, const int64_t* h_nc, con
   else launch_partition<false>(ctx, L, vec, st, tun.partition_threads, call);
   launch_resolve(ctx, mp, ds->sms, st, tun.resolve_threads);
   stage_mark(st, call, 5);
-  // setup, plan, 2 bucket kernels, 6 partition (with room for two passes: 8), resolve
-  g_launches += 11 + (L.S_total > 0 ? 1 : 0) + (L.two_pass ? 2 : 0);
+  if (ctx.deferred) {
+    k_scan_reduce<<<(unsigned)L.scan_blocks, kScanBlock, 0, st>>>(ctx, ctx.bk_nnz);
+    k_scan_top<<<1, 1024, 0, st>>>(ctx, L.scan_blocks);
+    k_scan_down<<<(unsigned)L.scan_blocks, kScanBlock, 0, st>>>(ctx, ctx.bk_nnz, ctx.bk_out);
+    const unsigned blocks = (unsigned)std::max<int64_t>(L.nbcap_total, 1);  // one per bucket (NB <= nbcap)
+    if (ctx.f64) k_emit<true><<<blocks, 256, 0, st>>>(ctx);
+    else k_emit<false><<<blocks, 256, 0, st>>>(ctx);
+  }
+  stage_mark(st, call, 6);
+  // setup, plan, 2 bucket kernels, 6 partition (with room for two passes: 8), resolve,
+  // and without the map 3 scan kernels and the placement
+  g_launches += 11 + (L.S_total > 0 ? 1 : 0) + (L.two_pass ? 2 : 0) + (ctx.deferred ? 4 : 0);
   if (cudaGetLastError() != cudaSuccess) return SPM_ERR_CUDA;
   return SPM_OK;
 }
@@ -2800,7 +3000,7 @@ spm_status spm_debug_plan_stats(const void* workspace, size_t ws_bytes, int64_t 
   HostPlan hp;
   const ModeParams mp = mode_params(mode, flags, tun);
   s = host_plan(1, &n_rows, &n_cols, tp, dtype == SPM_F64 ? 8 : 4, mp.seq, mp.tgt, ds->sms, tun.two_pass_min_writes,
-                hp);
+                tun.resolve_threads / 32, hp);
   if (s != SPM_OK) return s;
   if (ws_bytes < hp.L.total) return SPM_ERR_WORKSPACE_TOO_SMALL;
   const char* ws = static_cast<const char*>(workspace);
@@ -2846,7 +3046,7 @@ spm_status spm_assemble_csc_batched_workspace(int64_t batch, const int64_t* h_n_
   HostPlan hp;
   const ModeParams mp = mode_params(mode, flags, tun);
   const spm_status s = host_plan(batch, h_n_rows, h_n_cols, h_trip_ptr, dtype == SPM_F64 ? 8 : 4, mp.seq, mp.tgt,
-                                 num_sms_for_sizing(), tun.two_pass_min_writes, hp);
+                                 num_sms_for_sizing(), tun.two_pass_min_writes, tun.resolve_threads / 32, hp);
   if (s != SPM_OK) return s;
   *bytes = hp.L.total;
   return SPM_OK;

@@ -159,7 +159,7 @@ struct Layout {
   bool seq;
   // byte offsets
   size_t meta, scal, cta, samp, cellcnt, lut, l2cell, bk_lo, bk_info, bk_count, bk_start, bk_state,
-      scanpart, hist, rec, rs, tmp, rsub, total;
+      scanpart, hist, rec, rs, tmp, rsub, bk_nnz, bk_out, seg_desc, total;
   bool two_pass;   // writes reach their buckets in two passes (through tmp/rsub)
 };
 
@@ -179,6 +179,15 @@ struct CtaInfo {
   int64_t l0, l1;     // LUT slice
   uint32_t cb0, cb1;  // bucket range
   int32_t i0, i1;     // matrix range
+};
+
+// Where one resolve warp left the stored elements of its range of a bucket
+// (in the scratch array) when the final placement is deferred: how many, and
+// the first key from which the offsets of starting columns are its job.
+struct SegDesc {
+  uint32_t count;
+  uint32_t pad;
+  uint64_t ks;
 };
 
 // Arguments of the assembly kernels.
@@ -212,6 +221,9 @@ struct Ctx {
   uint64_t* rs;
   Rec* tmp;           // two-pass partition: records grouped by bucket group
   uint16_t* rsub;     // two-pass partition: bucket within the group of each tmp record
+  uint32_t* bk_nnz;   // deferred placement: stored elements per bucket
+  uint32_t* bk_out;   // deferred placement: their exclusive prefix over all buckets
+  SegDesc* seg_desc;  // deferred placement: [bucket][resolve warp]
   // sizes
   int64_t B, m_total, S_total, lut_total, nbcap_total, hist_bound, C;
   int32_t sum_mode, f64, keep_map, has_seq;
@@ -222,6 +234,8 @@ struct Ctx {
   int32_t two_pass;   // partition in two passes
   int32_t groups;     // two-pass partition: number of bucket groups aimed at (>= 1)
   int64_t min_fronts; // two-pass partition: used only above this many write fronts
+  int32_t deferred;   // resolve leaves placement to k_emit (calls without the map)
+  int32_t res_warps;  // warps per resolve block
 };
 
 }  // namespace spm
