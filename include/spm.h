@@ -177,7 +177,7 @@ spm_status spm_assemble_csc_batched(int64_t batch, const int64_t* h_n_rows, cons
  * this library's device image: every GPU on which the library is loaded
  * holds that array until the process exits.  The call itself allocates
  * nothing.  Sizes whose workspace (spm_assemble_csc_workspace) exceeds
- * 32 MiB -- roughly 1.5 million float64 writes -- are rejected with
+ * 32 MiB -- roughly 0.75 million float64 writes -- are rejected with
  * SPM_ERR_WORKSPACE_TOO_SMALL before anything is launched.
  *
  * The first call on a device looks up the array's device address (with that

@@ -23,7 +23,7 @@
 namespace spm {
 namespace {
 
-// 32 MiB of scratch: enough for the workspace of roughly 1.5 million float64
+// 32 MiB of scratch: enough for the workspace of roughly 0.75 million float64
 // writes (about 20 bytes per write plus the planner's tables).
 constexpr size_t kStaticScratchBytes = size_t{32} << 20;
 
