@@ -249,7 +249,7 @@ spm_status spm_triplet_dvals(int64_t m, const int32_t* rows, const int32_t* cols
  *                        first to about four groups of buckets per SM, then
  *                        within each group -- which keeps the set of partly
  *                        written cache lines small; the workspace then holds
- *                        2 more bytes per write (>= 0)
+ *                        4 more bytes per write (>= 0)
  *   two_pass_min_fronts  ... and only when the one-pass scatter would write
  *                        to more than this many (partition block, bucket)
  *                        pairs, counted on the device after the histogram;

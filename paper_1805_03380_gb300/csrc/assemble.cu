@@ -1008,19 +1008,19 @@ constexpr int kGroupMax = 1024;    // buckets per group, at most
 // slot and the running global cursor.
 __host__ __device__ inline size_t tile_smem_words(int threads, int ndig, bool with_sub) {
   const size_t T = (size_t)kTileItems * threads;
-  return 4 * T + T / 2 + (with_sub ? T / 2 : 0) + 5 * (size_t)ndig + 4;
+  return 4 * T + T / 2 + (with_sub ? T : 0) + 5 * (size_t)ndig + 4;
 }
 
 __host__ __device__ inline size_t part_a_smem_bytes(int threads) {
   return 4 * (tile_smem_words(threads, kMaxGroupsA, true) + (size_t)kLutCapSmem);
 }
 
-__host__ __device__ inline size_t part_b_smem_bytes(int threads) { return 4 * tile_smem_words(threads, kGroupMax, false); }
+__host__ __device__ inline size_t part_b_smem_bytes(int threads) { return 4 * tile_smem_words(threads, 2048, false); }
 
 struct TileSmem {
   uint4* stage;
   uint16_t* dig;
-  uint16_t* sub;
+  uint32_t* sub;    // pass A: the bucket of each staged record
   uint32_t* cnt0;   // count buffer 0; buffer 1 follows it at cnt0 + ndig
   uint32_t ndig;
   uint32_t* start;  // [ndig + 1]
@@ -1034,8 +1034,8 @@ __device__ __forceinline__ TileSmem tile_smem(uint32_t* sm, int ndig, bool with_
   TileSmem S;
   S.stage = reinterpret_cast<uint4*>(sm);
   S.dig = reinterpret_cast<uint16_t*>(S.stage + T);
-  S.sub = S.dig + T;
-  uint32_t* w = reinterpret_cast<uint32_t*>(S.sub + (with_sub ? T : 0));
+  S.sub = reinterpret_cast<uint32_t*>(S.dig + T);
+  uint32_t* w = S.sub + (with_sub ? T : 0);
   S.cnt0 = w;
   S.ndig = (uint32_t)ndig;
   S.start = w + 2 * ndig;
@@ -1170,7 +1170,7 @@ __global__ void __launch_bounds__(1024) k_part_a(Ctx c) {
           const uint32_t grp = div32(bg, dG);
           const uint32_t d = grp - g0;
           dr[u] = (d << 16) | atomicAdd(&(buf ? cnt1 : cnt0)[d], 1u);
-          sb[u] = bg - grp * G;
+          sb[u] = bg;
           vv[u] = (uint64_t)R.x[u];
         } else {
           bad = true;
@@ -1188,7 +1188,7 @@ __global__ void __launch_bounds__(1024) k_part_a(Ctx c) {
         const uint32_t p = S.start[d] + (dr[u] & 0xffffu);
         S.stage[p] = make_uint4(lk[u], (uint32_t)tpos(tb, u), (uint32_t)vv[u], (uint32_t)(vv[u] >> 32));
         S.dig[p] = (uint16_t)d;
-        S.sub[p] = (uint16_t)sb[u];
+        S.sub[p] = sb[u];
       }
     }
     __syncthreads();
@@ -1197,69 +1197,129 @@ __global__ void __launch_bounds__(1024) k_part_a(Ctx c) {
       const uint32_t d = S.dig[i];
       const uint32_t g = S.gbase[d] + (i - S.start[d]);
       tmp[g] = S.stage[i];
-      c.rsub[g] = S.sub[i];
+      c.rbk[g] = S.sub[i];
     }
   }
   if (bad) record_error(c, SPM_ERR_INDEX_OUT_OF_RANGE);
 }
 
-// Pass B: block g moves the records of bucket group g from tmp to their
-// buckets in rec (same tile scheme).
+// Pass B: equal tiles of tmp, spread evenly over the blocks (bucket groups
+// differ a lot in size, so a block per group would wait on the largest).
+// A tile's records lie in at most a few consecutive groups, so their buckets
+// form a short range: the tile is sorted by bucket in shared memory, each
+// bucket present reserves its slots in rec with one atomic, and the sorted
+// tile is written out.
+constexpr int kTileDig = 2048;  // bucket range a tile may span for the shared-memory sort
+
 __global__ void __launch_bounds__(1024) k_part_b(Ctx c) {
   extern __shared__ __align__(16) uint32_t sm[];
+  __shared__ uint32_t s_min[32], s_max[32], s_bmin, s_bmax;
   if (is_aborted(c) || !two_pass_on(c)) return;
-  const int tid = threadIdx.x, NT = blockDim.x;
+  const int tid = threadIdx.x, NT = blockDim.x, lane = tid & 31, wid = tid >> 5, NWb = NT >> 5;
   const uint32_t T = kTileItems * NT;
-  const uint32_t NB = c.scal->NB, G = c.scal->G;
-  const uint64_t b0 = (uint64_t)blockIdx.x * G;
-  if (G == 0 || b0 >= NB) return;
-  const uint32_t gn = (uint32_t)((uint64_t)G < (uint64_t)NB - b0 ? (uint64_t)G : (uint64_t)NB - b0);
-  if (gn > (uint32_t)kGroupMax) {
-    if (tid == 0) record_fatal(c, SPM_ERR_UNSUPPORTED);
-    return;
-  }
-  TileSmem S = tile_smem(sm, kGroupMax, false);
-  uint32_t* const cnt0 = S.cnt0;
-  uint32_t* const cnt1 = S.cnt0 + S.ndig;
-  for (uint32_t g = tid; g < gn; g += NT) {
-    S.cur[g] = c.bk_start[b0 + g];
-    cnt0[g] = cnt1[g] = 0u;
-  }
-  const uint32_t lo = c.bk_start[b0];
-  const uint32_t hi = c.bk_start[b0 + gn - 1] + c.bk_count[b0 + gn - 1];
-  __syncthreads();
+  const uint32_t NB = c.scal->NB;
+  if (NB == 0) return;
+  const uint32_t mtot = c.bk_start[NB - 1] + c.bk_count[NB - 1];
+  const uint32_t ntiles = (mtot + T - 1) / T;
+  TileSmem S = tile_smem(sm, kTileDig, false);
+  uint32_t* const cnt = S.cnt0;
+  for (uint32_t q = tid; q < (uint32_t)kTileDig; q += NT) cnt[q] = 0u;
   const uint4* src = reinterpret_cast<const uint4*>(c.tmp);
   uint4* dst = reinterpret_cast<uint4*>(c.rec);
   bool bad = false;
   uint4 r[kTileItems];
-  uint32_t g[kTileItems];
-  auto load = [&](uint32_t tb) {
+  uint32_t bk[kTileItems];
+  auto load = [&](uint32_t tile) {
 #pragma unroll
     for (int u = 0; u < kTileItems; ++u) {
-      const uint32_t k = tb + (uint32_t)u * NT + tid;
-      if (k < hi) {
+      const uint32_t k = tile * T + (uint32_t)u * NT + tid;
+      bk[u] = ~0u;
+      if (k < mtot) {
         r[u] = __ldcs(src + k);
-        g[u] = __ldcs(c.rsub + k);
+        bk[u] = __ldcs(c.rbk + k);
       }
     }
   };
-  load(lo);
-  int buf = 0;
-  for (uint32_t tb = lo; tb < hi; tb += T, buf ^= 1) {
+  uint32_t tile = blockIdx.x;
+  if (tile < ntiles) load(tile);
+  for (; tile < ntiles; tile += gridDim.x) {
     uint4 rr[kTileItems];
+    uint32_t bb[kTileItems];
+    uint32_t mn = ~0u, mx = 0u;
+#pragma unroll
+    for (int u = 0; u < kTileItems; ++u) {
+      rr[u] = r[u];
+      bb[u] = bk[u];
+      if (bb[u] != ~0u) {
+        if (bb[u] >= NB) {
+          bad = true;
+          bb[u] = ~0u;
+        } else {
+          mn = min(mn, bb[u]);
+          mx = max(mx, bb[u]);
+        }
+      }
+    }
+    if (tile + gridDim.x < ntiles) load(tile + gridDim.x);  // next tile's loads overlap this one
+    mn = __reduce_min_sync(0xffffffffu, mn);
+    mx = __reduce_max_sync(0xffffffffu, mx);
+    if (lane == 0) {
+      s_min[wid] = mn;
+      s_max[wid] = mx;
+    }
+    __syncthreads();  // (also: the previous tile's write-out is done)
+    if (wid == 0) {
+      const uint32_t a = __reduce_min_sync(0xffffffffu, lane < NWb ? s_min[lane] : ~0u);
+      const uint32_t b = __reduce_max_sync(0xffffffffu, lane < NWb ? s_max[lane] : 0u);
+      if (lane == 0) {
+        s_bmin = a;
+        s_bmax = b;
+      }
+    }
+    __syncthreads();
+    const uint32_t bmin = s_bmin;
+    if (s_bmin > s_bmax) continue;  // (no records)
+    const uint32_t nd = s_bmax - bmin + 1;
+    if (nd > (uint32_t)kTileDig) {
+      // a tile across many small groups: reserve slot by slot
+#pragma unroll
+      for (int u = 0; u < kTileItems; ++u)
+        if (bb[u] != ~0u) dst[atomicAdd(&c.bk_cur[bb[u]], 1u)] = rr[u];
+      continue;
+    }
     uint32_t dr[kTileItems];
 #pragma unroll
     for (int u = 0; u < kTileItems; ++u) {
       dr[u] = kNoItem;
-      rr[u] = r[u];
-      if (tb + (uint32_t)u * NT + tid < hi) {
-        if (g[u] < gn) dr[u] = (g[u] << 16) | atomicAdd(&(buf ? cnt1 : cnt0)[g[u]], 1u);
-        else bad = true;
+      if (bb[u] != ~0u) {
+        const uint32_t d = bb[u] - bmin;
+        dr[u] = (d << 16) | atomicAdd(&cnt[d], 1u);
       }
     }
-    if (tb + T < hi) load(tb + T);
     __syncthreads();
-    if (tid < 32) tile_scan_warp(S, buf, gn);
+    // every bucket present reserves its slots; one warp scans the counts
+    for (uint32_t d = tid; d < nd; d += NT) {
+      const uint32_t x = cnt[d];
+      if (x) S.gbase[d] = atomicAdd(&c.bk_cur[bmin + d], x);
+    }
+    if (wid == 0) {
+      const uint32_t per = (nd + 31) / 32;
+      const uint32_t a = min(nd, lane * per), e = min(nd, a + per);
+      uint32_t local = 0;
+      for (uint32_t q = a; q < e; ++q) local += cnt[q];
+      uint32_t inc = local;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+      }
+      uint32_t run = inc - local;
+      for (uint32_t q = a; q < e; ++q) {
+        S.start[q] = run;
+        run += cnt[q];
+      }
+      if (lane == 31) S.start[nd] = inc;
+    }
     __syncthreads();
 #pragma unroll
     for (int u = 0; u < kTileItems; ++u) {
@@ -1270,8 +1330,9 @@ __global__ void __launch_bounds__(1024) k_part_b(Ctx c) {
         S.dig[p] = (uint16_t)d;
       }
     }
+    for (uint32_t d = tid; d < nd; d += NT) cnt[d] = 0u;  // clean for the next tile
     __syncthreads();
-    const uint32_t nt = S.start[gn];
+    const uint32_t nt = S.start[nd];
     for (uint32_t i = tid; i < nt; i += NT) {
       const uint32_t d = S.dig[i];
       dst[S.gbase[d] + (i - S.start[d])] = S.stage[i];
@@ -2693,7 +2754,8 @@ spm_status host_plan(int64_t B, const int64_t* h_nr, const int64_t* h_nc, const 
   L.rs = seq ? take(8 * (size_t)(m_total + 4)) : o;
   L.two_pass = !seq && m_total > 0 && m_total >= two_pass_min && two_pass_groups(C, nbcap) <= kMaxGroupsA;
   L.tmp = take(sizeof(Rec) * (size_t)(m_total + 4));
-  L.rsub = L.two_pass ? take(2 * (size_t)(m_total + 4)) : o;
+  L.rbk = L.two_pass ? take(4 * (size_t)(m_total + 4)) : o;
+  L.bk_cur = take(4 * (size_t)std::max<int64_t>(nbcap, 1));
   L.bk_nnz = take(4 * (size_t)std::max<int64_t>(nbcap, 1));
   L.bk_out = take(4 * (size_t)std::max<int64_t>(nbcap, 1));
   L.seg_desc = take(sizeof(SegDesc) * (size_t)std::max<int64_t>(nbcap, 1) * (size_t)res_warps);
@@ -2701,8 +2763,20 @@ spm_status host_plan(int64_t B, const int64_t* h_nr, const int64_t* h_nc, const 
   return SPM_OK;
 }
 
+// Persistent grid: as many blocks as fit on the SMs at once.
+template <typename K>
+int resident_grid(K kernel, int sms, int threads, size_t smem) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess || per_sm < 1) {
+    cudaGetLastError();
+    per_sm = 1;
+  }
+  return sms * per_sm;
+}
+
 template <bool BATCHED>
-void launch_partition(const Ctx& ctx, const Layout& L, bool vec, cudaStream_t st, int threads, int64_t call) {
+void launch_partition(const Ctx& ctx, const Layout& L, bool vec, cudaStream_t st, int threads, int sms,
+                      int64_t call) {
   const size_t ps = partition_smem_bytes();
   const int C = (int)L.C;
   if (vec) k_hist<BATCHED, true><<<C, threads, ps, st>>>(ctx);
@@ -2723,7 +2797,12 @@ void launch_partition(const Ctx& ctx, const Layout& L, bool vec, cudaStream_t st
       if (f64) k_part_a<BATCHED, false, true><<<C, threads, pa, st>>>(ctx);
       else k_part_a<BATCHED, false, false><<<C, threads, pa, st>>>(ctx);
     }
-    k_part_b<<<(unsigned)ctx.groups, threads, part_b_smem_bytes(threads), st>>>(ctx);
+    cudaMemcpyAsync(ctx.bk_cur, ctx.bk_start, 4 * (size_t)std::max<int64_t>(L.nbcap_total, 1),
+                    cudaMemcpyDeviceToDevice, st);
+    // (pass B: two 512-thread blocks per SM interleave their tile pipelines)
+    const int tb = std::min(threads, 512);
+    const size_t pb = part_b_smem_bytes(tb);
+    k_part_b<<<resident_grid(k_part_b, sms, tb, pb), tb, pb, st>>>(ctx);
   }
 #define SPM_SCATTER(VE, F6, SQ) k_scatter<BATCHED, VE, F6, SQ><<<C, threads, ps, st>>>(ctx)
   if (vec) {
@@ -2735,17 +2814,6 @@ void launch_partition(const Ctx& ctx, const Layout& L, bool vec, cudaStream_t st
   }
 #undef SPM_SCATTER
   stage_mark(st, call, 4);
-}
-
-// Persistent grid: as many blocks as fit on the SMs at once.
-template <typename K>
-int resident_grid(K kernel, int sms, int threads, size_t smem) {
-  int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess || per_sm < 1) {
-    cudaGetLastError();
-    per_sm = 1;
-  }
-  return sms * per_sm;
 }
 
 void launch_resolve(const Ctx& ctx, const ModeParams& mp, int sms, cudaStream_t st, int threads) {
@@ -2827,7 +2895,8 @@ spm_status run_assembly(int64_t B, const int64_t* h_nr, const int64_t* h_nc, con
   ctx.rs = mp.seq ? reinterpret_cast<uint64_t*>(ws + L.rs) : nullptr;
   ctx.two_pass = L.two_pass ? 1 : 0;
   ctx.tmp = reinterpret_cast<Rec*>(ws + L.tmp);
-  ctx.rsub = L.two_pass ? reinterpret_cast<uint16_t*>(ws + L.rsub) : nullptr;
+  ctx.rbk = L.two_pass ? reinterpret_cast<uint32_t*>(ws + L.rbk) : nullptr;
+  ctx.bk_cur = reinterpret_cast<uint32_t*>(ws + L.bk_cur);
   ctx.groups = (int32_t)two_pass_groups(ds->sms, L.nbcap_total);
   ctx.min_fronts = tun.two_pass_min_fronts;
   ctx.deferred = keep_map ? 0 : 1;
@@ -2881,8 +2950,8 @@ spm_status run_assembly(int64_t B, const int64_t* h_nr, const int64_t* h_nc, con
   const bool vec = ((reinterpret_cast<uintptr_t>(rows) | reinterpret_cast<uintptr_t>(cols) |
                      reinterpret_cast<uintptr_t>(vals)) & 15u) == 0;
   const bool batched = B > 1;
-  if (batched) launch_partition<true>(ctx, L, vec, st, tun.partition_threads, call);
-  else launch_partition<false>(ctx, L, vec, st, tun.partition_threads, call);
+  if (batched) launch_partition<true>(ctx, L, vec, st, tun.partition_threads, ds->sms, call);
+  else launch_partition<false>(ctx, L, vec, st, tun.partition_threads, ds->sms, call);
   launch_resolve(ctx, mp, ds->sms, st, tun.resolve_threads);
   stage_mark(st, call, 5);
   if (ctx.deferred) {

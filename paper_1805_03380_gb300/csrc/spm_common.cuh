@@ -159,8 +159,8 @@ struct Layout {
   bool seq;
   // byte offsets
   size_t meta, scal, cta, samp, cellcnt, lut, l2cell, bk_lo, bk_info, bk_count, bk_start, bk_state,
-      scanpart, hist, rec, rs, tmp, rsub, bk_nnz, bk_out, seg_desc, total;
-  bool two_pass;   // writes reach their buckets in two passes (through tmp/rsub)
+      scanpart, hist, rec, rs, tmp, rbk, bk_cur, bk_nnz, bk_out, seg_desc, total;
+  bool two_pass;   // writes reach their buckets in two passes (through tmp/rbk)
 };
 
 // Device-side scalars block (in the workspace).
@@ -220,7 +220,8 @@ struct Ctx {
   Rec* rec;
   uint64_t* rs;
   Rec* tmp;           // two-pass partition: records grouped by bucket group
-  uint16_t* rsub;     // two-pass partition: bucket within the group of each tmp record
+  uint32_t* rbk;      // two-pass partition: bucket of each tmp record
+  uint32_t* bk_cur;   // two-pass partition: next free slot of each bucket in rec
   uint32_t* bk_nnz;   // deferred placement: stored elements per bucket
   uint32_t* bk_out;   // deferred placement: their exclusive prefix over all buckets
   SegDesc* seg_desc;  // deferred placement: [bucket][resolve warp]
