@@ -2402,39 +2402,54 @@ __global__ void __launch_bounds__(1024) k_resolve(Ctx c) {
 // Deferred placement: one block per bucket writes the bucket's stored
 // elements (the concatenation of its resolve warps' segments, in key order)
 // to their final positions, and the offsets of the columns that start in the
-// bucket's key range.  Every element is handled independently: element i
-// fills the offsets of the columns after the previous element's column up to
-// its own.
+// bucket's key range.  Each warp takes 32-element pieces of one segment;
+// every element fills the offsets of the columns after the previous
+// element's column up to its own.
 // ===========================================================================
 template <bool F64>
 __global__ void __launch_bounds__(256, 8) k_emit(Ctx c) {
   using VT = typename std::conditional<F64, uint64_t, uint32_t>::type;
-  __shared__ uint32_t pre[kMaxWarps + 1];  // exclusive prefix of the segment counts
-  __shared__ uint32_t sst[kMaxWarps];      // first slot of each segment (from the bucket's first)
+  __shared__ uint32_t pre[kMaxWarps + 1];   // exclusive prefix of the segment counts
+  __shared__ uint32_t cpre[kMaxWarps + 1];  // exclusive prefix of the segments' 32-element pieces
+  __shared__ uint32_t sst[kMaxWarps];       // first slot of each segment (from the bucket's first)
+  __shared__ uint32_t plast[kMaxWarps];     // key of the element before each segment's first
   __shared__ uint64_t s_col0, s_nr, s_jn, s_je, s_last;
   __shared__ uint32_t s_r0, s_fast, s_skip, s_last_bucket;
   __shared__ int64_t s_out, s_total, s_t0, s_col_base, s_ncols;
   __shared__ Div32 s_dv;
-  const int tid = threadIdx.x, NT = blockDim.x, NW = c.res_warps;
+  const int tid = threadIdx.x, NT = blockDim.x, NW = c.res_warps, lane = tid & 31;
   const int64_t b = blockIdx.x;
   if (b >= (int64_t)c.scal->NB || is_aborted(c)) return;
   const uint32_t info = c.bk_info[b];
   const int64_t mi = info >> 6;
+  const uint4* base = reinterpret_cast<const uint4*>(c.tmp + c.bk_start[b]);
   if (tid < 32) {
     const uint32_t n = c.bk_count[b];
     const SegDesc d = tid < NW ? c.seg_desc[b * NW + tid] : SegDesc{0u, 0u, 0ull};
-    uint32_t inc = d.count;
+    const uint32_t E = ((n + NW - 1) / NW + 31) & ~31u;
+    const uint32_t st = min(n, (uint32_t)tid * E);
+    const uint32_t npc = (d.count + 31) >> 5;
+    uint32_t inc = d.count, cinc = npc;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-      if (tid >= o) inc += y;
+      const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o), z = __shfl_up_sync(0xffffffffu, cinc, o);
+      if (tid >= o) inc += y, cinc += z;
     }
-    const uint32_t E = ((n + NW - 1) / NW + 31) & ~31u;
+    // key of each segment's last element, then of the last element before each segment
+    const uint32_t lastkey = d.count ? __ldcg(base + st + d.count - 1).x : 0u;
+    const unsigned nonempty = __ballot_sync(0xffffffffu, d.count != 0);
+    const unsigned below = nonempty & ((1u << tid) - 1u);
+    const uint32_t pk = __shfl_sync(0xffffffffu, lastkey, below ? 31 - __clz(below) : 0);
     if (tid < NW) {
       pre[tid] = inc - d.count;
-      sst[tid] = min(n, (uint32_t)tid * E);
+      cpre[tid] = cinc - npc;
+      sst[tid] = st;
+      plast[tid] = pk;
     }
-    if (tid == 31) pre[NW] = inc;
+    if (tid == 31) {
+      pre[NW] = inc;
+      cpre[NW] = cinc;
+    }
     if (tid == 0) {
       const MatMeta& mm = c.meta[mi];
       const uint64_t K = mm.K;
@@ -2467,45 +2482,45 @@ __global__ void __launch_bounds__(256, 8) k_emit(Ctx c) {
   }
   __syncthreads();
   if (s_skip) return;  // (resolve wrote the empty matrix's offsets)
-  const uint32_t nres = pre[NW];
+  const uint32_t nres = pre[NW], npieces = cpre[NW];
   const uint64_t col0 = s_col0, r0 = s_r0, nr = s_nr;
   const bool fast = s_fast != 0;
   const Div32 dv = s_dv;
   const int64_t out = s_out;
   auto cdiv = [&](uint64_t x) -> uint64_t { return fast ? (uint64_t)div32((uint32_t)x, dv) : x / nr; };
-  const uint4* base = reinterpret_cast<const uint4*>(c.tmp + c.bk_start[b]);
-  auto slot_of = [&](uint32_t i) -> uint32_t {  // scratch slot of the bucket's i-th element
-    int lo = 0, hi = NW - 1;                     // the last segment w with pre[w] <= i
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (pre[mid] <= i) lo = mid; else hi = mid - 1;
-    }
-    return sst[lo] + (i - pre[lo]);
-  };
   int64_t* colp = c.col_ptr + s_col_base;
   int32_t* rowp = c.row_idx + s_t0;
   VT* outp = reinterpret_cast<VT*>(c.out_vals) + s_t0;
-  const int lane = tid & 31;
-  for (uint32_t i0 = 0; i0 < nres; i0 += NT) {
-    const uint32_t i = i0 + tid;
-    const bool have = i < nres;
+  for (uint32_t pc0 = tid >> 5; pc0 < npieces; pc0 += NT >> 5) {
+    int w = 0;  // the segment of this piece: the last w with cpre[w] <= pc0
+    for (int s2 = 16; s2 > 0; s2 >>= 1)
+      if (w + s2 < NW && cpre[w + s2] <= pc0) w += s2;
+    const uint32_t i = (pc0 - cpre[w]) * 32 + lane;  // position in the segment
+    const uint32_t cntw = pre[w + 1] - pre[w];
+    const bool have = i < cntw;
+    const uint32_t e = pre[w] + i;                    // position in the bucket
     uint64_t col = 0;
-    uint32_t pkey = 0;
     if (have) {
-      const uint4 rr = __ldcs(base + slot_of(i));
-      if (lane == 0 && i > 0) pkey = __ldcg(base + slot_of(i - 1)).x;
+      const uint4 rr = __ldcs(base + sst[w] + i);
       const uint64_t x = r0 + rr.x;
       const uint64_t cr = cdiv(x);
       col = col0 + cr;
-      rowp[out + i] = (int32_t)(x - cr * nr);
-      outp[out + i] = (VT)(((uint64_t)rr.w << 32) | rr.z);
+      rowp[out + e] = (int32_t)(x - cr * nr);
+      outp[out + e] = (VT)(((uint64_t)rr.w << 32) | rr.z);
     }
-    // the previous element's column: from the neighbouring lane, or from its key
+    // the previous element's column: from the neighbouring lane, else from its key
     uint64_t pc = __shfl_up_sync(0xffffffffu, col, 1);
-    if (have && lane == 0) pc = i == 0 ? s_jn - 1 : col0 + cdiv(r0 + pkey);
+    if (have && lane == 0) {
+      if (e == 0) {
+        pc = s_jn - 1;
+      } else {
+        const uint32_t pkey = i ? __ldcg(base + sst[w] + i - 1).x : plast[w];
+        pc = col0 + cdiv(r0 + pkey);
+      }
+    }
     if (have)
-      for (uint64_t j = pc + 1; j <= col; ++j) colp[j] = out + i;
-    if (have && i == nres - 1) s_last = col;
+      for (uint64_t j = pc + 1; j <= col; ++j) colp[j] = out + e;
+    if (have && e == nres - 1) s_last = col;
   }
   __syncthreads();
   // columns that start after the bucket's last element (all of them if it has none)
