@@ -270,6 +270,9 @@ __global__ void k_sample(Ctx c) {
     if (r >= 0 && (int64_t)r < mm.n_rows && col >= 0 && (int64_t)col < mm.n_cols) {
       key = (uint64_t)col * (uint64_t)mm.n_rows + (uint64_t)r;
       cidx = (unsigned long long)mm.lut_off + (key >> mm.s1);
+      // one matrix: also the finer count the planner needs for the cells it
+      // refines (a level-2 cell is 2^8 times smaller than a level-1 cell)
+      if (c.l2h && mm.H2 > 0) atomicAdd(&c.l2h[key >> (mm.s1 - kL2Bits)], 1u);
     }
     c.samp[g] = key;
   }
@@ -398,7 +401,10 @@ __global__ void __launch_bounds__(1024) k_plan(Ctx c) {
   }
   __syncthreads();
   const int s2 = mm.s1 - kL2Bits;
-  if (h > 0) {
+  if (h > 0 && c.l2h) {
+    for (uint32_t q = tid; q < h * kL2Size; q += NT)
+      cnt2[q] = c.l2h[((uint64_t)tbl_cell[q >> kL2Bits] << kL2Bits) + (q & (kL2Size - 1))];
+  } else if (h > 0) {
     for (uint32_t q = tid; q < h * kL2Size; q += NT) cnt2[q] = 0u;
     __syncthreads();
     for (int64_t k = tid; k < mm.ns; k += NT) {
@@ -2771,6 +2777,9 @@ spm_status host_plan(int64_t B, const int64_t* h_nr, const int64_t* h_nc, const 
   L.tmp = take(sizeof(Rec) * (size_t)(m_total + 4));
   L.rbk = L.two_pass ? take(4 * (size_t)(m_total + 4)) : o;
   L.bk_cur = take(4 * (size_t)std::max<int64_t>(nbcap, 1));
+  // one matrix with level-2 tables: a sample count per level-2 cell
+  L.l2h_len = (B == 1 && hp.single.H2 > 0) ? (int64_t{1} << (hp.single.L1 + kL2Bits)) : 0;
+  L.l2h = L.l2h_len ? take(4 * (size_t)L.l2h_len) : o;
   L.bk_nnz = take(4 * (size_t)std::max<int64_t>(nbcap, 1));
   L.bk_out = take(4 * (size_t)std::max<int64_t>(nbcap, 1));
   L.seg_desc = take(sizeof(SegDesc) * (size_t)std::max<int64_t>(nbcap, 1) * (size_t)res_warps);
@@ -2911,6 +2920,7 @@ spm_status run_assembly(int64_t B, const int64_t* h_nr, const int64_t* h_nc, con
   ctx.two_pass = L.two_pass ? 1 : 0;
   ctx.tmp = reinterpret_cast<Rec*>(ws + L.tmp);
   ctx.rbk = L.two_pass ? reinterpret_cast<uint32_t*>(ws + L.rbk) : nullptr;
+  ctx.l2h = L.l2h_len ? reinterpret_cast<uint32_t*>(ws + L.l2h) : nullptr;
   ctx.bk_cur = reinterpret_cast<uint32_t*>(ws + L.bk_cur);
   ctx.groups = (int32_t)two_pass_groups(ds->sms, L.nbcap_total);
   ctx.min_fronts = tun.two_pass_min_fronts;
@@ -2945,6 +2955,7 @@ spm_status run_assembly(int64_t B, const int64_t* h_nr, const int64_t* h_nc, con
   cudaMemsetAsync(ws + L.scal, 0, sizeof(Scalars), st);
   cudaMemsetAsync(ws + L.cellcnt, 0, 4 * (size_t)std::max<int64_t>(L.lut_total, 1), st);
   cudaMemsetAsync(ws + L.bk_state, 0, 8 * (size_t)std::max<int64_t>(L.nbcap_total, 1), st);
+  if (L.l2h_len) cudaMemsetAsync(ws + L.l2h, 0, 4 * (size_t)L.l2h_len, st);
   if (B == 1 && d_tp == nullptr) {
     k_setup_single<<<1, 32, 0, st>>>(ctx, hp.single);
   } else {

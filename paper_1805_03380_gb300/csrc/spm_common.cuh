@@ -159,7 +159,8 @@ struct Layout {
   bool seq;
   // byte offsets
   size_t meta, scal, cta, samp, cellcnt, lut, l2cell, bk_lo, bk_info, bk_count, bk_start, bk_state,
-      scanpart, hist, rec, rs, tmp, rbk, bk_cur, bk_nnz, bk_out, seg_desc, total;
+      scanpart, hist, rec, rs, tmp, rbk, bk_cur, bk_nnz, bk_out, seg_desc, l2h, total;
+  int64_t l2h_len;  // one matrix with level-2 tables: sample counts of all level-2 cells
   bool two_pass;   // writes reach their buckets in two passes (through tmp/rbk)
 };
 
@@ -220,6 +221,7 @@ struct Ctx {
   Rec* rec;
   uint64_t* rs;
   Rec* tmp;           // two-pass partition: records grouped by bucket group
+  uint32_t* l2h;      // one matrix: sample counts of every level-2 cell (null: the planner counts)
   uint32_t* rbk;      // two-pass partition: bucket of each tmp record
   uint32_t* bk_cur;   // two-pass partition: next free slot of each bucket in rec
   uint32_t* bk_nnz;   // deferred placement: stored elements per bucket
