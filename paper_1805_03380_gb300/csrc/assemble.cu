@@ -706,7 +706,8 @@ __device__ __forceinline__ void load_view(const Ctx& c, const CtaInfo& ci, const
 // Classify one write: bucket (relative to the block's range) and key within
 // the bucket.  Returns false for an index outside the matrix.
 __device__ __forceinline__ bool classify(const MatView& v, int32_t r, int32_t col, uint32_t& brel, uint32_t& lkey) {
-  if (r < 0 || col < 0 || (uint64_t)r >= v.n_rows || (uint64_t)col >= v.n_cols) return false;
+  // (n_rows, n_cols < 2^31: one unsigned 32-bit compare per index)
+  if ((uint32_t)r >= (uint32_t)v.n_rows || (uint32_t)col >= (uint32_t)v.n_cols) return false;
   const uint64_t key = (uint64_t)col * v.n_rows + (uint64_t)r;
   uint32_t e = v.lut[key >> v.s1];
   int sh = v.s1;
@@ -786,18 +787,21 @@ __global__ void __launch_bounds__(1024) k_hist(Ctx c) {
     const int4* c4p = reinterpret_cast<const int4*>(c.cols + ci.e0);
     const int64_t NT = blockDim.x;
     int64_t q = threadIdx.x;
-    for (; q + NT < nvec; q += 2 * NT) {  // two independent 16-byte loads per array in flight
-      const int4 ra = __ldcs(r4p + q), ca = __ldcs(c4p + q);
-      const int4 rb = __ldcs(r4p + q + NT), cb = __ldcs(c4p + q + NT);
-      const int64_t ta = ci.e0 + 4 * q, tb = ci.e0 + 4 * (q + NT);
-      body(ta, ra.x, ca.x);
-      body(ta + 1, ra.y, ca.y);
-      body(ta + 2, ra.z, ca.z);
-      body(ta + 3, ra.w, ca.w);
-      body(tb, rb.x, cb.x);
-      body(tb + 1, rb.y, cb.y);
-      body(tb + 2, rb.z, cb.z);
-      body(tb + 3, rb.w, cb.w);
+    for (; q + 3 * NT < nvec; q += 4 * NT) {  // four independent 16-byte loads per array in flight
+      int4 ra[4], ca[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        ra[u] = __ldcs(r4p + q + u * NT);
+        ca[u] = __ldcs(c4p + q + u * NT);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int64_t t = ci.e0 + 4 * (q + u * NT);
+        body(t, ra[u].x, ca[u].x);
+        body(t + 1, ra[u].y, ca[u].y);
+        body(t + 2, ra[u].z, ca[u].z);
+        body(t + 3, ra[u].w, ca[u].w);
+      }
     }
     for (; q < nvec; q += NT) {
       const int4 r4 = __ldcs(r4p + q), c4 = __ldcs(c4p + q);
