@@ -87,7 +87,11 @@ int32_t spm_version(void);
  * spm_assemble_csc needs for these sizes, dtype, mode and flags.
  * Returns SPM_ERR_INVALID_ARG / SPM_ERR_UNSUPPORTED for sizes the call would
  * reject.  The workspace needs no initialisation and may be reused by
- * successive calls on the same stream.
+ * successive calls on the same stream.  It is dominated by 32 bytes per write
+ * (the writes in bucket order, then a scratch copy that holds the first
+ * partition pass and the per-bucket results), plus 8 per write with seq and 4
+ * per write when the two-pass partition may run; it depends on the tuning
+ * (spm_set_tuning).
  */
 spm_status spm_assemble_csc_workspace(int64_t n_rows, int64_t n_cols, int64_t m, spm_dtype dtype,
                                       spm_mode mode, uint32_t flags, size_t* bytes);
@@ -270,11 +274,15 @@ spm_status spm_get_tuning(spm_tuning* t);
 
 /*
  * spm_debug_withhold_publication -- fault injection for tests of the failure
- * path (the paper has no counterpart).  While set to b >= 0, the block that
- * resolves bucket b of an assembly call publishes no look-back state, so the
- * blocks of the following buckets of the same matrix wait until their bounded
- * wait (about 2 s) expires, record SPM_ERR_TIMEOUT in *d_status and stop.
- * Nothing traps or hangs.  -1 (the default) switches it off.  Process-wide.
+ * path (the paper has no counterpart).  Calls with SPM_KEEP_MAP place each
+ * bucket's elements in the resolving block itself, after a bounded wait for
+ * the running element count of the buckets before it (a decoupled look-back);
+ * calls without the map place them in a later kernel and no block waits for
+ * another.  While set to b >= 0, the block that resolves bucket b of a call
+ * with the map publishes no count, so the blocks of the following buckets of
+ * the same matrix wait until their bounded wait (about 2 s) expires, record
+ * SPM_ERR_TIMEOUT in *d_status and stop.  Nothing traps or hangs.  -1 (the
+ * default) switches it off.  Process-wide.
  */
 spm_status spm_debug_withhold_publication(int64_t bucket);
 
