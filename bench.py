@@ -50,6 +50,12 @@ def workload_spec(name):
                             m=10_000_000, n=100_000, dtype=np.float32, mode="sum", kind="zipf"),
         "fem2048": dict(desc="Q1 FEM 2048 x 2048 elements (4,198,401 nodes), 67,108,864 writes, float64, sum mode",
                         n_el=2048, dtype=np.float64, mode="sum", kind="fem"),
+        "update_n8": dict(desc="10^7 new writes (Zipf(1.1) columns, U(-1,1) float64) applied to the 100,000 x "
+                               "100,000 CSC matrix that the 10^8-write Zipf stream assembles to, sum mode",
+                          m=10_000_000, m_a=100_000_000, n=100_000, dtype=np.float64, mode="sum", kind="update"),
+        "update_n8_set": dict(desc="as update_n8, last-write mode (the matrix assembled in sum mode)",
+                              m=10_000_000, m_a=100_000_000, n=100_000, dtype=np.float64, mode="set",
+                              kind="update"),
     }
     return specs[name]
 
@@ -179,6 +185,154 @@ def oracle_rate(d, mode, sample):
     return sample / dt, dt
 
 
+UPDATE_METRIC = "elements merged into an existing CSC matrix per second (existing elements + new writes)"
+UPDATE_UNIT = "elements/s"
+
+
+def update_oracle_rate(spec, sample):
+    """CPU oracle of the update on a sample: the matrix assembled from the
+    first `sample` writes of the matrix stream, then the first sample/10 new
+    writes; (existing elements + writes) per second, and the seconds taken."""
+    import oracle
+    import workloads
+    da = workloads.zipf_batch(m=sample, n=spec["n"], dtype=spec["dtype"], seed=workloads.SEED_BASE + 2)
+    dw = workloads.zipf_batch(m=max(sample // 10, 1), n=spec["n"], dtype=spec["dtype"], seed=workloads.SEED_BASE + 8)
+    A = oracle.assemble_csc(da["rows"], da["cols"], da["vals"], da["shape"], mode="sum")
+    t0 = time.perf_counter()
+    oracle.csc_update(*A, da["shape"], dw["rows"], dw["cols"], dw["vals"], mode=spec["mode"])
+    dt = time.perf_counter() - t0
+    return (len(A[1]) + len(dw["rows"])) / dt, dt, len(A[1]), len(dw["rows"])
+
+
+def run_update(args, world, rank, local_rank):
+    """spm_csc_update on the workload: CUDA events around each call, inputs
+    resident in HBM.  The merge stage is the call minus the assembly of the
+    new writes alone (timed the same way); the alternative without a merge,
+    re-assembling the whole concatenated stream, is timed beside it."""
+    import numpy as np
+    import torch
+
+    import paper_1805_03380_gb300 as spm
+    import workloads
+    spec = workload_spec(args.workload)
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    sv = np.dtype(spec["dtype"]).itemsize
+    da = workloads.zipf_batch(m=spec["m_a"], n=spec["n"], dtype=spec["dtype"],
+                              seed=workloads.SEED_BASE + 2 + 1000 * rank)
+    dw = workloads.zipf_batch(m=spec["m"], n=spec["n"], dtype=spec["dtype"],
+                              seed=workloads.SEED_BASE + 8 + 1000 * rank)
+    shape = da["shape"]
+    n_rows, n_cols = shape
+    ar, ac, av = (torch.from_numpy(da[k]).to(dev) for k in ("rows", "cols", "vals"))
+    A = spm.assemble_csc(ar, ac, av, shape, mode="sum")
+    a_cp, a_ri, a_v = A.col_ptr, A.row_idx.clone(), A.vals.clone()
+    nnz_a = A.nnz
+    wr, wc, wv = (torch.from_numpy(dw[k]).to(dev) for k in ("rows", "cols", "vals"))
+    m = wr.numel()
+    mode = spec["mode"]
+    ws = torch.empty(spm.spm_csc_update_workspace(n_rows, n_cols, nnz_a, m, wv.dtype, mode), dtype=torch.uint8,
+                     device=dev)
+    o_cp = torch.empty(n_cols + 1, dtype=torch.int64, device=dev)
+    o_ri = torch.empty(nnz_a + m, dtype=torch.int32, device=dev)
+    o_v = torch.empty(nnz_a + m, dtype=wv.dtype, device=dev)
+    d_nnz = torch.zeros(1, dtype=torch.int64, device=dev)
+    d_status = torch.zeros(1, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def update():
+        spm.spm_csc_update(n_rows, n_cols, a_cp, a_ri, a_v, wr, wc, wv, None, mode, 0, o_cp, o_ri, o_v, d_nnz,
+                           d_status, ws)
+
+    def timed(fn, steps):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        torch.cuda.synchronize()
+        for e0, e1 in ev:
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+        torch.cuda.synchronize()
+        return [e0.elapsed_time(e1) for e0, e1 in ev]
+
+    for _ in range(args.warmup):
+        update()
+    torch.cuda.synchronize()
+    if int(d_status.item()) != 0:
+        raise RuntimeError(f"spm_csc_update status {int(d_status.item())}")
+    nnz_out = int(d_nnz.item())
+    sampler = ClockSampler(local_rank if "CUDA_VISIBLE_DEVICES" not in os.environ else 0)
+    sampler.start()
+    time.sleep(0.2)
+    launches0 = spm.spm_debug_launch_count()
+    if world > 1:
+        torch.distributed.barrier()
+    upd_ms = timed(update, args.steps)
+    launches = spm.spm_debug_launch_count() - launches0
+    sampler.stop()
+    if int(d_status.item()) != 0 or int(d_nnz.item()) != nnz_out:
+        raise RuntimeError("spm_csc_update changed its result between calls")
+    # the assembly of the new writes alone (the update's first stage)
+    asm_b = spm.Assembler(shape, m, wv.dtype, mode, device=dev)
+    for _ in range(args.warmup):
+        asm_b.run(wr, wc, wv)
+    b_ms = timed(lambda: asm_b.run(wr, wc, wv), args.steps)
+    nnz_b = asm_b.result().nnz
+    del asm_b
+    # re-assembling everything instead: A's elements as writes, then the new ones
+    colj = torch.repeat_interleave(torch.arange(n_cols, device=dev, dtype=torch.int32), a_cp.diff())
+    cr, cc, cv = torch.cat([a_ri, wr]), torch.cat([colj, wc]), torch.cat([a_v, wv])
+    del colj
+    asm_all = spm.Assembler(shape, cr.numel(), wv.dtype, mode, device=dev)
+    for _ in range(args.warmup):
+        asm_all.run(cr, cc, cv)
+    all_ms = timed(lambda: asm_all.run(cr, cc, cv), args.steps)
+    if asm_all.result().nnz != nnz_out:
+        raise RuntimeError("re-assembly and update disagree on the number of elements")
+    del asm_all, cr, cc, cv
+
+    upd = statistics.mean(upd_ms)
+    bms = statistics.mean(b_ms)
+    merge_ms = max(upd - bms, 1e-6)
+    tot_s, units = aggregate(sum(upd_ms) / 1000.0, (nnz_a + m) * args.steps, world, dev)
+    peak, peak_kind = measured_peak()
+    merge_bytes = (nnz_a + nnz_b + nnz_out) * (4 + sv) + 3 * (n_cols + 1) * 8
+    achieved = merge_bytes / (merge_ms / 1000.0) / 1e9
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, dt, sa, sw = update_oracle_rate(spec, min(args.ref_sample, 1_000_000))
+        cpu = {"value": rate, "unit": UPDATE_UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{sa} existing elements (first writes of the matrix stream) + {sw} new writes, "
+                         f"dict + two-pointer merge in Python, 1 thread, {dt:.1f} s"}
+    if rank == 0:
+        line = {
+            "metric": UPDATE_METRIC, "value": units / tot_s, "unit": UPDATE_UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot_s / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64" if sv == 8 else "f32",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "description": spec["desc"], "nnz_a": nnz_a, "m": m,
+                       "nnz_b": nnz_b, "nnz_out": nnz_out, "mode": mode,
+                       "l2": "inputs larger than the 129 MB L2 (no flush between steps)"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": None, "peak_kind": peak_kind + " copy bandwidth",
+                         "kernel": "merge stage (offset check, cuts, k_merge): call time minus the assembly of "
+                                   "the new writes alone",
+                         "algorithmic_bytes_per_launch": merge_bytes,
+                         "bytes_formula": "(nnz_a + nnz_b + nnz_out)*(4+sv) + 3*(n_cols+1)*8",
+                         "launch_ms_mean": merge_ms},
+            "update_ms_mean": upd, "assemble_new_writes_ms_mean": bms, "reassemble_all_ms_mean": statistics.mean(all_ms),
+            "cpu_baseline": cpu,
+            "clocks": sampler.summary(),
+            "gpu_launches": launches,
+            "gpu": torch.cuda.get_device_name(dev),
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
 def run_reference(args, world, rank):
     import numpy as np  # noqa: F401
     import workloads
@@ -186,6 +340,25 @@ def run_reference(args, world, rank):
         return
     spec = workload_spec(args.workload)
     sample = args.ref_sample
+    if spec["kind"] == "update":
+        sample = min(sample, 200_000)
+        times = []
+        for k in range(args.warmup + args.steps):
+            rate, dt, sa, sw = update_oracle_rate(spec, sample)
+            if k >= args.warmup:
+                times.append(dt)
+        value = (sa + sw) * args.steps / sum(times)
+        print(json.dumps({
+            "metric": UPDATE_METRIC, "value": value, "unit": UPDATE_UNIT, "impl": "reference", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * sum(times) / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "description": spec["desc"],
+                       "sample": f"{sa} existing elements + {sw} new writes per step"},
+            "cpu_baseline": {"value": value, "unit": UPDATE_UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{sa} existing elements + {sw} new writes, Python dict + merge, 1 thread"},
+            "e2e": {"value": value, "unit": UPDATE_UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}),
+            flush=True)
+        return
     # the prefix of the same stream (the generator draws in fixed chunks of 2^24)
     if spec["kind"] == "zipf":
         d = workloads.zipf_batch(m=max(sample, min(spec["m"], 1 << 24)), n=spec["n"], dtype=spec["dtype"],
@@ -219,7 +392,8 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="n8", choices=["n8", "zipf3e7", "zipf1e7", "zipf1e7_f32", "fem2048"])
+    ap.add_argument("--workload", default="n8",
+                    choices=["n8", "zipf3e7", "zipf1e7", "zipf1e7_f32", "fem2048", "update_n8", "update_n8_set"])
     ap.add_argument("--cpu-sample", type=int, default=10_000_000, help="writes the CPU oracle baseline times")
     ap.add_argument("--ref-sample", type=int, default=1_000_000, help="writes per step of --impl reference")
     ap.add_argument("--e2e-steps", type=int, default=None)
@@ -234,6 +408,9 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, world, rank)
+        return
+    if workload_spec(args.workload)["kind"] == "update":
+        run_update(args, world, rank, local_rank)
         return
 
     import numpy as np

@@ -201,6 +201,48 @@ spm_status spm_assemble_csc_static(int64_t n_rows, int64_t n_cols, int64_t m, co
                                    void* out_vals, int64_t* d_nnz, int32_t* map, int32_t* d_status, void* stream);
 
 /*
+ * spm_csc_update_workspace / spm_csc_update -- apply m element writes to an
+ * existing n_rows x n_cols matrix A held in canonical CSC and return the
+ * updated matrix in canonical CSC: the batch insertion of Section 3.1 (the
+ * new elements are sorted first, then merged with the existing arrays) and
+ * the sync of Section 3.4 after writes made while A was in compressed form.
+ *
+ * The writes are first resolved among themselves exactly as spm_assemble_csc
+ * resolves them (last write by (seq, position), or the correctly rounded sum
+ * of the writes to one element); then every element written replaces A's
+ * element in SPM_MODE_LAST_WRITE (a final write of zero removes it) and is
+ * added to it in SPM_MODE_SUM (one rounding of A's value + that sum; an
+ * element whose result is zero is removed).  A's other elements are kept.
+ *
+ *   a_col_ptr  int64[n_cols+1]       A's column offsets: a_col_ptr[0] = 0,
+ *                                    non-decreasing, a_col_ptr[n_cols] = nnz_a;
+ *                                    otherwise *d_status = SPM_ERR_INVALID_ARG
+ *   a_row_idx  int32[nnz_a]          A's rows, strictly increasing inside each
+ *                                    column (else SPM_ERR_INVALID_ARG) and in
+ *                                    [0, n_rows) (else SPM_ERR_INDEX_OUT_OF_RANGE)
+ *   a_vals     (dtype)[nnz_a]        A's values (zeros are allowed and are
+ *                                    removed like any other zero)
+ *   rows, cols, vals, seq [m]        the writes, as for spm_assemble_csc
+ *   col_ptr    int64[n_cols+1]       output column offsets
+ *   row_idx, out_vals  [nnz_a + m]   output elements (first *d_nnz used)
+ *   d_nnz, d_status                  as for spm_assemble_csc
+ *   workspace  at least spm_csc_update_workspace() bytes: the resolved
+ *              writes, the merge's cut table and the assembly's workspace
+ *
+ * The outputs must not overlap A's arrays or the writes.  When *d_status is
+ * not SPM_OK the output is unspecified.  SPM_KEEP_MAP is rejected
+ * (SPM_ERR_INVALID_ARG).
+ */
+spm_status spm_csc_update_workspace(int64_t n_rows, int64_t n_cols, int64_t nnz_a, int64_t m, spm_dtype dtype,
+                                    spm_mode mode, uint32_t flags, size_t* bytes);
+
+spm_status spm_csc_update(int64_t n_rows, int64_t n_cols, const int64_t* a_col_ptr, const int32_t* a_row_idx,
+                          const void* a_vals, int64_t nnz_a, int64_t m, const int32_t* rows, const int32_t* cols,
+                          const void* vals, const uint64_t* seq, spm_dtype dtype, spm_mode mode, uint32_t flags,
+                          int64_t* col_ptr, int32_t* row_idx, void* out_vals, int64_t* d_nnz, int32_t* d_status,
+                          void* workspace, size_t ws_bytes, void* stream);
+
+/*
  * spm_csc_mm -- Y = A X (transpose = 0) or Y = A^T X (transpose = 1) for A in
  * CSC (Section 3.1; the paper's use cases (iv) "multiplication of dense
  * vectors with sparse matrices", Fig. 2 "W = V * X").

@@ -5,7 +5,9 @@ CPU-baseline leg of ``bench.py`` may import this package.  The product path
 (``paper_1805_03380_gb300``) never imports it, and this package never imports
 the product.  The C++ source ``spm_oracle.cpp`` is a plain std::map (red-black
 tree) build followed by an in-order walk into CSC, following Sections 3.1 and
-3.3 of the paper; the functions here only marshal numpy arrays into it.
+3.3 of the paper; the functions here only marshal numpy arrays into it,
+except ``csc_update`` (batch insertion into an existing CSC matrix), which is
+plain Python: a dict keyed by the linear index, then a two-pointer merge.
 """
 from __future__ import annotations
 
@@ -134,3 +136,102 @@ def dvals(rows, cols, dY, X, map=None):
     if rc != 0:
         raise OracleError(f"oracle_dvals failed: {rc}")
     return out[:m].copy()
+
+
+def csc_update(col_ptr, row_idx, vals, shape, rows, cols, wvals, mode="set", seq=None, out_f32=None):
+    """Existing canonical CSC matrix A (col_ptr, row_idx, vals) after the
+    element writes (rows, cols, wvals[, seq]): batch insertion into a matrix
+    held in CSC (Section 3.1: the new elements are sorted first and then
+    merged with the existing arrays; Section 3.4: the sync after writes to a
+    matrix in compressed form).
+
+    Step 1, the new elements: the writes are applied in (seq, position) order
+    to a map keyed by the linear index row + col * n_rows (Section 3.3); set
+    mode keeps the last value, sum mode adds (the first write initialises the
+    element; double precision, in write order).  With float32 values each new
+    element is rounded to float32.
+    Step 2, the merge: A's elements (already in linear-index order, since CSC
+    is column-major) and the sorted new elements are walked together; a key
+    present in both takes the new value (set) or A's value + the new value
+    (sum, rounded to float32 for float32 values); elements equal to zero are
+    not stored.
+
+    Raises OracleError("invalid argument") if col_ptr does not run from 0 to
+    len(row_idx) without decreasing or rows do not strictly increase inside a
+    column, OracleError("index out of range") for an index outside the matrix.
+    Returns (col_ptr int64[n_cols+1], row_idx int64[nnz], values float64[nnz]).
+    """
+    n_rows, n_cols = int(shape[0]), int(shape[1])
+    a_cp = np.asarray(col_ptr, dtype=np.int64)
+    a_ri = np.asarray(row_idx, dtype=np.int64)
+    a_v = np.asarray(vals)
+    w_v = np.asarray(wvals)
+    if out_f32 is None:
+        out_f32 = w_v.dtype == np.float32
+    nnz_a = a_ri.shape[0]
+    if a_cp.shape[0] != n_cols + 1 or a_cp[0] != 0 or a_cp[-1] != nnz_a or np.any(np.diff(a_cp) < 0):
+        raise OracleError("invalid argument")
+    if a_v.shape[0] != nnz_a:
+        raise OracleError("invalid argument")
+    # A's elements as (linear index, value), checking that A is canonical
+    old_keys, old_vals = [], []
+    for j in range(n_cols):
+        prev = -1
+        for e in range(int(a_cp[j]), int(a_cp[j + 1])):
+            r = int(a_ri[e])
+            if r < 0 or r >= n_rows:
+                raise OracleError("index out of range")
+            if r <= prev:
+                raise OracleError("invalid argument")
+            prev = r
+            old_keys.append(r + j * n_rows)
+            old_vals.append(float(a_v[e]))
+    # step 1: the new elements
+    m = len(rows)
+    order = list(range(m))
+    if seq is not None:
+        s = np.asarray(seq, dtype=np.uint64)
+        order.sort(key=lambda t: (int(s[t]), t))
+    new = {}
+    for t in order:
+        r, c = int(rows[t]), int(cols[t])
+        if r < 0 or r >= n_rows or c < 0 or c >= n_cols:
+            raise OracleError("index out of range")
+        k = r + c * n_rows
+        v = float(w_v[t])
+        if mode == "sum" and k in new:
+            new[k] = new[k] + v
+        else:
+            new[k] = v
+    if out_f32:
+        new = {k: float(np.float32(v)) for k, v in new.items()}
+    new_keys = sorted(new)
+    # step 2: merge the two sorted sequences
+    out_keys, out_vals = [], []
+    i = k = 0
+    while i < len(old_keys) or k < len(new_keys):
+        if k == len(new_keys) or (i < len(old_keys) and old_keys[i] < new_keys[k]):
+            key, v = old_keys[i], old_vals[i]
+            i += 1
+        elif i == len(old_keys) or new_keys[k] < old_keys[i]:
+            key, v = new_keys[k], new[new_keys[k]]
+            k += 1
+        else:
+            key = old_keys[i]
+            if mode == "sum":
+                v = float(np.float32(old_vals[i]) + np.float32(new[key])) if out_f32 else old_vals[i] + new[key]
+            else:
+                v = new[key]
+            i += 1
+            k += 1
+        if v != 0.0:  # CSC stores non-zero elements only (NaN is kept)
+            out_keys.append(key)
+            out_vals.append(v)
+    counts = np.zeros(n_cols, dtype=np.int64)
+    out_rows = np.empty(len(out_keys), dtype=np.int64)
+    for p, key in enumerate(out_keys):
+        counts[key // n_rows] += 1
+        out_rows[p] = key % n_rows
+    cp = np.zeros(n_cols + 1, dtype=np.int64)
+    cp[1:] = np.cumsum(counts)
+    return cp, out_rows, np.asarray(out_vals, dtype=np.float64)

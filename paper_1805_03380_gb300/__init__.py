@@ -22,7 +22,8 @@ import torch
 __all__ = [
     "SpmError", "lib", "spm_assemble_csc", "spm_assemble_csc_workspace", "spm_assemble_csc_batched",
     "spm_assemble_csc_batched_workspace", "spm_csc_mm", "spm_triplet_dvals", "spm_set_tuning", "spm_get_tuning",
-    "assemble_csc", "assemble_csc_batched", "csc_mm", "triplet_dvals", "AssembleMM", "Assembler", "CSC",
+    "spm_csc_update", "spm_csc_update_workspace",
+    "assemble_csc", "assemble_csc_batched", "csc_update", "csc_mm", "triplet_dvals", "AssembleMM", "Assembler", "CSC",
     "MODE_LAST_WRITE", "MODE_SUM", "KEEP_MAP", "SEQ_EXPLICIT", "LIB_PATH",
 ]
 
@@ -38,7 +39,8 @@ KEEP_MAP, CHECK_BOUNDS, SEQ_EXPLICIT = 1, 2, 4
 EXPORTED = ["spm_status_string", "spm_version", "spm_assemble_csc_workspace", "spm_assemble_csc",
             "spm_assemble_csc_batched_workspace", "spm_assemble_csc_batched", "spm_csc_mm", "spm_triplet_dvals",
             "spm_set_tuning", "spm_get_tuning", "spm_debug_withhold_publication", "spm_debug_stage_timing",
-            "spm_debug_stage_times", "spm_debug_launch_count", "spm_debug_plan_stats", "spm_assemble_csc_static"]
+            "spm_debug_stage_times", "spm_debug_launch_count", "spm_debug_plan_stats", "spm_assemble_csc_static",
+            "spm_csc_update_workspace", "spm_csc_update"]
 
 
 class SpmError(RuntimeError):
@@ -77,6 +79,9 @@ def lib():
                                            p, p, p, p, p, sz, p]
     L.spm_assemble_csc_static.argtypes = [i64, i64, i64, p, p, p, p, ctypes.c_int, ctypes.c_int, u32, p, p, p, p, p,
                                           p, p]
+    L.spm_csc_update_workspace.argtypes = [i64, i64, i64, i64, ctypes.c_int, ctypes.c_int, u32, ctypes.POINTER(sz)]
+    L.spm_csc_update.argtypes = [i64, i64, p, p, p, i64, i64, p, p, p, p, ctypes.c_int, ctypes.c_int, u32, p, p, p,
+                                 p, p, p, sz, p]
     L.spm_csc_mm.argtypes = [i64, i64, p, p, p, ctypes.c_int, i32, i64, p, i64, p, i64, p]
     L.spm_triplet_dvals.argtypes = [i64, p, p, p, ctypes.c_int, i64, p, i64, p, i64, p, p]
     L.spm_set_tuning.argtypes = [ctypes.POINTER(_Tuning)]
@@ -154,6 +159,25 @@ def spm_assemble_csc_static(n_rows, n_cols, rows, cols, vals, seq, mode, flags, 
                                          _ptr(col_ptr), _ptr(row_idx), _ptr(out_vals), _ptr(d_nnz), _ptr(map),
                                          _ptr(d_status), _stream(stream))
     _check(code, "spm_assemble_csc_static")
+
+
+def spm_csc_update_workspace(n_rows, n_cols, nnz_a, m, dtype, mode, flags=0):
+    out = ctypes.c_size_t(0)
+    _check(lib().spm_csc_update_workspace(int(n_rows), int(n_cols), int(nnz_a), int(m), _dtype_code(dtype),
+                                          _mode_code(mode), int(flags), ctypes.byref(out)), "spm_csc_update_workspace")
+    return int(out.value)
+
+
+def spm_csc_update(n_rows, n_cols, a_col_ptr, a_row_idx, a_vals, rows, cols, vals, seq, mode, flags, col_ptr, row_idx,
+                   out_vals, d_nnz, d_status, workspace, stream=None):
+    """Existing CSC A (a_col_ptr, a_row_idx, a_vals) updated by the writes
+    (rows, cols, vals[, seq]); outputs as for spm_assemble_csc."""
+    code = lib().spm_csc_update(int(n_rows), int(n_cols), _ptr(a_col_ptr), _ptr(a_row_idx), _ptr(a_vals),
+                                a_row_idx.numel(), rows.numel(), _ptr(rows), _ptr(cols), _ptr(vals), _ptr(seq),
+                                _dtype_code(vals.dtype), _mode_code(mode), int(flags), _ptr(col_ptr), _ptr(row_idx),
+                                _ptr(out_vals), _ptr(d_nnz), _ptr(d_status), _ptr(workspace),
+                                workspace.numel() * workspace.element_size(), _stream(stream))
+    _check(code, "spm_csc_update")
 
 
 def _host_i64(a):
@@ -327,6 +351,47 @@ def assemble_csc(rows, cols, vals, shape, mode="set", seq=None, keep_map=False, 
     a = Assembler(shape, rows.numel(), vals.dtype, mode, seq is not None, keep_map, dev)
     a.run(rows, cols, vals, seq, stream)
     return a.result()
+
+
+def csc_update(a, rows, cols, vals, mode="set", seq=None, stream=None):
+    """The CSC ``a`` (a CSC tuple, or (col_ptr, row_idx, vals, shape)) after the
+    element writes (rows, cols, vals[, seq]); a new CSC, ``a`` is not modified."""
+    if isinstance(a, CSC):
+        a_cp, a_ri, a_v, shape = a.col_ptr, a.row_idx, a.vals, a.shape
+    else:
+        a_cp, a_ri, a_v, shape = a
+    n_rows, n_cols = int(shape[0]), int(shape[1])
+    vals = torch.as_tensor(vals)
+    if not vals.is_cuda:
+        raise ValueError("vals must be a CUDA tensor")
+    dev = vals.device
+    if a_v.dtype != vals.dtype:
+        raise TypeError("the matrix and the writes must have the same value type")
+    a_cp = torch.as_tensor(a_cp, device=dev).to(torch.int64).contiguous()
+    a_ri = _as_index(a_ri, dev)
+    a_v = a_v.contiguous()
+    rows, cols, vals = _as_index(rows, dev), _as_index(cols, dev), vals.contiguous()
+    if seq is not None:
+        seq = torch.as_tensor(seq, device=dev).to(torch.int64).contiguous()
+    if a_cp.numel() != n_cols + 1 or a_ri.numel() != a_v.numel():
+        raise ValueError("col_ptr must have n_cols + 1 entries and row_idx/vals the same length")
+    if not (rows.numel() == cols.numel() == vals.numel()) or (seq is not None and seq.numel() != rows.numel()):
+        raise ValueError("rows, cols, vals (and seq) must have the same length")
+    flags = SEQ_EXPLICIT if seq is not None else 0
+    cap = max(a_ri.numel() + rows.numel(), 1)
+    ws = spm_csc_update_workspace(n_rows, n_cols, a_ri.numel(), rows.numel(), vals.dtype, mode, flags)
+    workspace = torch.empty(ws, dtype=torch.uint8, device=dev)
+    col_ptr = torch.empty(n_cols + 1, dtype=torch.int64, device=dev)
+    row_idx = torch.empty(cap, dtype=torch.int32, device=dev)
+    out_vals = torch.empty(cap, dtype=vals.dtype, device=dev)
+    d_nnz = torch.zeros(1, dtype=torch.int64, device=dev)
+    d_status = torch.zeros(1, dtype=torch.int32, device=dev)
+    spm_csc_update(n_rows, n_cols, a_cp, a_ri, a_v, rows, cols, vals, seq, mode, flags, col_ptr, row_idx, out_vals,
+                   d_nnz, d_status, workspace, stream)
+    (stream if stream is not None else torch.cuda.current_stream()).synchronize()
+    _raise_status(d_status, "spm_csc_update")
+    nnz = int(d_nnz.item())
+    return CSC(col_ptr, row_idx[:nnz], out_vals[:nnz], nnz, None, (n_rows, n_cols))
 
 
 def assemble_csc_batched(rows, cols, vals, n_rows, n_cols, trip_ptr, mode="set", seq=None, keep_map=False):

@@ -1754,6 +1754,7 @@ __device__ uint32_t resolve_records(const Ctx& c, const MatMeta& mm, int64_t b, 
   // for the positional write pass.)
   const bool mapping = POS && c.keep_map;
   const bool deferred = c.deferred != 0;
+  const bool kz = !SUM && c.keep_zeros;  // last-write mode, stored zeros kept
   uint4* const seg = reinterpret_cast<uint4*>(c.tmp + seg_base) + s;
   if (lane == 0) B.wstart[w] = s;
   auto finish_run = [&](const R& r, uint32_t hr, uint32_t hp, bool multi, uint64_t& bits) -> bool {
@@ -1764,7 +1765,7 @@ __device__ uint32_t resolve_records(const Ctx& c, const MatMeta& mm, int64_t b, 
       // last-write map: the winner's stream position goes to the run's second record
       if (map_lw && multi) reinterpret_cast<uint32_t*>(recs + ridx_of(perm[hp + 1]))[2] = r.pos;
     }
-    return keep;
+    return keep || kz;
   };
   auto append = [&](bool keep, uint32_t key, uint64_t bits) {  // warp-wide
     const unsigned km = __ballot_sync(kFull, keep);
@@ -1787,7 +1788,7 @@ __device__ uint32_t resolve_records(const Ctx& c, const MatMeta& mm, int64_t b, 
     if (hm == vm && tm == vm) {
       // every write is an element of its own: its value is the result
       const uint64_t v1 = F64 ? rec_val(rec) : (uint64_t)rec.z;
-      append(valid && bits_nonzero<F64>(v1), key, v1);
+      append(valid && (kz || bits_nonzero<F64>(v1)), key, v1);
       open = foreign = false;
       return;
     }
@@ -2176,6 +2177,7 @@ __device__ uint32_t resolve_single_key(const Ctx& c, const MatMeta& mm, uint64_t
     for (int w2 = 1; w2 < NW; ++w2) all.merge(*reinterpret_cast<const R*>(B.wp[w2].part), emax);
     bool keep;
     const uint64_t bits = all.finish(emax, keep);
+    keep = keep || (!SUM && c.keep_zeros);
     s_bits = bits;
     s_keep = keep ? 1u : 0u;
     s_win = SUM ? 0u : all.idx;
@@ -2865,7 +2867,7 @@ spm_status run_assembly(int64_t B, const int64_t* h_nr, const int64_t* h_nc, con
                         int32_t* d_status, void* workspace, size_t ws_bytes, void* stream) {
   if (dtype != SPM_F32 && dtype != SPM_F64) return SPM_ERR_INVALID_ARG;
   if (mode != SPM_MODE_LAST_WRITE && mode != SPM_MODE_SUM) return SPM_ERR_INVALID_ARG;
-  if (flags & ~7u) return SPM_ERR_INVALID_ARG;
+  if (flags & ~(7u | kFlagKeepZeros)) return SPM_ERR_INVALID_ARG;
   const bool has_seq = (flags & SPM_SEQ_EXPLICIT) != 0;
   if (has_seq != (seq != nullptr)) return SPM_ERR_INVALID_ARG;
   const bool keep_map = (flags & SPM_KEEP_MAP) != 0;
@@ -2943,6 +2945,7 @@ spm_status run_assembly(int64_t B, const int64_t* h_nr, const int64_t* h_nc, con
   ctx.sum_mode = mode == SPM_MODE_SUM;
   ctx.f64 = dtype == SPM_F64;
   ctx.keep_map = keep_map;
+  ctx.keep_zeros = (flags & kFlagKeepZeros) != 0 && mode == SPM_MODE_LAST_WRITE && !keep_map;
   ctx.has_seq = mp.seq;
   ctx.tgt = mp.tgt;
   ctx.cap = mp.cap;
@@ -3003,6 +3006,16 @@ spm_status run_assembly(int64_t B, const int64_t* h_nr, const int64_t* h_nc, con
 }  // namespace
 
 void count_launches(int64_t n) { g_launches += n; }
+
+spm_status assemble_internal(int64_t n_rows, int64_t n_cols, int64_t m, const int32_t* rows, const int32_t* cols,
+                             const void* vals, const uint64_t* seq, spm_dtype dtype, spm_mode mode, uint32_t flags,
+                             int64_t* col_ptr, int32_t* row_idx, void* out_vals, int64_t* d_nnz, int32_t* d_status,
+                             void* workspace, size_t ws_bytes, void* stream) {
+  if (m < 0 || (flags & SPM_KEEP_MAP)) return SPM_ERR_INVALID_ARG;
+  const int64_t tp[2] = {0, m};
+  return run_assembly(1, &n_rows, &n_cols, tp, nullptr, nullptr, nullptr, rows, cols, vals, seq, dtype, mode, flags,
+                      col_ptr, row_idx, out_vals, d_nnz, nullptr, d_status, workspace, ws_bytes, stream);
+}
 
 }  // namespace spm
 
@@ -3162,7 +3175,7 @@ spm_status spm_assemble_csc(int64_t n_rows, int64_t n_cols, int64_t m, const int
                             const void* vals, const uint64_t* seq, spm_dtype dtype, spm_mode mode, uint32_t flags,
                             int64_t* col_ptr, int32_t* row_idx, void* out_vals, int64_t* d_nnz, int32_t* map,
                             int32_t* d_status, void* workspace, size_t ws_bytes, void* stream) {
-  if (m < 0) return SPM_ERR_INVALID_ARG;
+  if (m < 0 || (flags & ~7u)) return SPM_ERR_INVALID_ARG;
   const int64_t tp[2] = {0, m};
   return run_assembly(1, &n_rows, &n_cols, tp, nullptr, nullptr, nullptr, rows, cols, vals, seq, dtype, mode, flags,
                       col_ptr, row_idx, out_vals, d_nnz, map, d_status, workspace, ws_bytes, stream);
@@ -3176,6 +3189,7 @@ spm_status spm_assemble_csc_batched(int64_t batch, const int64_t* h_n_rows, cons
                                     int64_t* d_nnz, int32_t* map, int32_t* d_status, void* workspace,
                                     size_t ws_bytes, void* stream) {
   if (batch > 0 && (!d_n_rows || !d_n_cols || !d_trip_ptr)) return SPM_ERR_INVALID_ARG;
+  if (flags & ~7u) return SPM_ERR_INVALID_ARG;
   return run_assembly(batch, h_n_rows, h_n_cols, h_trip_ptr, d_n_rows, d_n_cols, d_trip_ptr, rows, cols, vals, seq,
                       dtype, mode, flags, col_ptr, row_idx, out_vals, d_nnz, map, d_status, workspace, ws_bytes,
                       stream);

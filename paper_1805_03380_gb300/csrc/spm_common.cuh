@@ -239,6 +239,21 @@ struct Ctx {
   int64_t min_fronts; // two-pass partition: used only above this many write fronts
   int32_t deferred;   // resolve leaves placement to k_emit (calls without the map)
   int32_t res_warps;  // warps per resolve block
+  int32_t keep_zeros; // last-write mode: elements whose value is zero are stored too
 };
+
+// Flag bit of the library's own calls (never accepted from the C ABI):
+// last-write mode keeps elements whose final value is zero.
+constexpr uint32_t kFlagKeepZeros = 1u << 30;
+
+// Launch counter of the library's kernels (spm_debug_launch_count).
+void count_launches(int64_t n);
+
+// spm_assemble_csc for the library's own calls: `flags` may hold
+// kFlagKeepZeros.
+spm_status assemble_internal(int64_t n_rows, int64_t n_cols, int64_t m, const int32_t* rows, const int32_t* cols,
+                             const void* vals, const uint64_t* seq, spm_dtype dtype, spm_mode mode, uint32_t flags,
+                             int64_t* col_ptr, int32_t* row_idx, void* out_vals, int64_t* d_nnz, int32_t* d_status,
+                             void* workspace, size_t ws_bytes, void* stream);
 
 }  // namespace spm

@@ -98,3 +98,32 @@ def contribution_abs_sums(rows, cols, vals, shape, col_ptr, row_idx):
         for q in range(int(col_ptr[c]), int(col_ptr[c + 1])):
             out[q] = acc[(int(row_idx[q]), c)]
     return out
+
+
+def brute_force_update(col_ptr, row_idx, vals, shape, rows, cols, wvals, mode, seq=None, out_f32=False):
+    """Dense definition of writes to an existing matrix: start from A as a
+    dense array, apply each write in (seq, position) order as X[r,c] = v
+    (set) or X[r,c] += v (sum), then read the non-zero entries column by
+    column.  With dyadic values every summation order is exact, so this
+    equals any correctly implemented update bit for bit."""
+    X = densify(col_ptr, row_idx, vals, shape)
+    m = len(rows)
+    order = list(range(m))
+    if seq is not None:
+        order.sort(key=lambda t: (int(seq[t]), t))
+    for t in order:
+        r, c, v = int(rows[t]), int(cols[t]), float(wvals[t])
+        if mode == "set":
+            X[r, c] = v
+        else:
+            X[r, c] += v
+    if out_f32:
+        X = X.astype(np.float32).astype(np.float64)
+    n_cols = shape[1]
+    cp, ri, out = [0], [], []
+    for c in range(n_cols):
+        nz = np.nonzero(X[:, c])[0]
+        ri.extend(nz.tolist())
+        out.extend(X[nz, c].tolist())
+        cp.append(len(ri))
+    return np.array(cp, dtype=np.int64), np.array(ri, dtype=np.int64), np.array(out, dtype=np.float64)

@@ -326,3 +326,113 @@ def test_dvals_matches_finite_differences_and_dense_gradient(mode):
     else:
         for t in range(m):
             assert (mp[t] == -1) == (winner[(rows[t], cols[t])] != t)
+
+
+# --------------------------------------------------------------------------------------------
+# Batch insertion into an existing CSC matrix (Section 3.1 sort-then-merge, Section 3.4 sync)
+# --------------------------------------------------------------------------------------------
+def _dyadic(rng, k, bits=12):
+    return rng.integers(-(1 << bits) + 1, 1 << bits, size=k).astype(np.float64) * 2.0 ** -bits
+
+
+def _tiny_update_case(rng, zero_frac=0.2, hit_frac=0.5):
+    """A canonical CSC matrix built by scipy from a dense array, and writes,
+    part of them to A's elements; dyadic values (all sums exact)."""
+    sp = pytest.importorskip("scipy.sparse")
+    n_rows = int(rng.integers(1, 25))
+    n_cols = int(rng.integers(1, 25))
+    dense = np.where(rng.random((n_rows, n_cols)) < 0.3, _dyadic(rng, n_rows * n_cols).reshape(n_rows, n_cols), 0.0)
+    A = sp.csc_matrix(dense)
+    A.sort_indices()
+    m = int(rng.integers(0, 80))
+    rows = rng.integers(0, n_rows, m)
+    cols = rng.integers(0, n_cols, m)
+    nz_r, nz_c = np.nonzero(dense)
+    if len(nz_r) and m:
+        hit = rng.random(m) < hit_frac
+        pick = rng.integers(0, len(nz_r), m)
+        rows[hit], cols[hit] = nz_r[pick[hit]], nz_c[pick[hit]]
+    vals = _dyadic(rng, m)
+    vals[rng.random(m) < zero_frac] = 0.0
+    if m and len(nz_r):  # writes that cancel an element exactly (sum mode removes it)
+        k = int(rng.integers(0, m))
+        rows[k], cols[k] = nz_r[0], nz_c[0]
+        vals[k] = -dense[nz_r[0], nz_c[0]]
+    return (A.indptr.astype(np.int64), A.indices.astype(np.int64), A.data.astype(np.float64), (n_rows, n_cols),
+            rows, cols, vals)
+
+
+@pytest.mark.parametrize("mode", ["set", "sum"])
+@pytest.mark.parametrize("use_seq", [False, True])
+@pytest.mark.parametrize("out_f32", [False, True])
+def test_update_matches_dense_sequential_writes(mode, use_seq, out_f32):
+    rng = np.random.default_rng(1805_2 + 7 * use_seq + 3 * out_f32 + (mode == "sum"))
+    from tests._refimpl import brute_force_update
+    for _ in range(40):
+        cp, ri, v, shape, rows, cols, vals = _tiny_update_case(rng)
+        seq = rng.integers(0, 4, len(rows)).astype(np.uint64) if use_seq else None
+        wv = vals.astype(np.float32) if out_f32 else vals
+        av = v.astype(np.float32) if out_f32 else v
+        got = oracle.csc_update(cp, ri, av, shape, rows, cols, wv, mode=mode, seq=seq)
+        want = brute_force_update(cp, ri, v, shape, rows, cols, vals, mode, seq=seq, out_f32=out_f32)
+        _assert_csc_equal(got, want)
+        check_csc_invariants(*got, shape)
+
+
+def test_update_sum_is_scipy_addition():
+    """Sum mode: A + (the new writes assembled with duplicates summed), by scipy."""
+    sp = pytest.importorskip("scipy.sparse")
+    rng = np.random.default_rng(18053)
+    for _ in range(40):
+        cp, ri, v, shape, rows, cols, vals = _tiny_update_case(rng)
+        A = sp.csc_matrix((v, ri, cp), shape=shape)
+        Bm = sp.coo_matrix((vals, (rows, cols)), shape=shape).tocsc()
+        C = (A + Bm).tocsc()
+        C.eliminate_zeros()
+        C.sort_indices()
+        got = oracle.csc_update(cp, ri, v, shape, rows, cols, vals, mode="sum")
+        np.testing.assert_array_equal(got[0], C.indptr)
+        np.testing.assert_array_equal(got[1], C.indices)
+        np.testing.assert_array_equal(got[2], C.data)
+
+
+def test_update_special_cases():
+    rng = np.random.default_rng(18054)
+    for _ in range(20):
+        cp, ri, v, shape, rows, cols, vals = _tiny_update_case(rng, zero_frac=0.0)
+        # no writes: A itself (A holds no zeros)
+        _assert_csc_equal(oracle.csc_update(cp, ri, v, shape, rows[:0], cols[:0], vals[:0]), (cp, ri, v))
+        # an empty A: the plain assembly of the writes
+        empty = (np.zeros(shape[1] + 1, dtype=np.int64), np.zeros(0, dtype=np.int64), np.zeros(0))
+        for mode in ("set", "sum"):
+            _assert_csc_equal(oracle.csc_update(*empty, shape, rows, cols, vals, mode=mode),
+                              oracle.assemble_csc(rows, cols, vals, shape, mode=mode))
+        # last-write mode composes: two batches in turn equal their concatenation
+        h = len(rows) // 2
+        once = oracle.csc_update(cp, ri, v, shape, rows, cols, vals, mode="set")
+        first = oracle.csc_update(cp, ri, v, shape, rows[:h], cols[:h], vals[:h], mode="set")
+        twice = oracle.csc_update(*first, shape, rows[h:], cols[h:], vals[h:], mode="set")
+        _assert_csc_equal(twice, once)
+        # zeros written over every element of A (set) or its negation added (sum) empty the matrix
+        colj = np.repeat(np.arange(shape[1]), np.diff(cp))
+        for mode, w in (("set", np.zeros(len(ri))), ("sum", -v)):
+            cp2, ri2, v2 = oracle.csc_update(cp, ri, v, shape, ri, colj, w, mode=mode)
+            assert cp2[-1] == 0 and len(ri2) == 0
+
+
+def test_update_rejects_malformed_matrices():
+    cp, ri, v = np.array([0, 2, 3]), np.array([0, 2, 1]), np.array([1.0, 2.0, 3.0])
+    shape = (3, 2)
+    none = (np.zeros(0, dtype=np.int64),) * 2 + (np.zeros(0),)
+    oracle.csc_update(cp, ri, v, shape, *none)
+    bad = {
+        "invalid argument": [(np.array([1, 2, 3]), ri), (np.array([0, 3, 2]), ri), (np.array([0, 2, 2]), ri),
+                             (cp, np.array([2, 0, 1])), (cp, np.array([1, 1, 1]))],
+        "index out of range": [(cp, np.array([0, 3, 1])), (cp, np.array([-1, 2, 1]))],
+    }
+    for msg, cases in bad.items():
+        for c, r in cases:
+            with pytest.raises(oracle.OracleError, match=msg):
+                oracle.csc_update(c, r, v, shape, *none)
+    with pytest.raises(oracle.OracleError, match="index out of range"):
+        oracle.csc_update(cp, ri, v, shape, np.array([3]), np.array([0]), np.array([1.0]))

@@ -25,6 +25,9 @@ Workloads
   batched path (set semantics, float32 N(0,1) values, 10 % rewrites).
 * ``density_sweep``    the shape of the paper's unordered-insertion experiment:
   10,000 x 10,000, uniform coordinates, m = density * 10^8.
+* ``update_batch``     writes that build an existing matrix plus a batch of
+  new writes to it, part of them hitting existing elements, part of them
+  zero (insertion into a matrix already in CSC, Section 3.1).
 """
 from __future__ import annotations
 
@@ -135,6 +138,47 @@ def fem_q1(n_el=2048, dtype=np.float64, sigma=0.1, seed=SEED_BASE + 3, unperturb
         vals = (base * f).astype(dtype)
     n_nodes = nn * nn
     return dict(rows=rows, cols=cols, vals=vals, seq=None, shape=(n_nodes, n_nodes))
+
+
+def update_batch(n_rows=3000, n_cols=2000, m_a=60_000, m=20_000, hit_frac=0.3, zero_frac=0.05, zipf_s=None,
+                 dtype=np.float64, dyadic=False, seed=SEED_BASE + 7):
+    """Writes to a matrix that is already held in CSC.
+
+    ``a_rows, a_cols, a_vals`` (m_a writes) are the writes that built the
+    existing matrix A (the caller assembles them); ``rows, cols, vals`` are
+    the m new writes: a fraction ``hit_frac`` of them targets coordinates
+    written for A (an update of an existing element), the rest uniform
+    coordinates; a fraction ``zero_frac`` has value 0.0 (which removes an
+    element in last-write mode).  Columns are uniform, or bounded Zipf(s)
+    (column 0 hottest) with ``zipf_s``.  Values N(0,1), or dyadic multiples of
+    2^-20 with ``dyadic`` (every sum of a few of them is exact in float32).
+    """
+    rng = _rng(seed)
+
+    def draw_cols(k):
+        if zipf_s is None:
+            return rng.integers(0, n_cols, size=k)
+        return np.minimum(np.searchsorted(zipf_cdf(n_cols, zipf_s), rng.random(k), side="right"), n_cols - 1)
+
+    def draw_vals(k):
+        if dyadic:
+            return (rng.integers(-(1 << 20) + 1, 1 << 20, size=k).astype(np.float64) * 2.0 ** -20).astype(dtype)
+        return rng.standard_normal(k).astype(dtype)
+
+    a_rows = rng.integers(0, n_rows, size=m_a).astype(np.int32)
+    a_cols = draw_cols(m_a).astype(np.int32)
+    a_vals = draw_vals(m_a)
+    rows = rng.integers(0, n_rows, size=m).astype(np.int32)
+    cols = draw_cols(m).astype(np.int32)
+    if m_a > 0:
+        hit = rng.random(m) < hit_frac
+        src = rng.integers(0, m_a, size=m)
+        rows[hit] = a_rows[src[hit]]
+        cols[hit] = a_cols[src[hit]]
+    vals = draw_vals(m)
+    vals[rng.random(m) < zero_frac] = 0.0
+    return dict(a_rows=a_rows, a_cols=a_cols, a_vals=a_vals, rows=rows, cols=cols, vals=vals, seq=None,
+                shape=(n_rows, n_cols))
 
 
 def dense_rhs(n, k=16, dtype=np.float32, seed=SEED_BASE + 5):
