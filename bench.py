@@ -53,6 +53,9 @@ def workload_spec(name):
         "update_n8": dict(desc="10^7 new writes (Zipf(1.1) columns, U(-1,1) float64) applied to the 100,000 x "
                                "100,000 CSC matrix that the 10^8-write Zipf stream assembles to, sum mode",
                           m=10_000_000, m_a=100_000_000, n=100_000, dtype=np.float64, mode="sum", kind="update"),
+        "update_small": dict(desc="2*10^6 new writes applied to the 100,000 x 100,000 CSC matrix that 2*10^7 writes of "
+                                  "the Zipf stream assemble to, sum mode (a smaller case, for profiling)",
+                             m=2_000_000, m_a=20_000_000, n=100_000, dtype=np.float64, mode="sum", kind="update"),
         "update_n8_set": dict(desc="as update_n8, last-write mode (the matrix assembled in sum mode)",
                               m=10_000_000, m_a=100_000_000, n=100_000, dtype=np.float64, mode="set",
                               kind="update"),
@@ -393,7 +396,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="n8",
-                    choices=["n8", "zipf3e7", "zipf1e7", "zipf1e7_f32", "fem2048", "update_n8", "update_n8_set"])
+                    choices=["n8", "zipf3e7", "zipf1e7", "zipf1e7_f32", "fem2048", "update_n8", "update_n8_set",
+                             "update_small"])
     ap.add_argument("--cpu-sample", type=int, default=10_000_000, help="writes the CPU oracle baseline times")
     ap.add_argument("--ref-sample", type=int, default=1_000_000, help="writes per step of --impl reference")
     ap.add_argument("--e2e-steps", type=int, default=None)

@@ -58,6 +58,8 @@ struct UScal {
   int64_t nnz_b;    // stored elements of B (written by the assembly)
   uint32_t ticket;  // next tile for k_merge
   int32_t go;       // k_merge runs only if nothing failed before it
+  int32_t bad_a;    // k_split: two of A's elements out of order across a cut
+  int32_t pad;
 };
 
 struct UpdateLayout {
@@ -164,6 +166,7 @@ __global__ void k_split(MergeArgs a) {
   if (t > tiles) return;
   const int64_t d = std::min(t * kTile, L);
   int64_t ia = a.nnz_a, ib = nnz_b;
+  int64_t jhi = a.n_cols;  // the first column starting at or after the cut is at most this
   if (d < L) {
     // column c holding merged position d: the last column whose merged start is <= d
     int64_t lo = 1, hi = a.n_cols;
@@ -185,46 +188,22 @@ __global__ void k_split(MergeArgs a) {
     ib = b0 + off - l2;
     // keep an element of A and the write to the same element in one tile
     if (l2 > 0 && off - l2 < len_b && a.row_a[ia - 1] == a.row_b[ib]) ++ib;
+    // A's elements on either side of the cut, if in one column, must have increasing rows
+    // (k_merge checks the pairs inside a tile)
+    if (l2 > 0 && l2 < len_a && a.row_a[ia - 1] >= a.row_a[ia]) atomicExch(&a.scal->bad_a, (int)SPM_ERR_INVALID_ARG);
+    // column c starts before the cut unless the cut is its start: then the
+    // answer is c + 1, else it lies in [0, c]
+    jhi = (a0 + b0 < ia + ib) ? c + 1 : c;
   }
   const int64_t cut = ia + ib;
   // first column whose merged start is at or after the cut
-  int64_t lo = 0, hi = a.n_cols;
+  int64_t lo = 0, hi = jhi;
+  if (d < L && jhi > 0 && merged_start(a, jhi - 1) < cut) lo = jhi;
   while (lo < hi) {
     const int64_t mid = (lo + hi) >> 1;
     if (merged_start(a, mid) >= cut) hi = mid; else lo = mid + 1;
   }
   a.cuts[t] = Cut{ia, ib, lo, 0};
-}
-
-// In-place inclusive max-scan of v[0, n) (n <= kTileCap) starting from init.
-__device__ void block_max_scan(int32_t* v, int n, int32_t init, int32_t* wtot) {
-  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  int32_t x[kMI];
-  int32_t run = INT_MIN;
-#pragma unroll
-  for (int k = 0; k < kMI; ++k) {
-    const int p = tid * kMI + k;
-    run = max(run, p < n ? v[p] : INT_MIN);
-    x[k] = run;
-  }
-  int32_t inc = run;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int32_t y = __shfl_up_sync(kAll, inc, o);
-    if (lane >= o) inc = max(inc, y);
-  }
-  if (lane == 31) wtot[w] = inc;
-  __syncthreads();
-  int32_t pre = init;
-  for (int u = 0; u < w; ++u) pre = max(pre, wtot[u]);
-  const int32_t ex = __shfl_up_sync(kAll, inc, 1);
-  if (lane > 0) pre = max(pre, ex);
-#pragma unroll
-  for (int k = 0; k < kMI; ++k) {
-    const int p = tid * kMI + k;
-    if (p < n) v[p] = max(pre, x[k]);
-  }
-  __syncthreads();
 }
 
 template <typename VT>
@@ -245,29 +224,34 @@ __device__ __forceinline__ bool nonzero(VT bits) {
 
 template <typename VT>
 constexpr size_t merge_smem_bytes() {
-  return (size_t)kTileCap * (8 + sizeof(VT) + 4) + 4 * ((size_t)kTileCap + 4);
+  return (size_t)kTileCap * (8 + sizeof(VT) + 4);
 }
 
 template <typename VT, bool SUM>
-__global__ void __launch_bounds__(kMT) k_merge(MergeArgs a) {
+__global__ void __launch_bounds__(kMT, 5) k_merge(MergeArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  uint64_t* key = reinterpret_cast<uint64_t*>(smem);             // A's part, then B's part
+  // key: keys (A's part, then B's part), then the output rows (int32);
+  // aux: the column of each element
+  uint64_t* key = reinterpret_cast<uint64_t*>(smem);
   VT* val = reinterpret_cast<VT*>(key + kTileCap);
-  int32_t* row = reinterpret_cast<int32_t*>(val + kTileCap);
-  int32_t* aux = row + kTileCap;                                 // columns, then kept-before counts
+  int32_t* aux = reinterpret_cast<int32_t*>(val + kTileCap);
   __shared__ int32_t s_wtot[kMT / 32];
   __shared__ int64_t s_tile, s_excl;
   __shared__ int32_t s_bad;
+  __shared__ int32_t s_ta[kMT], s_tb[kMT];  // column starts inside the tile, relative to A's and B's part
+  __shared__ int32_t s_texcl[kMT];          // per thread: output slot of its first kept element
+  __shared__ uint32_t s_tmask[kMT];         // per thread: which of its positions are kept
 
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  if (!a.scal->go) return;
-  const int64_t L = a.nnz_a + a.cp_b[a.n_cols];
-  const int64_t tiles = L / kTile + 1;
   if (tid == 0) {
     s_tile = atomicAdd(&a.scal->ticket, 1u);
     s_bad = 0;
   }
+  const int go = *reinterpret_cast<volatile int32_t*>(&a.scal->go);
+  const int64_t L = a.nnz_a + a.cp_b[a.n_cols];
   __syncthreads();
+  if (!go) return;
+  const int64_t tiles = L / kTile + 1;
   const int64_t t = s_tile;
   if (t >= tiles) return;
   const bool last = t == tiles - 1;
@@ -283,41 +267,87 @@ __global__ void __launch_bounds__(kMT) k_merge(MergeArgs a) {
   const VT* va = static_cast<const VT*>(a.val_a);
   const VT* vb = static_cast<const VT*>(a.val_b);
 
-  // load the tile's part of A and of B
-  for (int k = tid; k < n; k += kMT) {
+  // every global load the tile needs before the merge, issued together: its
+  // part of A and B and the column starts inside it
+  int32_t lr[kMI];
+  VT lv[kMI];
+#pragma unroll
+  for (int i = 0; i < kMI; ++i) {
+    const int k = tid + i * kMT;
+    lr[i] = 0;
+    lv[i] = 0;
     if (k < nA) {
-      row[k] = __ldg(a.row_a + c0.a + k);
-      val[k] = __ldg(va + c0.a + k);
-    } else {
-      row[k] = __ldg(a.row_b + c0.b + (k - nA));
-      val[k] = __ldg(vb + c0.b + (k - nA));
+      lr[i] = __ldg(a.row_a + c0.a + k);
+      lv[i] = __ldg(va + c0.a + k);
+    } else if (k < n) {
+      lr[i] = __ldg(a.row_b + c0.b + (k - nA));
+      lv[i] = __ldg(vb + c0.b + (k - nA));
     }
-    aux[k] = -1;
+  }
+  // the column starts inside the tile (nc of them): a table in shared
+  // memory when they are few, else read from global memory
+  const int64_t jcap = jend < a.n_cols ? jend : a.n_cols;
+  const int nc = (int)(jcap > jlo ? (jcap - jlo < INT_MAX ? jcap - jlo : INT_MAX) : 0);
+  const bool table = nc <= kMT;
+  const int64_t j0 = jlo + tid;
+  int64_t cpa0 = 0, cpb0 = 0;
+  if (j0 < jend) {
+    cpa0 = a.cp_a[j0];
+    cpb0 = a.cp_b[j0];
+  }
+  auto clamp_rel = [](int64_t v) { return (int32_t)(v < -1 ? -1 : (v > kTileCap + 1 ? kTileCap + 1 : v)); };
+  if (table && j0 < jcap) {
+    s_ta[tid] = clamp_rel(cpa0 - c0.a);
+    s_tb[tid] = clamp_rel(cpb0 - c0.b);
+  }
+#pragma unroll
+  for (int i = 0; i < kMI; ++i) {
+    const int k = tid + i * kMT;
+    if (k < n) val[k] = lv[i];
   }
   __syncthreads();
-  // column of every element: mark where each column starts, then max-scan
-  for (int64_t j = jlo + tid; j < jend; j += kMT) {
-    if (j >= a.n_cols) break;
-    const int64_t pa = a.cp_a[j] - c0.a, pb = a.cp_b[j] - c0.b;
-    if (pa >= 0 && pa < nA) atomicMax(&aux[pa], (int32_t)j);
-    if (pb >= 0 && pb < nB) atomicMax(&aux[nA + pb], (int32_t)j);
-  }
-  __syncthreads();
-  block_max_scan(aux, (int)nA, (int32_t)(jlo - 1), s_wtot);
-  block_max_scan(aux + nA, (int)nB, (int32_t)(jlo - 1), s_wtot);
+  // column of every element: jlo - 1 plus the number of columns starting
+  // inside the tile at or before it (CSC offsets never decrease)
   const uint64_t nr = (uint64_t)a.n_rows;
-  for (int k = tid; k < n; k += kMT) {
-    const int32_t r = row[k];
-    key[k] = (uint64_t)(uint32_t)aux[k] * nr + (uint64_t)(uint32_t)r;
-    if (k < nA) {
-      // A must be canonical: rows inside the matrix, strictly increasing inside a column
-      if (r < 0 || (int64_t)r >= a.n_rows) s_bad = SPM_ERR_INDEX_OUT_OF_RANGE;
-      else if (k > 0 && aux[k] == aux[k - 1] && row[k - 1] >= r) s_bad = SPM_ERR_INVALID_ARG;
-      else if (k == 0 && c0.a > 0 && a.cp_a[aux[0]] < c0.a && __ldg(a.row_a + c0.a - 1) >= r)
-        s_bad = SPM_ERR_INVALID_ARG;
+  int bad = 0;
+#pragma unroll
+  for (int i = 0; i < kMI; ++i) {
+    const int k = tid + i * kMT;
+    if (k < n) {
+      const bool in_a = k < nA;
+      const int32_t rel = in_a ? k : k - (int)nA;
+      int lo = 0, hi = nc;
+      if (table) {
+        const int32_t* tab = in_a ? s_ta : s_tb;
+        while (lo < hi) {
+          const int mid = (lo + hi) >> 1;
+          if (tab[mid] <= rel) lo = mid + 1; else hi = mid;
+        }
+      } else {
+        const int64_t* cp = (in_a ? a.cp_a : a.cp_b) + jlo;
+        const int64_t base = (in_a ? c0.a : c0.b) + rel;
+        while (lo < hi) {
+          const int mid = (lo + hi) >> 1;
+          if (cp[mid] <= base) lo = mid + 1; else hi = mid;
+        }
+      }
+      const int32_t col = (int32_t)(jlo - 1 + lo);
+      const int32_t r = lr[i];
+      aux[k] = col;
+      key[k] = (uint64_t)(uint32_t)col * nr + (uint64_t)(uint32_t)r;
+      // A must be canonical: rows inside the matrix (order checked below)
+      if (in_a && (r < 0 || (int64_t)r >= a.n_rows)) bad = SPM_ERR_INDEX_OUT_OF_RANGE;
     }
   }
+  if (bad) atomicMax(&s_bad, bad);
   __syncthreads();
+  // ... and strictly increasing linear indices inside A's part of the tile
+  // (k_split checks the pair of A's elements on either side of each cut)
+#pragma unroll
+  for (int i = 0; i < kMI; ++i) {
+    const int k = tid + i * kMT;
+    if (k > 0 && k < nA && key[k] <= key[k - 1]) atomicMax(&s_bad, (int32_t)SPM_ERR_INVALID_ARG);
+  }
 
   // each thread merges kMI consecutive positions (A first on equal keys)
   const int p0 = min(tid * kMI, n);
@@ -336,21 +366,24 @@ __global__ void __launch_bounds__(kMT) k_merge(MergeArgs a) {
     oval[k] = 0;
     if (p0 + k < n) {
       const bool take_a = ib >= nB || (ia < nA && key[ia] <= key[nA + ib]);
+      int src;
       bool out;
+      VT v;
       if (take_a) {
-        orow[k] = row[ia];
-        VT v = val[ia];
+        src = ia;
+        v = val[ia];
         if (ib < nB && key[nA + ib] == key[ia]) v = SUM ? combine_add<VT>(v, val[nA + ib]) : val[nA + ib];
-        oval[k] = v;
         out = true;
         ++ia;
       } else {
-        orow[k] = row[nA + ib];
-        oval[k] = val[nA + ib];
-        out = !(ia > 0 && key[ia - 1] == key[nA + ib]);  // B's half of a combined element
+        src = (int)nA + ib;
+        v = val[src];
+        out = !(ia > 0 && key[ia - 1] == key[src]);  // B's half of a combined element
         ++ib;
       }
-      if (out && nonzero<VT>(oval[k])) kmask |= 1u << k;
+      orow[k] = (int32_t)(key[src] - (uint64_t)(uint32_t)aux[src] * nr);
+      oval[k] = v;
+      if (out && nonzero<VT>(v)) kmask |= 1u << k;
     }
   }
   // exclusive scan of the kept counts over the block
@@ -361,7 +394,7 @@ __global__ void __launch_bounds__(kMT) k_merge(MergeArgs a) {
     const int y = __shfl_up_sync(kAll, inc, o);
     if (lane >= o) inc += y;
   }
-  __syncthreads();  // everyone is done reading the tile (aux is reused below)
+  __syncthreads();  // everyone is done reading the tile (key, val and aux are reused below)
   if (lane == 31) s_wtot[w] = inc;
   __syncthreads();
   int wpre = 0, total = 0;
@@ -370,11 +403,18 @@ __global__ void __launch_bounds__(kMT) k_merge(MergeArgs a) {
     total += s_wtot[u];
   }
   const int excl_t = wpre + inc - cnt;
-  // kept-before counts per merged position, for the column offsets
+  // each thread's first output slot and kept mask (the column offsets read
+  // them); the kept elements staged in output order
+  s_texcl[tid] = excl_t;
+  s_tmask[tid] = kmask;
+  int32_t* srow = reinterpret_cast<int32_t*>(key);
 #pragma unroll
   for (int k = 0; k < kMI; ++k)
-    if (p0 + k < n) aux[p0 + k] = excl_t + __popc(kmask & ((1u << k) - 1u));
-  if (tid == 0) aux[n] = total;
+    if (kmask & (1u << k)) {
+      const int o = excl_t + __popc(kmask & ((1u << k) - 1u));
+      srow[o] = orow[k];
+      val[o] = oval[k];
+    }
 
   // the tile's output offset: decoupled look-back over earlier tiles (bounded wait)
   if (w == 0) {
@@ -403,7 +443,7 @@ __global__ void __launch_bounds__(kMT) k_merge(MergeArgs a) {
           top -= 32;
           continue;
         }
-        __nanosleep(128);
+        __nanosleep(64);
         int stop = 0;
         if (lane == 0 && (++spins & 7) == 0 && now_ns() - t_start > kWaitNs) {
           fail(a.status, SPM_ERR_TIMEOUT);
@@ -417,26 +457,26 @@ __global__ void __launch_bounds__(kMT) k_merge(MergeArgs a) {
   }
   __syncthreads();
   const int64_t excl = s_excl;
-  // stage the kept elements in output order, then write them out coalesced
-#pragma unroll
-  for (int k = 0; k < kMI; ++k)
-    if (kmask & (1u << k)) {
-      const int o = excl_t + __popc(kmask & ((1u << k) - 1u));
-      row[o] = orow[k];
-      val[o] = oval[k];
-    }
-  __syncthreads();
   VT* vo = static_cast<VT*>(a.val_out);
   for (int k = tid; k < total; k += kMT) {
-    a.row_out[excl + k] = row[k];
+    a.row_out[excl + k] = srow[k];
     vo[excl + k] = val[k];
   }
   // column offsets of the columns that start inside this tile
-  for (int64_t j = jlo + tid; j < jend; j += kMT) {
-    const int64_t p = merged_start(a, j) - bd;
-    a.col_ptr[j] = excl + aux[p < 0 ? 0 : (p > n ? n : p)];
+  for (int64_t j = j0; j < jend; j += kMT) {
+    int64_t p = (j == j0 ? cpa0 + cpb0 : merged_start(a, j)) - bd;
+    p = p < 0 ? 0 : (p > n ? n : p);
+    int before = total;  // elements kept before merged position p of the tile
+    if (p < n) {
+      const int th = (int)p / kMI, k = (int)p % kMI;
+      before = s_texcl[th] + __popc(s_tmask[th] & ((1u << k) - 1u));
+    }
+    a.col_ptr[j] = excl + before;
   }
-  if (last && tid == 0) *a.d_nnz = excl + total;
+  if (last && tid == 0) {
+    *a.d_nnz = excl + total;
+    if (a.scal->bad_a) fail(a.status, a.scal->bad_a);
+  }
   if (tid == 0 && s_bad) fail(a.status, s_bad);
 }
 
