@@ -56,6 +56,15 @@ def workload_spec(name):
         "update_small": dict(desc="2*10^6 new writes applied to the 100,000 x 100,000 CSC matrix that 2*10^7 writes of "
                                   "the Zipf stream assemble to, sum mode (a smaller case, for profiling)",
                              m=2_000_000, m_a=20_000_000, n=100_000, dtype=np.float64, mode="sum", kind="update"),
+        "lookup_n8": dict(desc="10^7 element reads (half of them stored elements) from the 100,000 x 100,000 CSC "
+                               "matrix that the 10^8-write Zipf stream assembles to, float64",
+                          q=10_000_000, m_a=100_000_000, n=100_000, dtype=np.float64, mode="sum", kind="lookup"),
+        "coo_n8": dict(desc="coordinate-list export (column of every element, rows and values copied) of the "
+                            "100,000 x 100,000 CSC matrix that the 10^8-write Zipf stream assembles to, float64",
+                       m_a=100_000_000, n=100_000, dtype=np.float64, mode="sum", kind="coo"),
+        "trace_10k": dict(desc="trace(A^T B) of two random 10,000 x 10,000 CSC matrices (uniform coordinates, "
+                               "N(0,1) float64) at density 10 %; densities 0.01 %, 0.1 %, 1 % timed beside it",
+                          n=10_000, density=0.1, dtype=np.float64, kind="trace"),
         "update_n8_set": dict(desc="as update_n8, last-write mode (the matrix assembled in sum mode)",
                               m=10_000_000, m_a=100_000_000, n=100_000, dtype=np.float64, mode="set",
                               kind="update"),
@@ -336,6 +345,131 @@ def run_update(args, world, rank, local_rank):
         torch.distributed.destroy_process_group()
 
 
+def run_access(args, world, rank, local_rank):
+    """Element lookup, coordinate-list export or trace(A^T B): CUDA events
+    around each call, inputs resident in HBM."""
+    import numpy as np
+    import torch
+
+    import paper_1805_03380_gb300 as spm
+    import workloads
+    spec = workload_spec(args.workload)
+    kind = spec["kind"]
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    sv = np.dtype(spec["dtype"]).itemsize
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, steps):
+        for _ in range(args.warmup):
+            fn()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        torch.cuda.synchronize()
+        for e0, e1 in ev:
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+        torch.cuda.synchronize()
+        return statistics.mean(e0.elapsed_time(e1) for e0, e1 in ev)
+
+    def matrix_from(d):
+        r, c, v = (torch.from_numpy(d[k]).to(dev) for k in ("rows", "cols", "vals"))
+        A = spm.assemble_csc(r, c, v, d["shape"], mode="sum" if kind != "trace" else "set")
+        return A.col_ptr, A.row_idx.clone(), A.vals.clone(), d["shape"]
+
+    d_status = torch.zeros(1, dtype=torch.int32, device=dev)
+    extra = {}
+    launches0 = spm.spm_debug_launch_count()
+    if kind in ("lookup", "coo"):
+        cp, ri, v, shape = matrix_from(workloads.zipf_batch(m=spec["m_a"], n=spec["n"], dtype=spec["dtype"],
+                                                            seed=workloads.SEED_BASE + 2 + 1000 * rank))
+        nnz = ri.numel()
+        n_cols = shape[1]
+        if kind == "lookup":
+            q = spec["q"]
+            g = torch.Generator(device=dev)
+            g.manual_seed(workloads.SEED_BASE + 9 + rank)
+            colj = torch.repeat_interleave(torch.arange(n_cols, device=dev, dtype=torch.int32), cp.diff())
+            pick = torch.randint(0, nnz, (q,), device=dev, generator=g)
+            hit = torch.rand(q, device=dev, generator=g) < 0.5
+            qr = torch.where(hit, ri[pick], torch.randint(0, shape[0], (q,), device=dev, generator=g,
+                                                          dtype=torch.int32))
+            qc = torch.where(hit, colj[pick], torch.randint(0, n_cols, (q,), device=dev, generator=g,
+                                                            dtype=torch.int32))
+            del colj, pick, hit
+            out = torch.empty(q, dtype=v.dtype, device=dev)
+            pos = torch.empty(q, dtype=torch.int64, device=dev)
+            launches0 = spm.spm_debug_launch_count()
+            ms = timed(lambda: spm.spm_csc_lookup(shape[0], n_cols, cp, ri, v, qr, qc, out, pos, d_status), args.steps)
+            units = q
+            unit = "reads/s"
+            metric = "element reads from a CSC matrix per second (column start + binary search)"
+            alg = q * (4 + 4 + sv + 8) + q * 16
+            formula = "q*(4+4+sv+8) + q*16 (query in, value and position out, the column's two offsets)"
+            kernel = "k_lookup (one thread per read)"
+            extra = {"stored_fraction": float((pos >= 0).double().mean().item())}
+        else:
+            o_r, o_c, o_v = torch.empty_like(ri), torch.empty_like(ri), torch.empty_like(v)
+            launches0 = spm.spm_debug_launch_count()
+            ms = timed(lambda: spm.spm_csc_to_coo(n_cols, cp, ri, v, o_r, o_c, o_v, d_status), args.steps)
+            units = nnz
+            unit = "elements/s"
+            metric = "elements exported from CSC to a coordinate list per second"
+            alg = nnz * (4 + sv + 4 + 4 + sv) + (n_cols + 1) * 8
+            formula = "nnz*(4+sv read + 4+4+sv written) + (n_cols+1)*8"
+            kernel = "k_to_coo (tile of 2048 elements per block)"
+        extra.update({"nnz": nnz, "n_rows": shape[0], "n_cols": n_cols})
+    else:
+        per = {}
+        for dens in (0.0001, 0.001, 0.01, spec["density"]):
+            A = matrix_from(workloads.density_sweep(dens, n=spec["n"], dtype=spec["dtype"],
+                                                    seed=workloads.SEED_BASE + 6 + 1000 * rank))
+            B = matrix_from(workloads.density_sweep(dens, n=spec["n"], dtype=spec["dtype"],
+                                                    seed=workloads.SEED_BASE + 16 + 1000 * rank))
+            ws = torch.empty(spm.spm_csc_trace_atb_workspace(spec["n"], A[1].numel(), B[1].numel()),
+                             dtype=torch.uint8, device=dev)
+            res = torch.zeros(1, dtype=torch.float64, device=dev)
+
+            def call():
+                spm.spm_csc_trace_atb(spec["n"], spec["n"], A[0], A[1], A[2], B[0], B[1], B[2], res, d_status, ws)
+            launches0 = spm.spm_debug_launch_count()
+            ms_d = timed(call, args.steps)
+            per[f"{dens * 100:g}%"] = {"ms": ms_d, "nnz_a": A[1].numel(), "nnz_b": B[1].numel(),
+                                       "trace": float(res.item())}
+        ms = per[f"{spec['density'] * 100:g}%"]["ms"]
+        nnz_a, nnz_b = per[f"{spec['density'] * 100:g}%"]["nnz_a"], per[f"{spec['density'] * 100:g}%"]["nnz_b"]
+        units = nnz_a + nnz_b
+        unit = "elements/s"
+        metric = "elements of A and B reduced into trace(A^T B) per second"
+        alg = (nnz_a + nnz_b) * (4 + sv) + 2 * (spec["n"] + 1) * 8
+        formula = "(nnz_a + nnz_b)*(4+sv) + 2*(n_cols+1)*8"
+        kernel = "whole call (offset checks, cuts, k_merge in dot form, final sum)"
+        extra = {"densities": per}
+    launches = spm.spm_debug_launch_count() - launches0
+    torch.cuda.synchronize()
+    if int(d_status.item()) != 0:
+        raise RuntimeError(f"device status {int(d_status.item())}")
+    tot_s, tot_units = aggregate(ms / 1000.0 * args.steps, units * args.steps, world, dev)
+    peak, peak_kind = measured_peak()
+    achieved = alg / (ms / 1000.0) / 1e9
+    if rank == 0:
+        print(json.dumps({
+            "metric": metric, "value": tot_units / tot_s, "unit": unit, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if sv == 8 else "f32", "data": "synthetic",
+            "config": dict({"workload": args.workload, "description": spec["desc"]}, **extra),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind + " copy bandwidth",
+                         "kernel": kernel, "algorithmic_bytes_per_launch": alg, "bytes_formula": formula,
+                         "launch_ms_mean": ms},
+            "gpu_launches": launches, "gpu": torch.cuda.get_device_name(dev)}), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
 def run_reference(args, world, rank):
     import numpy as np  # noqa: F401
     import workloads
@@ -343,6 +477,10 @@ def run_reference(args, world, rank):
         return
     spec = workload_spec(args.workload)
     sample = args.ref_sample
+    if spec["kind"] in ("lookup", "coo", "trace"):
+        print(json.dumps({"impl": "reference", "unavailable": "the CPU reference leg times the assembly and update "
+                                                              "workloads only"}), flush=True)
+        return
     if spec["kind"] == "update":
         sample = min(sample, 200_000)
         times = []
@@ -397,7 +535,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="n8",
                     choices=["n8", "zipf3e7", "zipf1e7", "zipf1e7_f32", "fem2048", "update_n8", "update_n8_set",
-                             "update_small"])
+                             "update_small", "lookup_n8", "coo_n8", "trace_10k"])
     ap.add_argument("--cpu-sample", type=int, default=10_000_000, help="writes the CPU oracle baseline times")
     ap.add_argument("--ref-sample", type=int, default=1_000_000, help="writes per step of --impl reference")
     ap.add_argument("--e2e-steps", type=int, default=None)
@@ -415,6 +553,9 @@ def main():
         return
     if workload_spec(args.workload)["kind"] == "update":
         run_update(args, world, rank, local_rank)
+        return
+    if workload_spec(args.workload)["kind"] in ("lookup", "coo", "trace"):
+        run_access(args, world, rank, local_rank)
         return
 
     import numpy as np

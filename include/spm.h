@@ -243,6 +243,71 @@ spm_status spm_csc_update(int64_t n_rows, int64_t n_cols, const int64_t* a_col_p
                           void* workspace, size_t ws_bytes, void* stream);
 
 /*
+ * spm_csc_lookup -- values of q elements of a canonical CSC matrix
+ * (Section 3.1: one read of the column's start and end, then a binary search
+ * among the column's row indices; an element that is not stored reads 0).
+ *
+ *   col_ptr int64[n_cols+1], row_idx int32[nnz], vals (dtype)[nnz]   the matrix
+ *           (rows strictly increasing inside each column; otherwise the
+ *           results are unspecified; offsets that are not 0 .. nnz and
+ *           non-decreasing set *d_status = SPM_ERR_INVALID_ARG)
+ *   q_rows, q_cols  int32[q]   the elements asked for; one outside the matrix
+ *                              sets *d_status = SPM_ERR_INDEX_OUT_OF_RANGE and
+ *                              reads 0
+ *   out_vals  (dtype)[q]       the values (0 where not stored)
+ *   out_pos   NULL or int64[q] the element's index in row_idx / vals, or -1
+ *   d_status  int32[1]         set to SPM_OK first, see the conventions
+ */
+spm_status spm_csc_lookup(int64_t n_rows, int64_t n_cols, int64_t nnz, const int64_t* col_ptr, const int32_t* row_idx,
+                          const void* vals, spm_dtype dtype, int64_t q, const int32_t* q_rows, const int32_t* q_cols,
+                          void* out_vals, int64_t* out_pos, int32_t* d_status, void* stream);
+
+/*
+ * spm_csc_to_coo -- the coordinate list (Section 3.2) of a CSC matrix, in
+ * the CSC's order: out_cols[e] is the column of stored element e; with
+ * out_rows / out_vals not NULL the row indices and values are copied there
+ * too (the CSC arrays already hold them, so they may also be used as they
+ * are).  The reverse conversion is spm_assemble_csc.
+ *
+ *   col_ptr int64[n_cols+1]  offsets 0 .. nnz, non-decreasing (otherwise
+ *                            *d_status = SPM_ERR_INVALID_ARG and the output
+ *                            is unspecified)
+ *   row_idx int32[nnz], vals (dtype)[nnz]   read only for the copies
+ *   out_rows NULL or int32[nnz], out_cols int32[nnz], out_vals NULL or (dtype)[nnz]
+ *   d_status int32[1]        set to SPM_OK first
+ */
+spm_status spm_csc_to_coo(int64_t n_cols, int64_t nnz, const int64_t* col_ptr, const int32_t* row_idx,
+                          const void* vals, spm_dtype dtype, int32_t* out_rows, int32_t* out_cols, void* out_vals,
+                          int32_t* d_status, void* stream);
+
+/*
+ * spm_csc_trace_atb_workspace / spm_csc_trace_atb -- trace(A^T B) for two
+ * canonical n_rows x n_cols CSC matrices, without forming the transpose or
+ * the product (Section 2: only the diagonal of A^T B is accumulated; the
+ * paper's second timed workload, Fig. 1b).  It equals the sum, over the
+ * elements stored in both matrices, of A(i,j) * B(i,j).
+ *
+ *   a_col_ptr, a_row_idx, a_vals, nnz_a   A (rows strictly increasing inside
+ *   b_col_ptr, b_row_idx, b_vals, nnz_b   each column), B likewise; malformed
+ *                                         offsets or rows set *d_status =
+ *                                         SPM_ERR_INVALID_ARG, a row outside
+ *                                         the matrix SPM_ERR_INDEX_OUT_OF_RANGE
+ *   dtype       the value type of both
+ *   d_result    double[1]  the trace: products and sums in double precision;
+ *               the sum is taken in a fixed order for given nnz_a, nnz_b and
+ *               structure, so repeated calls give the same bits
+ *   d_status    int32[1]   set to SPM_OK first
+ *   workspace   at least spm_csc_trace_atb_workspace() bytes (about 40
+ *               bytes per 2047 elements of A and B together)
+ */
+spm_status spm_csc_trace_atb_workspace(int64_t n_cols, int64_t nnz_a, int64_t nnz_b, size_t* bytes);
+
+spm_status spm_csc_trace_atb(int64_t n_rows, int64_t n_cols, const int64_t* a_col_ptr, const int32_t* a_row_idx,
+                             const void* a_vals, int64_t nnz_a, const int64_t* b_col_ptr, const int32_t* b_row_idx,
+                             const void* b_vals, int64_t nnz_b, spm_dtype dtype, double* d_result, int32_t* d_status,
+                             void* workspace, size_t ws_bytes, void* stream);
+
+/*
  * spm_csc_mm -- Y = A X (transpose = 0) or Y = A^T X (transpose = 1) for A in
  * CSC (Section 3.1; the paper's use cases (iv) "multiplication of dense
  * vectors with sparse matrices", Fig. 2 "W = V * X").

@@ -22,7 +22,8 @@ import torch
 __all__ = [
     "SpmError", "lib", "spm_assemble_csc", "spm_assemble_csc_workspace", "spm_assemble_csc_batched",
     "spm_assemble_csc_batched_workspace", "spm_csc_mm", "spm_triplet_dvals", "spm_set_tuning", "spm_get_tuning",
-    "spm_csc_update", "spm_csc_update_workspace",
+    "spm_csc_update", "spm_csc_update_workspace", "spm_csc_lookup", "spm_csc_to_coo", "csc_lookup", "csc_to_coo",
+    "spm_csc_trace_atb", "spm_csc_trace_atb_workspace", "csc_trace_atb",
     "assemble_csc", "assemble_csc_batched", "csc_update", "csc_mm", "triplet_dvals", "AssembleMM", "Assembler", "CSC",
     "MODE_LAST_WRITE", "MODE_SUM", "KEEP_MAP", "SEQ_EXPLICIT", "LIB_PATH",
 ]
@@ -40,7 +41,8 @@ EXPORTED = ["spm_status_string", "spm_version", "spm_assemble_csc_workspace", "s
             "spm_assemble_csc_batched_workspace", "spm_assemble_csc_batched", "spm_csc_mm", "spm_triplet_dvals",
             "spm_set_tuning", "spm_get_tuning", "spm_debug_withhold_publication", "spm_debug_stage_timing",
             "spm_debug_stage_times", "spm_debug_launch_count", "spm_debug_plan_stats", "spm_assemble_csc_static",
-            "spm_csc_update_workspace", "spm_csc_update"]
+            "spm_csc_update_workspace", "spm_csc_update", "spm_csc_lookup", "spm_csc_to_coo",
+            "spm_csc_trace_atb_workspace", "spm_csc_trace_atb"]
 
 
 class SpmError(RuntimeError):
@@ -82,6 +84,10 @@ def lib():
     L.spm_csc_update_workspace.argtypes = [i64, i64, i64, i64, ctypes.c_int, ctypes.c_int, u32, ctypes.POINTER(sz)]
     L.spm_csc_update.argtypes = [i64, i64, p, p, p, i64, i64, p, p, p, p, ctypes.c_int, ctypes.c_int, u32, p, p, p,
                                  p, p, p, sz, p]
+    L.spm_csc_lookup.argtypes = [i64, i64, i64, p, p, p, ctypes.c_int, i64, p, p, p, p, p, p]
+    L.spm_csc_to_coo.argtypes = [i64, i64, p, p, p, ctypes.c_int, p, p, p, p, p]
+    L.spm_csc_trace_atb_workspace.argtypes = [i64, i64, i64, ctypes.POINTER(sz)]
+    L.spm_csc_trace_atb.argtypes = [i64, i64, p, p, p, i64, p, p, p, i64, ctypes.c_int, p, p, p, sz, p]
     L.spm_csc_mm.argtypes = [i64, i64, p, p, p, ctypes.c_int, i32, i64, p, i64, p, i64, p]
     L.spm_triplet_dvals.argtypes = [i64, p, p, p, ctypes.c_int, i64, p, i64, p, i64, p, p]
     L.spm_set_tuning.argtypes = [ctypes.POINTER(_Tuning)]
@@ -178,6 +184,42 @@ def spm_csc_update(n_rows, n_cols, a_col_ptr, a_row_idx, a_vals, rows, cols, val
                                 _ptr(out_vals), _ptr(d_nnz), _ptr(d_status), _ptr(workspace),
                                 workspace.numel() * workspace.element_size(), _stream(stream))
     _check(code, "spm_csc_update")
+
+
+def spm_csc_lookup(n_rows, n_cols, col_ptr, row_idx, vals, q_rows, q_cols, out_vals, out_pos, d_status,
+                   stream=None):
+    """Values of the elements (q_rows[i], q_cols[i]) of a CSC matrix (0 where not stored)."""
+    code = lib().spm_csc_lookup(int(n_rows), int(n_cols), row_idx.numel(), _ptr(col_ptr), _ptr(row_idx), _ptr(vals),
+                                _dtype_code(vals.dtype), q_rows.numel(), _ptr(q_rows), _ptr(q_cols), _ptr(out_vals),
+                                _ptr(out_pos), _ptr(d_status), _stream(stream))
+    _check(code, "spm_csc_lookup")
+
+
+def spm_csc_to_coo(n_cols, col_ptr, row_idx, vals, out_rows, out_cols, out_vals, d_status, stream=None):
+    """Column of every stored element (and copies of rows and values when given)."""
+    code = lib().spm_csc_to_coo(int(n_cols), row_idx.numel(), _ptr(col_ptr), _ptr(row_idx), _ptr(vals),
+                                _dtype_code(vals.dtype), _ptr(out_rows), _ptr(out_cols), _ptr(out_vals),
+                                _ptr(d_status), _stream(stream))
+    _check(code, "spm_csc_to_coo")
+
+
+def spm_csc_trace_atb_workspace(n_cols, nnz_a, nnz_b):
+    out = ctypes.c_size_t(0)
+    _check(lib().spm_csc_trace_atb_workspace(int(n_cols), int(nnz_a), int(nnz_b), ctypes.byref(out)),
+           "spm_csc_trace_atb_workspace")
+    return int(out.value)
+
+
+def spm_csc_trace_atb(n_rows, n_cols, a_col_ptr, a_row_idx, a_vals, b_col_ptr, b_row_idx, b_vals, d_result, d_status,
+                      workspace, stream=None):
+    """trace(A^T B) of two CSC matrices into the device double d_result."""
+    if a_vals.dtype != b_vals.dtype:
+        raise TypeError("A and B must have the same value type")
+    code = lib().spm_csc_trace_atb(int(n_rows), int(n_cols), _ptr(a_col_ptr), _ptr(a_row_idx), _ptr(a_vals),
+                                   a_row_idx.numel(), _ptr(b_col_ptr), _ptr(b_row_idx), _ptr(b_vals),
+                                   b_row_idx.numel(), _dtype_code(a_vals.dtype), _ptr(d_result), _ptr(d_status),
+                                   _ptr(workspace), workspace.numel() * workspace.element_size(), _stream(stream))
+    _check(code, "spm_csc_trace_atb")
 
 
 def _host_i64(a):
@@ -356,10 +398,7 @@ def assemble_csc(rows, cols, vals, shape, mode="set", seq=None, keep_map=False, 
 def csc_update(a, rows, cols, vals, mode="set", seq=None, stream=None):
     """The CSC ``a`` (a CSC tuple, or (col_ptr, row_idx, vals, shape)) after the
     element writes (rows, cols, vals[, seq]); a new CSC, ``a`` is not modified."""
-    if isinstance(a, CSC):
-        a_cp, a_ri, a_v, shape = a.col_ptr, a.row_idx, a.vals, a.shape
-    else:
-        a_cp, a_ri, a_v, shape = a
+    a_cp, a_ri, a_v, shape = _csc_parts(a)
     n_rows, n_cols = int(shape[0]), int(shape[1])
     vals = torch.as_tensor(vals)
     if not vals.is_cuda:
@@ -392,6 +431,68 @@ def csc_update(a, rows, cols, vals, mode="set", seq=None, stream=None):
     _raise_status(d_status, "spm_csc_update")
     nnz = int(d_nnz.item())
     return CSC(col_ptr, row_idx[:nnz], out_vals[:nnz], nnz, None, (n_rows, n_cols))
+
+
+def _csc_parts(a):
+    if isinstance(a, CSC):
+        return a.col_ptr, a.row_idx, a.vals, a.shape
+    return a
+
+
+def csc_lookup(a, rows, cols, stream=None):
+    """Values (0 where not stored) and positions (-1 where not stored) of the
+    elements (rows[i], cols[i]) of the CSC ``a`` (a CSC tuple, or
+    (col_ptr, row_idx, vals, shape))."""
+    cp, ri, v, shape = _csc_parts(a)
+    dev = v.device
+    rows, cols = _as_index(rows, dev), _as_index(cols, dev)
+    if rows.numel() != cols.numel():
+        raise ValueError("rows and cols must have the same length")
+    cp = torch.as_tensor(cp, device=dev).to(torch.int64).contiguous()
+    ri, v = _as_index(ri, dev), v.contiguous()
+    out = torch.empty(rows.numel(), dtype=v.dtype, device=dev)
+    pos = torch.empty(rows.numel(), dtype=torch.int64, device=dev)
+    d_status = torch.zeros(1, dtype=torch.int32, device=dev)
+    spm_csc_lookup(shape[0], shape[1], cp, ri, v, rows, cols, out, pos, d_status, stream)
+    (stream if stream is not None else torch.cuda.current_stream()).synchronize()
+    _raise_status(d_status, "spm_csc_lookup")
+    return out, pos
+
+
+def csc_trace_atb(a, b, stream=None):
+    """trace(A^T B) (a Python float) of the CSC matrices ``a`` and ``b`` of one shape."""
+    acp, ari, av, shape = _csc_parts(a)
+    bcp, bri, bv, bshape = _csc_parts(b)
+    if tuple(shape) != tuple(bshape):
+        raise ValueError("A and B must have the same shape")
+    dev = av.device
+    acp = torch.as_tensor(acp, device=dev).to(torch.int64).contiguous()
+    bcp = torch.as_tensor(bcp, device=dev).to(torch.int64).contiguous()
+    ari, bri = _as_index(ari, dev), _as_index(bri, dev)
+    av, bv = av.contiguous(), bv.contiguous()
+    ws = torch.empty(spm_csc_trace_atb_workspace(shape[1], ari.numel(), bri.numel()), dtype=torch.uint8, device=dev)
+    res = torch.zeros(1, dtype=torch.float64, device=dev)
+    d_status = torch.zeros(1, dtype=torch.int32, device=dev)
+    spm_csc_trace_atb(shape[0], shape[1], acp, ari, av, bcp, bri, bv, res, d_status, ws, stream)
+    (stream if stream is not None else torch.cuda.current_stream()).synchronize()
+    _raise_status(d_status, "spm_csc_trace_atb")
+    return float(res.item())
+
+
+def csc_to_coo(a, stream=None):
+    """Coordinate list (rows, cols, vals) of the CSC ``a``, in column-major order."""
+    cp, ri, v, shape = _csc_parts(a)
+    dev = v.device
+    cp = torch.as_tensor(cp, device=dev).to(torch.int64).contiguous()
+    ri, v = _as_index(ri, dev), v.contiguous()
+    rows = torch.empty_like(ri)
+    cols = torch.empty_like(ri)
+    vals = torch.empty_like(v)
+    d_status = torch.zeros(1, dtype=torch.int32, device=dev)
+    spm_csc_to_coo(shape[1], cp, ri, v, rows, cols, vals, d_status, stream)
+    (stream if stream is not None else torch.cuda.current_stream()).synchronize()
+    _raise_status(d_status, "spm_csc_to_coo")
+    return rows, cols, vals
 
 
 def assemble_csc_batched(rows, cols, vals, n_rows, n_cols, trip_ptr, mode="set", seq=None, keep_map=False):

@@ -25,6 +25,13 @@
 //      columns that start inside the tile.  It also checks that A is
 //      canonical (rows inside [0, n_rows), strictly increasing inside a
 //      column).
+//
+// The same cuts and tiles compute trace(A^T B) for two CSC matrices of one
+// shape (Section 2: the expression is evaluated without forming the
+// transpose or the product, by accumulating only the diagonal of A^T B, which
+// is the sum over the elements stored in both of A(i,j) * B(i,j); Fig. 1b).
+// k_merge in its dot form multiplies the pairs of each tile and writes one
+// partial sum per tile; k_dot_sum adds them in tile order.
 #include <algorithm>
 #include <climits>
 #include <cstdint>
@@ -45,6 +52,7 @@ constexpr uint64_t kAgg = 1ull << 62;         // tile look-back states
 constexpr uint64_t kIncl = 2ull << 62;
 constexpr uint64_t kValMask = (1ull << 62) - 1;
 constexpr uint64_t kWaitNs = 2000000000ull;   // look-back wait limit
+constexpr int kOpSet = 0, kOpSum = 1, kOpDot = 2;
 
 size_t align256(size_t x) { return (x + 255) & ~size_t{255}; }
 
@@ -147,6 +155,8 @@ struct MergeArgs {
   void* val_out;
   int64_t* d_nnz;
   int32_t* status;
+  double* partial;  // trace: one partial sum per tile
+  int32_t check_b;  // B is an input (the trace): check that it is canonical too
 };
 
 // Merged start of column j: its elements in A before it plus those in B.
@@ -191,6 +201,8 @@ __global__ void k_split(MergeArgs a) {
     // A's elements on either side of the cut, if in one column, must have increasing rows
     // (k_merge checks the pairs inside a tile)
     if (l2 > 0 && l2 < len_a && a.row_a[ia - 1] >= a.row_a[ia]) atomicExch(&a.scal->bad_a, (int)SPM_ERR_INVALID_ARG);
+    if (a.check_b && ib > b0 && ib < b0 + len_b && a.row_b[ib - 1] >= a.row_b[ib])
+      atomicExch(&a.scal->bad_a, (int)SPM_ERR_INVALID_ARG);
     // column c starts before the cut unless the cut is its start: then the
     // answer is c + 1, else it lies in [0, c]
     jhi = (a0 + b0 < ia + ib) ? c + 1 : c;
@@ -218,6 +230,11 @@ __device__ __forceinline__ uint64_t combine_add<uint64_t>(uint64_t x, uint64_t y
 }
 
 template <typename VT>
+__device__ __forceinline__ double as_double(VT bits) {
+  return sizeof(VT) == 8 ? __longlong_as_double((long long)bits) : (double)__uint_as_float((uint32_t)bits);
+}
+
+template <typename VT>
 __device__ __forceinline__ bool nonzero(VT bits) {
   return sizeof(VT) == 8 ? ((uint64_t)bits & 0x7FFFFFFFFFFFFFFFull) != 0 : ((uint32_t)bits & 0x7FFFFFFFu) != 0;
 }
@@ -227,8 +244,11 @@ constexpr size_t merge_smem_bytes() {
   return (size_t)kTileCap * (8 + sizeof(VT) + 4);
 }
 
-template <typename VT, bool SUM>
+// OP: kOpSet / kOpSum merge A with the resolved writes B (the update);
+// kOpDot accumulates the products of the elements present in both (the trace).
+template <typename VT, int OP>
 __global__ void __launch_bounds__(kMT, 5) k_merge(MergeArgs a) {
+  constexpr bool SUM = OP == kOpSum;
   extern __shared__ __align__(16) unsigned char smem[];
   // key: keys (A's part, then B's part), then the output rows (int32);
   // aux: the column of each element
@@ -335,8 +355,9 @@ __global__ void __launch_bounds__(kMT, 5) k_merge(MergeArgs a) {
       const int32_t r = lr[i];
       aux[k] = col;
       key[k] = (uint64_t)(uint32_t)col * nr + (uint64_t)(uint32_t)r;
-      // A must be canonical: rows inside the matrix (order checked below)
-      if (in_a && (r < 0 || (int64_t)r >= a.n_rows)) bad = SPM_ERR_INDEX_OUT_OF_RANGE;
+      // A (and B when it is an input) must be canonical: rows inside the
+      // matrix (order checked below)
+      if ((in_a || a.check_b) && (r < 0 || (int64_t)r >= a.n_rows)) bad = SPM_ERR_INDEX_OUT_OF_RANGE;
     }
   }
   if (bad) atomicMax(&s_bad, bad);
@@ -347,6 +368,7 @@ __global__ void __launch_bounds__(kMT, 5) k_merge(MergeArgs a) {
   for (int i = 0; i < kMI; ++i) {
     const int k = tid + i * kMT;
     if (k > 0 && k < nA && key[k] <= key[k - 1]) atomicMax(&s_bad, (int32_t)SPM_ERR_INVALID_ARG);
+    if (a.check_b && k > nA && k < n && key[k] <= key[k - 1]) atomicMax(&s_bad, (int32_t)SPM_ERR_INVALID_ARG);
   }
 
   // each thread merges kMI consecutive positions (A first on equal keys)
@@ -357,6 +379,34 @@ __global__ void __launch_bounds__(kMT, 5) k_merge(MergeArgs a) {
     if (key[mid] <= key[nA + p0 - 1 - mid]) lo = mid + 1; else hi = mid;
   }
   int ia = lo, ib = p0 - lo;
+  if (OP == kOpDot) {
+    // products of the elements present in A and in B (each such pair is adjacent, A first)
+    double acc = 0.0;
+#pragma unroll
+    for (int k = 0; k < kMI; ++k) {
+      if (p0 + k < n) {
+        const bool take_a = ib >= nB || (ia < nA && key[ia] <= key[nA + ib]);
+        if (take_a) {
+          if (ib < nB && key[nA + ib] == key[ia]) acc = fma(as_double<VT>(val[ia]), as_double<VT>(val[nA + ib]), acc);
+          ++ia;
+        } else {
+          ++ib;
+        }
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kAll, acc, o);
+    __shared__ double s_part[kMT / 32];
+    if (lane == 0) s_part[w] = acc;
+    __syncthreads();
+    if (tid == 0) {
+      double sum = 0.0;
+      for (int u = 0; u < kMT / 32; ++u) sum += s_part[u];
+      a.partial[t] = sum;
+      if (s_bad) fail(a.status, s_bad);
+    }
+    return;
+  }
   int32_t orow[kMI];
   VT oval[kMI];
   uint32_t kmask = 0;
@@ -480,13 +530,37 @@ __global__ void __launch_bounds__(kMT, 5) k_merge(MergeArgs a) {
   if (tid == 0 && s_bad) fail(a.status, s_bad);
 }
 
-template <typename VT, bool SUM>
+template <typename VT, int OP>
 cudaError_t launch_merge(const MergeArgs& args, int64_t tiles_max, cudaStream_t st) {
   constexpr size_t smem = merge_smem_bytes<VT>();
-  cudaError_t e = cudaFuncSetAttribute(k_merge<VT, SUM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(k_merge<VT, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_merge<VT, SUM><<<(unsigned)tiles_max, kMT, smem, st>>>(args);
+  k_merge<VT, OP><<<(unsigned)tiles_max, kMT, smem, st>>>(args);
   return cudaGetLastError();
+}
+
+// The trace: the sum of the tiles' partial sums, in tile order (one block,
+// so the result does not depend on timing), and the checks of k_split.
+__global__ void __launch_bounds__(1024) k_dot_sum(MergeArgs a, double* result) {
+  __shared__ double s_w[32];
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int go = a.scal->go;
+  double acc = 0.0;
+  if (go) {
+    const int64_t L = a.nnz_a + a.cp_b[a.n_cols];
+    const int64_t tiles = L / kTile + 1;
+    for (int64_t t = tid; t < tiles; t += blockDim.x) acc += a.partial[t];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kAll, acc, o);
+  if (lane == 0) s_w[w] = acc;
+  __syncthreads();
+  if (tid == 0) {
+    double sum = 0.0;
+    for (int u = 0; u < (int)(blockDim.x / 32); ++u) sum += s_w[u];
+    *result = go ? sum : 0.0;
+    if (a.scal->bad_a) fail(a.status, a.scal->bad_a);
+  }
 }
 
 }  // namespace
@@ -520,7 +594,7 @@ spm_status spm_csc_update(int64_t n_rows, int64_t n_cols, const int64_t* a_col_p
   if (!workspace || ws_bytes < L.total) return SPM_ERR_WORKSPACE_TOO_SMALL;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   char* ws = static_cast<char*>(workspace);
-  MergeArgs a;
+  MergeArgs a = {};
   a.n_rows = n_rows;
   a.n_cols = n_cols;
   a.nnz_a = nnz_a;
@@ -551,12 +625,91 @@ spm_status spm_csc_update(int64_t n_rows, int64_t n_cols, const int64_t* a_col_p
   k_split<<<(unsigned)((L.tiles_max + 1 + 255) / 256), 256, 0, st>>>(a);
   cudaError_t e;
   if (dtype == SPM_F64)
-    e = mode == SPM_MODE_SUM ? launch_merge<uint64_t, true>(a, L.tiles_max, st)
-                             : launch_merge<uint64_t, false>(a, L.tiles_max, st);
+    e = mode == SPM_MODE_SUM ? launch_merge<uint64_t, kOpSum>(a, L.tiles_max, st)
+                             : launch_merge<uint64_t, kOpSet>(a, L.tiles_max, st);
   else
-    e = mode == SPM_MODE_SUM ? launch_merge<uint32_t, true>(a, L.tiles_max, st)
-                             : launch_merge<uint32_t, false>(a, L.tiles_max, st);
+    e = mode == SPM_MODE_SUM ? launch_merge<uint32_t, kOpSum>(a, L.tiles_max, st)
+                             : launch_merge<uint32_t, kOpSet>(a, L.tiles_max, st);
   spm::count_launches(3);
+  if (e != cudaSuccess || cudaGetLastError() != cudaSuccess) return SPM_ERR_CUDA;
+  return SPM_OK;
+}
+
+namespace {
+
+struct TraceLayout {
+  size_t scal, cuts, partial, total;
+  int64_t tiles_max;
+};
+
+spm_status trace_layout(int64_t n_cols, int64_t nnz_a, int64_t nnz_b, TraceLayout& L) {
+  if (n_cols < 0 || nnz_a < 0 || nnz_b < 0) return SPM_ERR_INVALID_ARG;
+  if (n_cols > INT32_MAX || nnz_a + nnz_b >= (int64_t{1} << 40)) return SPM_ERR_UNSUPPORTED;
+  L.tiles_max = tiles_upper(nnz_a, nnz_b);
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = o;
+    o = align256(o + bytes);
+    return at;
+  };
+  L.scal = take(sizeof(UScal));
+  L.cuts = take(sizeof(Cut) * ((size_t)L.tiles_max + 1));
+  L.partial = take(8 * (size_t)L.tiles_max);
+  L.total = o;
+  return SPM_OK;
+}
+
+}  // namespace
+
+spm_status spm_csc_trace_atb_workspace(int64_t n_cols, int64_t nnz_a, int64_t nnz_b, size_t* bytes) {
+  if (!bytes) return SPM_ERR_INVALID_ARG;
+  TraceLayout L;
+  const spm_status s = trace_layout(n_cols, nnz_a, nnz_b, L);
+  if (s != SPM_OK) return s;
+  *bytes = L.total;
+  return SPM_OK;
+}
+
+spm_status spm_csc_trace_atb(int64_t n_rows, int64_t n_cols, const int64_t* a_col_ptr, const int32_t* a_row_idx,
+                             const void* a_vals, int64_t nnz_a, const int64_t* b_col_ptr, const int32_t* b_row_idx,
+                             const void* b_vals, int64_t nnz_b, spm_dtype dtype, double* d_result, int32_t* d_status,
+                             void* workspace, size_t ws_bytes, void* stream) {
+  TraceLayout L;
+  spm_status s = trace_layout(n_cols, nnz_a, nnz_b, L);
+  if (s != SPM_OK) return s;
+  if (n_rows < 0) return SPM_ERR_INVALID_ARG;
+  if (n_rows > INT32_MAX) return SPM_ERR_UNSUPPORTED;
+  if (dtype != SPM_F32 && dtype != SPM_F64) return SPM_ERR_INVALID_ARG;
+  if (!a_col_ptr || !b_col_ptr || !d_result || !d_status) return SPM_ERR_INVALID_ARG;
+  if ((nnz_a > 0 && (!a_row_idx || !a_vals)) || (nnz_b > 0 && (!b_row_idx || !b_vals))) return SPM_ERR_INVALID_ARG;
+  if (!workspace || ws_bytes < L.total) return SPM_ERR_WORKSPACE_TOO_SMALL;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  char* ws = static_cast<char*>(workspace);
+  MergeArgs a = {};
+  a.n_rows = n_rows;
+  a.n_cols = n_cols;
+  a.nnz_a = nnz_a;
+  a.cp_a = a_col_ptr;
+  a.row_a = a_row_idx;
+  a.val_a = a_vals;
+  a.cp_b = b_col_ptr;
+  a.row_b = b_row_idx;
+  a.val_b = b_vals;
+  a.scal = reinterpret_cast<UScal*>(ws + L.scal);
+  a.cuts = reinterpret_cast<Cut*>(ws + L.cuts);
+  a.partial = reinterpret_cast<double*>(ws + L.partial);
+  a.status = d_status;
+  a.check_b = 1;
+  cudaMemsetAsync(d_status, 0, sizeof(int32_t), st);
+  cudaMemsetAsync(a.scal, 0, sizeof(UScal), st);
+  const unsigned cblocks = (unsigned)((n_cols + 1 + 255) / 256);
+  k_check_cp<<<cblocks, 256, 0, st>>>(a_col_ptr, n_cols, nnz_a, d_status);
+  k_check_cp<<<cblocks, 256, 0, st>>>(b_col_ptr, n_cols, nnz_b, d_status);
+  k_split<<<(unsigned)((L.tiles_max + 1 + 255) / 256), 256, 0, st>>>(a);
+  const cudaError_t e = dtype == SPM_F64 ? launch_merge<uint64_t, kOpDot>(a, L.tiles_max, st)
+                                         : launch_merge<uint32_t, kOpDot>(a, L.tiles_max, st);
+  k_dot_sum<<<1, 1024, 0, st>>>(a, d_result);
+  spm::count_launches(5);
   if (e != cudaSuccess || cudaGetLastError() != cudaSuccess) return SPM_ERR_CUDA;
   return SPM_OK;
 }

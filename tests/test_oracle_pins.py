@@ -436,3 +436,56 @@ def test_update_rejects_malformed_matrices():
                 oracle.csc_update(c, r, v, shape, *none)
     with pytest.raises(oracle.OracleError, match="index out of range"):
         oracle.csc_update(cp, ri, v, shape, np.array([3]), np.array([0]), np.array([1.0]))
+
+
+# --------------------------------------------------------------------------------------------
+# Element lookup (Section 3.1) and coordinate-list export (Section 3.2)
+# --------------------------------------------------------------------------------------------
+def test_lookup_matches_dense_indexing():
+    rng = np.random.default_rng(18055)
+    for _ in range(30):
+        cp, ri, v, shape, rows, cols, vals = _tiny_update_case(rng)
+        X = densify(cp, ri, v, shape)
+        qr = rng.integers(0, shape[0], 60)
+        qc = rng.integers(0, shape[1], 60)
+        got, pos = oracle.csc_lookup(cp, ri, v, shape, qr, qc)
+        np.testing.assert_array_equal(got, X[qr, qc])
+        stored = pos >= 0
+        np.testing.assert_array_equal(stored, X[qr, qc] != 0)
+        np.testing.assert_array_equal(ri[pos[stored]], qr[stored])
+        assert np.all((cp[qc[stored]] <= pos[stored]) & (pos[stored] < cp[qc[stored] + 1]))
+    with pytest.raises(oracle.OracleError, match="index out of range"):
+        oracle.csc_lookup(cp, ri, v, shape, [shape[0]], [0])
+
+
+def test_coo_export_matches_scipy_and_round_trips():
+    sp = pytest.importorskip("scipy.sparse")
+    rng = np.random.default_rng(18056)
+    for _ in range(30):
+        cp, ri, v, shape, *_ = _tiny_update_case(rng)
+        r, c, x = oracle.csc_to_coo(cp, ri, v)
+        coo = sp.csc_matrix((v, ri, cp), shape=shape).tocoo()
+        order = np.lexsort((coo.row, coo.col))
+        np.testing.assert_array_equal(r, coo.row[order])
+        np.testing.assert_array_equal(c, coo.col[order])
+        np.testing.assert_array_equal(x, coo.data[order])
+        # the coordinate list assembles back to the same matrix
+        _assert_csc_equal(oracle.assemble_csc(r, c, x, shape, mode="set"), (cp, ri, v))
+
+
+# --------------------------------------------------------------------------------------------
+# trace(A^T B) without the transpose or the product (Section 2, Fig. 1b)
+# --------------------------------------------------------------------------------------------
+def test_trace_matches_dense_and_scipy():
+    sp = pytest.importorskip("scipy.sparse")
+    rng = np.random.default_rng(18057)
+    for _ in range(40):
+        cp, ri, v, shape, *_ = _tiny_update_case(rng)
+        dense_b = np.where(rng.random(shape) < 0.4, _dyadic(rng, shape[0] * shape[1]).reshape(shape), 0.0)
+        B = sp.csc_matrix(dense_b)
+        B.sort_indices()
+        got = oracle.csc_trace_atb(cp, ri, v, B.indptr, B.indices, B.data)
+        A = densify(cp, ri, v, shape)
+        assert got == np.trace(A.T @ dense_b)           # dyadic values: exact in any order
+        assert got == float(sp.csc_matrix((v, ri, cp), shape=shape).multiply(B).sum())
+        assert got == oracle.csc_trace_atb(B.indptr, B.indices, B.data, cp, ri, v)  # trace(A^T B) = trace(B^T A)
