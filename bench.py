@@ -50,6 +50,13 @@ def workload_spec(name):
                             m=10_000_000, n=100_000, dtype=np.float32, mode="sum", kind="zipf"),
         "fem2048": dict(desc="Q1 FEM 2048 x 2048 elements (4,198,401 nodes), 67,108,864 writes, float64, sum mode",
                         n_el=2048, dtype=np.float64, mode="sum", kind="fem"),
+        "ordered_n8": dict(desc="100,000 x 100,000, 10^8 writes in column-major order with random gaps (5 % "
+                                "repeated), U(-1,1) float64, sum mode",
+                           m=100_000_000, n=100_000, dtype=np.float64, mode="sum", kind="ordered", swap=0.0),
+        "ordered_2e7": dict(desc="as ordered_n8 with 2*10^7 writes (a smaller case, for profiling)",
+                            m=20_000_000, n=100_000, dtype=np.float64, mode="sum", kind="ordered", swap=0.0),
+        "quasi_n8": dict(desc="as ordered_n8 with 1 % of adjacent pairs swapped (quasi-ordered)",
+                         m=100_000_000, n=100_000, dtype=np.float64, mode="sum", kind="ordered", swap=0.01),
         "update_n8": dict(desc="10^7 new writes (Zipf(1.1) columns, U(-1,1) float64) applied to the 100,000 x "
                                "100,000 CSC matrix that the 10^8-write Zipf stream assembles to, sum mode",
                           m=10_000_000, m_a=100_000_000, n=100_000, dtype=np.float64, mode="sum", kind="update"),
@@ -77,6 +84,9 @@ def make_workload(name, rank=0):
     s = workload_spec(name)
     if s["kind"] == "zipf":
         d = workloads.zipf_batch(m=s["m"], n=s["n"], dtype=s["dtype"], seed=workloads.SEED_BASE + 2 + 1000 * rank)
+    elif s["kind"] == "ordered":
+        d = workloads.quasi_ordered(m=s["m"], n=s["n"], swap_frac=s["swap"], dtype=s["dtype"],
+                                    seed=workloads.SEED_BASE + 10 + 1000 * rank)
     else:
         d = workloads.fem_q1(n_el=s["n_el"], dtype=s["dtype"], seed=workloads.SEED_BASE + 3 + 1000 * rank)
     return d, s
@@ -504,6 +514,9 @@ def run_reference(args, world, rank):
     if spec["kind"] == "zipf":
         d = workloads.zipf_batch(m=max(sample, min(spec["m"], 1 << 24)), n=spec["n"], dtype=spec["dtype"],
                                  seed=workloads.SEED_BASE + 2)
+    elif spec["kind"] == "ordered":  # the gaps depend on m: draw the whole stream, use its prefix
+        d = workloads.quasi_ordered(m=spec["m"], n=spec["n"], swap_frac=spec["swap"], dtype=spec["dtype"],
+                                    seed=workloads.SEED_BASE + 10)
     else:
         d = workloads.fem_q1(n_el=spec["n_el"], dtype=spec["dtype"], seed=workloads.SEED_BASE + 3)
     for _ in range(args.warmup):
@@ -535,7 +548,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="n8",
                     choices=["n8", "zipf3e7", "zipf1e7", "zipf1e7_f32", "fem2048", "update_n8", "update_n8_set",
-                             "update_small", "lookup_n8", "coo_n8", "trace_10k"])
+                             "update_small", "lookup_n8", "coo_n8", "trace_10k", "ordered_n8",
+                             "quasi_n8", "ordered_2e7"])
     ap.add_argument("--cpu-sample", type=int, default=10_000_000, help="writes the CPU oracle baseline times")
     ap.add_argument("--ref-sample", type=int, default=1_000_000, help="writes per step of --impl reference")
     ap.add_argument("--e2e-steps", type=int, default=None)

@@ -366,6 +366,15 @@ spm_status spm_triplet_dvals(int64_t m, const int32_t* rows, const int32_t* cols
  *                        pairs, counted on the device after the histogram;
  *                        0 with two_pass_min_writes = 0 forces two passes
  *                        (>= 0)
+ *   ordered_path         1: a call on one matrix (no map, no seq in
+ *                        last-write mode) first tries a single pass that
+ *                        works when the writes are already in column-major
+ *                        order (the linear indices never decrease); it gives
+ *                        up at the first write out of order and the general
+ *                        path runs.  0: never tried.  The result is the same
+ *                        either way (sums agree except for bits more than 58
+ *                        below an element's largest value, which the general
+ *                        path aligns per bucket)
  */
 typedef struct {
   int32_t bucket_target;
@@ -374,6 +383,7 @@ typedef struct {
   int32_t resolve_threads;
   int32_t two_pass_min_writes;
   int32_t two_pass_min_fronts;
+  int32_t ordered_path;
 } spm_tuning;
 
 spm_status spm_set_tuning(const spm_tuning* t);
@@ -419,7 +429,9 @@ spm_status spm_debug_stage_timing(int32_t enable);
  * read back from its workspace (synchronous copies) statistics of the bucket
  * plan: stats[0] buckets, [1] largest bucket, [2] buckets above the
  * in-shared-memory capacity, [3] writes in those buckets, [4] capacity,
- * [5] level-2 tables used, [6] planner's bucket bound.  Same sizing arguments
+ * [5] level-2 tables used, [6] planner's bucket bound, [7] 1 if the call was
+ * finished by the single pass for writes in column-major order (the plan
+ * statistics are then those of a plan that was not made).  Same sizing arguments
  * as spm_assemble_csc_workspace.  A diagnostic; the paper has no counterpart.
  */
 spm_status spm_debug_plan_stats(const void* workspace, size_t ws_bytes, int64_t n_rows, int64_t n_cols, int64_t m,

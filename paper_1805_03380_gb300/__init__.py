@@ -54,7 +54,8 @@ class SpmError(RuntimeError):
 class _Tuning(ctypes.Structure):
     _fields_ = [("bucket_target", ctypes.c_int32), ("sub_bits", ctypes.c_int32),
                 ("partition_threads", ctypes.c_int32), ("resolve_threads", ctypes.c_int32),
-                ("two_pass_min_writes", ctypes.c_int32), ("two_pass_min_fronts", ctypes.c_int32)]
+                ("two_pass_min_writes", ctypes.c_int32), ("two_pass_min_fronts", ctypes.c_int32),
+                ("ordered_path", ctypes.c_int32)]
 
 
 _lib = None
@@ -261,7 +262,7 @@ def spm_triplet_dvals(rows, cols, map, dY, X, dvals, stream=None):
 
 
 def spm_set_tuning(bucket_target=None, sub_bits=None, partition_threads=None, resolve_threads=None,
-                   two_pass_min_writes=None, two_pass_min_fronts=None, reset=False):
+                   two_pass_min_writes=None, two_pass_min_fronts=None, ordered_path=None, reset=False):
     """Set the process-wide tuning (fields left as None keep their value); returns the new tuning."""
     if reset:
         _check(lib().spm_set_tuning(None), "spm_set_tuning")
@@ -269,7 +270,7 @@ def spm_set_tuning(bucket_target=None, sub_bits=None, partition_threads=None, re
     cur = spm_get_tuning()
     new = dict(bucket_target=bucket_target, sub_bits=sub_bits, partition_threads=partition_threads,
                resolve_threads=resolve_threads, two_pass_min_writes=two_pass_min_writes,
-               two_pass_min_fronts=two_pass_min_fronts)
+               two_pass_min_fronts=two_pass_min_fronts, ordered_path=ordered_path)
     t = _Tuning(*[cur[f] if new[f] is None else int(new[f]) for f, _ in _Tuning._fields_])
     _check(lib().spm_set_tuning(ctypes.byref(t)), "spm_set_tuning")
     return spm_get_tuning()
@@ -302,11 +303,12 @@ def spm_debug_launch_count():
 
 def spm_debug_plan_stats(asm):
     """Bucket-plan statistics of the last call of an Assembler (synchronous)."""
-    out = (ctypes.c_int64 * 7)()
+    out = (ctypes.c_int64 * 8)()
     _check(lib().spm_debug_plan_stats(_ptr(asm.workspace), asm.workspace.numel(), asm.n_rows, asm.n_cols, asm.m,
-                                      _dtype_code(asm.dtype), _mode_code(asm.mode), asm.flags, out, 7),
+                                      _dtype_code(asm.dtype), _mode_code(asm.mode), asm.flags, out, 8),
            "spm_debug_plan_stats")
-    keys = ("buckets", "largest", "over_capacity", "writes_over_capacity", "capacity", "l2_tables", "bucket_bound")
+    keys = ("buckets", "largest", "over_capacity", "writes_over_capacity", "capacity", "l2_tables", "bucket_bound",
+            "ordered_pass")
     return dict(zip(keys, [int(x) for x in out]))
 
 

@@ -2549,7 +2549,7 @@ __global__ void __launch_bounds__(256, 8) k_emit(Ctx c) {
 // ===========================================================================
 namespace {
 
-constexpr spm_tuning kDefaultTuning = {6144, 11, 1024, 512, 1 << 22, 1 << 19};
+constexpr spm_tuning kDefaultTuning = {6144, 11, 1024, 512, 1 << 22, 1 << 19, 1};
 spm_tuning g_tuning = kDefaultTuning;
 int64_t g_withhold = -1;
 std::mutex g_mutex;
@@ -2963,6 +2963,13 @@ spm_status run_assembly(int64_t B, const int64_t* h_nr, const int64_t* h_nc, con
   cudaMemsetAsync(ws + L.cellcnt, 0, 4 * (size_t)std::max<int64_t>(L.lut_total, 1), st);
   cudaMemsetAsync(ws + L.bk_state, 0, 8 * (size_t)std::max<int64_t>(L.nbcap_total, 1), st);
   if (L.l2h_len) cudaMemsetAsync(ws + L.l2h, 0, 4 * (size_t)L.l2h_len, st);
+  if (tun.ordered_path && B == 1 && d_tp == nullptr && !mp.seq && !keep_map && L.m_total > 0) {
+    // a stream already in column-major order is finished in one pass; the
+    // kernels below then find the abort flag set and return at once
+    cudaMemsetAsync(ws + L.tmp, 0, 8 * (size_t)ordered_tiles(L.m_total), st);
+    launch_ordered(ctx, h_nr[0], h_nc[0], ds->sms, st);
+    g_launches += 1;
+  }
   if (B == 1 && d_tp == nullptr) {
     k_setup_single<<<1, 32, 0, st>>>(ctx, hp.single);
   } else {
@@ -3051,6 +3058,7 @@ spm_status spm_set_tuning(const spm_tuning* t) {
   if (t->resolve_threads != 256 && t->resolve_threads != 512 && t->resolve_threads != 1024)
     return SPM_ERR_INVALID_ARG;
   if (t->two_pass_min_writes < 0 || t->two_pass_min_fronts < 0) return SPM_ERR_INVALID_ARG;
+  if (t->ordered_path != 0 && t->ordered_path != 1) return SPM_ERR_INVALID_ARG;
   g_tuning = *t;
   return SPM_OK;
 }
@@ -3131,8 +3139,9 @@ spm_status spm_debug_plan_stats(const void* workspace, size_t ws_bytes, int64_t 
       over_w += c;
     }
   }
-  const int64_t v[7] = {(int64_t)sc.NB, mx, over, over_w, mp.cap, mm.h2used, mm.nbcap};
-  for (int i = 0; i < n_stats && i < 7; ++i) stats[i] = v[i];
+  const bool ordered = m > 0 && sc.ord_fail == 0u && (int64_t)sc.ord_done == ordered_tiles(m);
+  const int64_t v[8] = {(int64_t)sc.NB, mx, over, over_w, mp.cap, mm.h2used, mm.nbcap, ordered ? 1 : 0};
+  for (int i = 0; i < n_stats && i < 8; ++i) stats[i] = v[i];
   return SPM_OK;
 }
 

@@ -171,6 +171,10 @@ struct Scalars {
   uint32_t abort;     // set when a fatal device error was recorded
   uint32_t G;         // two-pass partition: buckets per group (group g = buckets [g*G, (g+1)*G))
   unsigned long long fronts;  // (partition block, bucket) pairs with writes: the scatter's write fronts
+  uint32_t ord_ticket;  // ordered single pass: next tile
+  uint32_t ord_done;    // ordered single pass: tiles finished
+  uint32_t ord_fail;    // ordered single pass: the stream is not in order (the general path runs)
+  uint32_t ord_exit;    // ordered single pass: blocks that have left
 };
 
 // Per partition block (chunk of writes) information.
@@ -248,6 +252,12 @@ constexpr uint32_t kFlagKeepZeros = 1u << 30;
 
 // Launch counter of the library's kernels (spm_debug_launch_count).
 void count_launches(int64_t n);
+
+// Single pass for a stream already in column-major order (one matrix, no
+// seq in last-write mode, no map): tiles of the stream, the look-back states
+// in c.tmp (ordered_tiles(m) words, zeroed by the caller).
+int64_t ordered_tiles(int64_t m);
+cudaError_t launch_ordered(const Ctx& c, int64_t n_rows, int64_t n_cols, int sms, cudaStream_t st);
 
 // spm_assemble_csc for the library's own calls: `flags` may hold
 // kFlagKeepZeros.

@@ -114,10 +114,13 @@ def test_host_argument_validation_launches_nothing(spm):
 def test_tuning_roundtrip(spm):
     t0 = spm.spm_get_tuning()
     try:
+        assert t0["ordered_path"] == 1
         t = spm.spm_set_tuning(bucket_target=2048, sub_bits=10, partition_threads=512, resolve_threads=256,
-                               two_pass_min_writes=0, two_pass_min_fronts=7)
+                               two_pass_min_writes=0, two_pass_min_fronts=7, ordered_path=0)
         assert t == {"bucket_target": 2048, "sub_bits": 10, "partition_threads": 512, "resolve_threads": 256,
-                     "two_pass_min_writes": 0, "two_pass_min_fronts": 7}
+                     "two_pass_min_writes": 0, "two_pass_min_fronts": 7, "ordered_path": 0}
+        with pytest.raises(spm.SpmError):
+            spm.spm_set_tuning(ordered_path=2)
         with pytest.raises(spm.SpmError):
             spm.spm_set_tuning(bucket_target=100)
         with pytest.raises(spm.SpmError):

@@ -25,6 +25,9 @@ Workloads
   batched path (set semantics, float32 N(0,1) values, 10 % rewrites).
 * ``density_sweep``    the shape of the paper's unordered-insertion experiment:
   10,000 x 10,000, uniform coordinates, m = density * 10^8.
+* ``quasi_ordered``    incremental construction: writes in column-major order
+  with random gaps, 5 % repeated, 1 % of adjacent pairs swapped (the paper's
+  quasi-ordered insertion experiment).
 * ``update_batch``     writes that build an existing matrix plus a batch of
   new writes to it, part of them hitting existing elements, part of them
   zero (insertion into a matrix already in CSC, Section 3.1).
@@ -179,6 +182,34 @@ def update_batch(n_rows=3000, n_cols=2000, m_a=60_000, m=20_000, hit_frac=0.3, z
     vals[rng.random(m) < zero_frac] = 0.0
     return dict(a_rows=a_rows, a_cols=a_cols, a_vals=a_vals, rows=rows, cols=cols, vals=vals, seq=None,
                 shape=(n_rows, n_cols))
+
+
+def quasi_ordered(m=100_000_000, n=100_000, dup_frac=0.05, swap_frac=0.01, dtype=np.float64,
+                  seed=SEED_BASE + 10, chunk=1 << 24):
+    """Incremental construction (the paper's quasi-ordered insertion): writes
+    walk the n x n matrix in column-major order.  The gap between the linear
+    positions of consecutive writes is 0 with probability ``dup_frac`` (a
+    repeated write) and otherwise uniform in 1 .. 2*(n*n/m) - 1, so the walk
+    spans the matrix; then a fraction ``swap_frac`` of adjacent pairs is
+    swapped (quasi-ordered).  Values U(-1,1).  Returns dict(rows, cols, vals)."""
+    rng = _rng(seed)
+    span = max(1, (2 * n * n) // m - 1)
+    pos = np.empty(m, dtype=np.int64)
+    base = 0
+    for a in range(0, m, chunk):
+        b = min(m, a + chunk)
+        gaps = rng.integers(1, span + 1, size=b - a)
+        gaps[rng.random(b - a) < dup_frac] = 0
+        pos[a:b] = base + np.cumsum(gaps)
+        base = int(pos[b - 1])
+    pos = np.minimum(pos, n * n - 1)
+    sw = np.flatnonzero(rng.random(m - 1) < swap_frac) if m > 1 else np.zeros(0, dtype=np.int64)
+    sw = sw[np.concatenate([[True], np.diff(sw) > 1])] if len(sw) else sw  # disjoint pairs
+    pos[sw], pos[sw + 1] = pos[sw + 1].copy(), pos[sw].copy()
+    cols = (pos // n).astype(np.int32)
+    rows = (pos - cols.astype(np.int64) * n).astype(np.int32)
+    vals = rng.uniform(-1.0, 1.0, size=m).astype(dtype)
+    return dict(rows=rows, cols=cols, vals=vals, seq=None, shape=(n, n))
 
 
 def dense_rhs(n, k=16, dtype=np.float32, seed=SEED_BASE + 5):
