@@ -146,3 +146,37 @@ def test_product_package_does_not_import_the_oracle():
             assert not re.search(r"^\s*(import|from)\s+paper_1805_03380_gb300\b", text, re.M), fn
             assert not re.search(r"#\s*include\s*[<\"]spm\.h", text), fn
             assert "libspm.so" not in text, fn
+
+
+def test_update_trace_lookup_coo_host_checks(spm):
+    """Workspace sizes and argument checks of the update, trace, lookup and
+    COO entry points (all return before anything is launched)."""
+    import torch
+    m, nnz_a, n = 1_000_000, 5_000_000, 100_000
+    asm = spm.spm_assemble_csc_workspace(n, n, m, torch.float64, "sum")
+    upd = spm.spm_csc_update_workspace(n, n, nnz_a, m, torch.float64, "sum")
+    # the resolved writes (col_ptr, rows, values), one cut and one state per 2047 merged elements,
+    # then the assembly's own workspace
+    assert asm + 12 * m + 8 * (n + 1) < upd < asm + 12 * m + 8 * (n + 1) + 41 * (nnz_a + m) // 2047 + 4096
+    assert spm.spm_csc_update_workspace(n, n, 2 * nnz_a, m, torch.float64, "sum") > upd
+    for bad in (dict(nnz_a=-1), dict(m=-1)):
+        args = dict(n_rows=n, n_cols=n, nnz_a=nnz_a, m=m, dtype=torch.float64, mode="sum")
+        args.update(bad)
+        with pytest.raises(spm.SpmError):
+            spm.spm_csc_update_workspace(**args)
+    with pytest.raises(spm.SpmError, match="INVALID_ARG"):
+        spm.spm_csc_update_workspace(n, n, nnz_a, m, torch.float64, "set", spm.KEEP_MAP)
+    tr = spm.spm_csc_trace_atb_workspace(n, nnz_a, nnz_a)
+    assert 40 * (2 * nnz_a) // 2047 <= tr < 40 * (2 * nnz_a) // 2047 + 4096
+    with pytest.raises(spm.SpmError):
+        spm.spm_csc_trace_atb_workspace(-1, 0, 0)
+    L = spm.lib()
+    null = None
+    # NULL pointers and negative sizes are refused on the host
+    assert L.spm_csc_update(n, n, null, null, null, 0, 0, null, null, null, null, 1, 1, 0, null, null, null, null,
+                            null, null, 0, null) == 1
+    assert L.spm_csc_trace_atb(n, n, null, null, null, 0, null, null, null, 0, 1, null, null, null, 0, null) == 1
+    assert L.spm_csc_lookup(-1, n, 0, null, null, null, 1, 0, null, null, null, null, null, null) == 1
+    assert L.spm_csc_lookup(n, n, 0, null, null, null, 1, 0, null, null, null, null, null, null) == 1
+    assert L.spm_csc_to_coo(-1, 0, null, null, null, 1, null, null, null, null, null) == 1
+    assert L.spm_csc_to_coo(n, 0, null, null, null, 1, null, null, null, null, null) == 1
