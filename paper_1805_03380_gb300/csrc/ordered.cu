@@ -33,7 +33,7 @@
 namespace spm {
 namespace {
 
-constexpr int kOT = 256;                    // threads per block
+constexpr int kOT = 512;                    // threads per block
 constexpr int kOI = 8;                      // positions per thread
 constexpr int kOTile = kOT * kOI;           // positions per tile
 constexpr int kOExt = 64;                   // positions read past the tile for a run that continues
@@ -97,9 +97,11 @@ __device__ uint64_t reduce_run(const uint64_t* val, int j, int e, bool keep_zero
 }
 
 template <bool F64, bool SUM>
-__global__ void __launch_bounds__(kOT, 4) k_ordered(Ctx c, int64_t n_rows, int64_t n_cols) {
-  __shared__ int32_t s_row[kOBuf], s_col[kOBuf];
-  __shared__ uint64_t s_val[kOBuf];
+__global__ void __launch_bounds__(kOT, 2) k_ordered(Ctx c, int64_t n_rows, int64_t n_cols) {
+  extern __shared__ __align__(16) unsigned char o_smem[];
+  uint64_t* s_val = reinterpret_cast<uint64_t*>(o_smem);  // [kOBuf]
+  int32_t* s_row = reinterpret_cast<int32_t*>(s_val + kOBuf);
+  int32_t* s_col = s_row + kOBuf;
   __shared__ int32_t s_cnt[kOI * (kOT / 32)], s_pre[kOI * (kOT / 32)];  // kept per (slot row, warp)
   __shared__ int32_t s_total;
   __shared__ int32_t s_first, s_wait, s_stop;
@@ -224,19 +226,29 @@ __global__ void __launch_bounds__(kOT, 4) k_ordered(Ctx c, int64_t n_rows, int64
       if (tid == 0) atomicExch(&c.scal->ord_fail, 1u);
       break;
     }
-    if (w == 0) {  // exclusive scan of the kOI * 8 counts, two per lane
+    if (w == 0) {  // exclusive scan of the kOI * (kOT / 32) counts, kPer per lane
       constexpr int kCnt = kOI * (kOT / 32);
-      static_assert(kCnt == 64, "two counts per lane");
-      const int a0 = s_cnt[2 * lane], a1 = s_cnt[2 * lane + 1];
-      int inc = a0 + a1;
+      constexpr int kPer = kCnt / 32;
+      static_assert(kCnt % 32 == 0, "whole counts per lane");
+      int a[kPer];
+      int sum = 0;
+#pragma unroll
+      for (int u = 0; u < kPer; ++u) {
+        a[u] = s_cnt[kPer * lane + u];
+        sum += a[u];
+      }
+      int inc = sum;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
         const int y = __shfl_up_sync(kAll, inc, o);
         if (lane >= o) inc += y;
       }
-      const int ex = inc - a0 - a1;
-      s_pre[2 * lane] = ex;
-      s_pre[2 * lane + 1] = ex + a0;
+      int ex = inc - sum;
+#pragma unroll
+      for (int u = 0; u < kPer; ++u) {
+        s_pre[kPer * lane + u] = ex;
+        ex += a[u];
+      }
       if (lane == 31) s_total = inc;
     }
     __syncthreads();
@@ -349,17 +361,23 @@ __global__ void __launch_bounds__(kOT, 4) k_ordered(Ctx c, int64_t n_rows, int64
 
 int64_t ordered_tiles(int64_t m) { return (m + kOTile - 1) / kOTile; }
 
+template <bool F64, bool SUM>
+cudaError_t launch_ordered_t(const Ctx& c, int64_t n_rows, int64_t n_cols, unsigned grid, cudaStream_t st) {
+  constexpr int smem = kOBuf * (8 + 4 + 4);
+  const cudaError_t e = cudaFuncSetAttribute(k_ordered<F64, SUM>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  k_ordered<F64, SUM><<<grid, kOT, smem, st>>>(c, n_rows, n_cols);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_ordered(const Ctx& c, int64_t n_rows, int64_t n_cols, int sms, cudaStream_t st) {
   const int64_t tiles = ordered_tiles(c.m_total);
-  const unsigned grid = (unsigned)std::min<int64_t>(tiles, (int64_t)sms * 4);
-  if (c.f64) {
-    if (c.sum_mode) k_ordered<true, true><<<grid, kOT, 0, st>>>(c, n_rows, n_cols);
-    else k_ordered<true, false><<<grid, kOT, 0, st>>>(c, n_rows, n_cols);
-  } else {
-    if (c.sum_mode) k_ordered<false, true><<<grid, kOT, 0, st>>>(c, n_rows, n_cols);
-    else k_ordered<false, false><<<grid, kOT, 0, st>>>(c, n_rows, n_cols);
-  }
-  return cudaGetLastError();
+  const unsigned grid = (unsigned)std::min<int64_t>(tiles, (int64_t)sms * 2);
+  if (c.f64)
+    return c.sum_mode ? launch_ordered_t<true, true>(c, n_rows, n_cols, grid, st)
+                      : launch_ordered_t<true, false>(c, n_rows, n_cols, grid, st);
+  return c.sum_mode ? launch_ordered_t<false, true>(c, n_rows, n_cols, grid, st)
+                    : launch_ordered_t<false, false>(c, n_rows, n_cols, grid, st);
 }
 
 }  // namespace spm
