@@ -22,6 +22,7 @@
 // below the run's largest exponent) rounded once.
 #include <algorithm>
 #include <cstdint>
+#include <mutex>
 #include <type_traits>
 
 #include <cuda_runtime.h>
@@ -357,20 +358,43 @@ __global__ void __launch_bounds__(kOT, 2) k_ordered(Ctx c, int64_t n_rows, int64
   }
 }
 
+constexpr int kOSmem = kOBuf * (8 + 4 + 4);
+
+template <bool F64, bool SUM>
+cudaError_t launch_ordered_t(const Ctx& c, int64_t n_rows, int64_t n_cols, unsigned grid, cudaStream_t st) {
+  k_ordered<F64, SUM><<<grid, kOT, kOSmem, st>>>(c, n_rows, n_cols);
+  return cudaGetLastError();
+}
+
+// The shared-memory limit of the four instances, raised once per device (on
+// the first call, which comes before any stream capture).
+bool g_ord_ready[64] = {};
+std::mutex g_ord_mutex;
+
+cudaError_t ordered_prepare() {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (g_ord_ready[dev]) return cudaSuccess;
+  std::lock_guard<std::mutex> lk(g_ord_mutex);
+  if (g_ord_ready[dev]) return cudaSuccess;
+  const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  if ((e = cudaFuncSetAttribute(k_ordered<true, true>, a, kOSmem)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_ordered<true, false>, a, kOSmem)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_ordered<false, true>, a, kOSmem)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_ordered<false, false>, a, kOSmem)) != cudaSuccess) return e;
+  g_ord_ready[dev] = true;
+  return cudaSuccess;
+}
+
 }  // namespace
 
 int64_t ordered_tiles(int64_t m) { return (m + kOTile - 1) / kOTile; }
 
-template <bool F64, bool SUM>
-cudaError_t launch_ordered_t(const Ctx& c, int64_t n_rows, int64_t n_cols, unsigned grid, cudaStream_t st) {
-  constexpr int smem = kOBuf * (8 + 4 + 4);
-  const cudaError_t e = cudaFuncSetAttribute(k_ordered<F64, SUM>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e != cudaSuccess) return e;
-  k_ordered<F64, SUM><<<grid, kOT, smem, st>>>(c, n_rows, n_cols);
-  return cudaGetLastError();
-}
-
 cudaError_t launch_ordered(const Ctx& c, int64_t n_rows, int64_t n_cols, int sms, cudaStream_t st) {
+  const cudaError_t e = ordered_prepare();
+  if (e != cudaSuccess) return e;
   const int64_t tiles = ordered_tiles(c.m_total);
   const unsigned grid = (unsigned)std::min<int64_t>(tiles, (int64_t)sms * 2);
   if (c.f64)

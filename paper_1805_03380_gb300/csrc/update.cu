@@ -35,6 +35,7 @@
 #include <algorithm>
 #include <climits>
 #include <cstdint>
+#include <mutex>
 
 #include <cuda_runtime.h>
 
@@ -530,12 +531,35 @@ __global__ void __launch_bounds__(kMT, 5) k_merge(MergeArgs a) {
   if (tid == 0 && s_bad) fail(a.status, s_bad);
 }
 
+// The shared-memory limit of the six k_merge instances, raised once per device.
+bool g_merge_ready[64] = {};
+std::mutex g_merge_mutex;
+
+cudaError_t merge_prepare() {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (g_merge_ready[dev]) return cudaSuccess;
+  std::lock_guard<std::mutex> lk(g_merge_mutex);
+  if (g_merge_ready[dev]) return cudaSuccess;
+  const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  const int s64 = (int)merge_smem_bytes<uint64_t>(), s32 = (int)merge_smem_bytes<uint32_t>();
+  if ((e = cudaFuncSetAttribute(k_merge<uint64_t, kOpSet>, a, s64)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_merge<uint64_t, kOpSum>, a, s64)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_merge<uint64_t, kOpDot>, a, s64)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_merge<uint32_t, kOpSet>, a, s32)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_merge<uint32_t, kOpSum>, a, s32)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_merge<uint32_t, kOpDot>, a, s32)) != cudaSuccess) return e;
+  g_merge_ready[dev] = true;
+  return cudaSuccess;
+}
+
 template <typename VT, int OP>
 cudaError_t launch_merge(const MergeArgs& args, int64_t tiles_max, cudaStream_t st) {
-  constexpr size_t smem = merge_smem_bytes<VT>();
-  cudaError_t e = cudaFuncSetAttribute(k_merge<VT, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const cudaError_t e = merge_prepare();
   if (e != cudaSuccess) return e;
-  k_merge<VT, OP><<<(unsigned)tiles_max, kMT, smem, st>>>(args);
+  k_merge<VT, OP><<<(unsigned)tiles_max, kMT, merge_smem_bytes<VT>(), st>>>(args);
   return cudaGetLastError();
 }
 

@@ -149,3 +149,33 @@ def test_ordered_at_scale():
     want = oracle.assemble_csc(d["rows"], d["cols"], d["vals"], d["shape"], mode="sum")
     assert_same_structure(got, want)
     np.testing.assert_allclose(got[2], want[2], rtol=1e-12, atol=1e-12)
+
+
+def test_graph_replay_switches_between_the_two_paths():
+    """One captured call replayed on an ordered stream (single pass) and on an unordered one
+    (general path): both results match the oracle."""
+    import paper_1805_03380_gb300 as spm
+    m, n = 200_000, 2000
+    d_ord = workloads.quasi_ordered(m=m, n=n, swap_frac=0.0, seed=workloads.SEED_BASE + 67)
+    d_rnd = workloads.zipf_batch(m=m, n=n, seed=workloads.SEED_BASE + 68)
+    rows, cols, vals = to_dev(d_ord["rows"], np.int32), to_dev(d_ord["cols"], np.int32), to_dev(d_ord["vals"])
+    a = spm.Assembler((n, n), m, torch.float64, "sum")
+    a.run(rows, cols, vals)  # first call on the device (sets kernel attributes)
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            a.run(rows, cols, vals, stream=s)
+    for d, ordered in ((d_rnd, 0), (d_ord, 1), (d_rnd, 0)):
+        rows.copy_(to_dev(d["rows"], np.int32))
+        cols.copy_(to_dev(d["cols"], np.int32))
+        vals.copy_(to_dev(d["vals"]))
+        g.replay()
+        torch.cuda.synchronize()
+        A = a.result()
+        assert spm.spm_debug_plan_stats(a)["ordered_pass"] == ordered
+        want = oracle.assemble_csc(d["rows"], d["cols"], d["vals"], (n, n), mode="sum")
+        got = (A.col_ptr.cpu().numpy(), A.row_idx.cpu().numpy().astype(np.int64), A.vals.cpu().numpy())
+        assert_same_structure(got, want)
+        np.testing.assert_allclose(got[2], want[2], rtol=1e-12, atol=1e-12)
