@@ -18,7 +18,9 @@
 //      separate an element of A from the write to the same element in B
 //      moves one position on.
 //   4. k_merge: one block per tile (taken in order through a ticket) merges
-//      its part of A and B in shared memory, combines an element present in
+//      its part of A and B in shared memory -- column by column with 32-bit
+//      row compares when the columns starting inside the tile fit a table,
+//      else on 64-bit linear indices -- combines an element present in
 //      both (last-write mode: B's value; add mode: A's value + B's value),
 //      drops zeros, finds the tile's output offset by a bounded decoupled
 //      look-back and writes the stored elements and the column offsets of the
@@ -321,80 +323,181 @@ __global__ void __launch_bounds__(kMT, 5) k_merge(MergeArgs a) {
     s_ta[tid] = clamp_rel(cpa0 - c0.a);
     s_tb[tid] = clamp_rel(cpb0 - c0.b);
   }
-#pragma unroll
-  for (int i = 0; i < kMI; ++i) {
-    const int k = tid + i * kMT;
-    if (k < n) val[k] = lv[i];
-  }
-  __syncthreads();
-  // column of every element: jlo - 1 plus the number of columns starting
-  // inside the tile at or before it (CSC offsets never decrease)
-  const uint64_t nr = (uint64_t)a.n_rows;
+  // values (and, for the column-by-column merge, rows) to shared memory; A
+  // (and B when it is an input) must be canonical: rows inside the matrix
   int bad = 0;
 #pragma unroll
   for (int i = 0; i < kMI; ++i) {
     const int k = tid + i * kMT;
     if (k < n) {
-      const bool in_a = k < nA;
-      const int32_t rel = in_a ? k : k - (int)nA;
-      int lo = 0, hi = nc;
-      if (table) {
-        const int32_t* tab = in_a ? s_ta : s_tb;
-        while (lo < hi) {
-          const int mid = (lo + hi) >> 1;
-          if (tab[mid] <= rel) lo = mid + 1; else hi = mid;
-        }
-      } else {
-        const int64_t* cp = (in_a ? a.cp_a : a.cp_b) + jlo;
-        const int64_t base = (in_a ? c0.a : c0.b) + rel;
-        while (lo < hi) {
-          const int mid = (lo + hi) >> 1;
-          if (cp[mid] <= base) lo = mid + 1; else hi = mid;
-        }
-      }
-      const int32_t col = (int32_t)(jlo - 1 + lo);
-      const int32_t r = lr[i];
-      aux[k] = col;
-      key[k] = (uint64_t)(uint32_t)col * nr + (uint64_t)(uint32_t)r;
-      // A (and B when it is an input) must be canonical: rows inside the
-      // matrix (order checked below)
-      if ((in_a || a.check_b) && (r < 0 || (int64_t)r >= a.n_rows)) bad = SPM_ERR_INDEX_OUT_OF_RANGE;
+      val[k] = lv[i];
+      if (table) aux[k] = lr[i];
+      if ((k < nA || a.check_b) && (lr[i] < 0 || (int64_t)lr[i] >= a.n_rows)) bad = SPM_ERR_INDEX_OUT_OF_RANGE;
     }
   }
   if (bad) atomicMax(&s_bad, bad);
   __syncthreads();
-  // ... and strictly increasing linear indices inside A's part of the tile
-  // (k_split checks the pair of A's elements on either side of each cut)
-#pragma unroll
-  for (int i = 0; i < kMI; ++i) {
-    const int k = tid + i * kMT;
-    if (k > 0 && k < nA && key[k] <= key[k - 1]) atomicMax(&s_bad, (int32_t)SPM_ERR_INVALID_ARG);
-    if (a.check_b && k > nA && k < n && key[k] <= key[k - 1]) atomicMax(&s_bad, (int32_t)SPM_ERR_INVALID_ARG);
-  }
 
-  // each thread merges kMI consecutive positions (A first on equal keys)
+  // each thread merges kMI consecutive positions (A first on equal rows of a column)
   const int p0 = min(tid * kMI, n);
-  int lo = max(0, p0 - (int)nB), hi = min(p0, (int)nA);
-  while (lo < hi) {
-    const int mid = (lo + hi) >> 1;
-    if (key[mid] <= key[nA + p0 - 1 - mid]) lo = mid + 1; else hi = mid;
+  int32_t orow[kMI];
+  VT oval[kMI];
+  uint32_t kmask = 0;
+  double acc = 0.0;
+#pragma unroll
+  for (int k = 0; k < kMI; ++k) {
+    orow[k] = 0;
+    oval[k] = 0;
   }
-  int ia = lo, ib = p0 - lo;
-  if (OP == kOpDot) {
-    // products of the elements present in A and in B (each such pair is adjacent, A first)
-    double acc = 0.0;
+  if (table) {
+    // Column by column: the merged tile is column jlo - 1 (from the tile's
+    // start) and then the columns starting inside it, each the merge of its
+    // rows in A and in B; rows are compared as 32-bit integers.
+    // Segment q = 0 is column jlo - 1; q >= 1 is column jlo + q - 1.
+    const int32_t* rowA = aux;
+    const int32_t* rowB = aux + nA;
+    const int nAi = (int)nA, nBi = (int)nB;
+    auto sa = [&](int q) -> int {
+      const int v = q == 0 ? 0 : s_ta[q - 1];
+      return v < 0 ? 0 : (v > nAi ? nAi : v);
+    };
+    auto sb = [&](int q) -> int {
+      const int v = q == 0 ? 0 : s_tb[q - 1];
+      return v < 0 ? 0 : (v > nBi ? nBi : v);
+    };
+    // the segment holding merged position p0: the last one that starts at or before it
+    int lo = 0, hi = nc;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (sa(mid) + sb(mid) <= p0) lo = mid; else hi = mid - 1;
+    }
+    int q = lo;
+    int aS = sa(q), bS = sb(q);
+    int aE = q < nc ? sa(q + 1) : nAi, bE = q < nc ? sb(q + 1) : nBi;
+    aE = aE < aS ? aS : aE;  // (only a malformed A breaks the order)
+    bE = bE < bS ? bS : bE;
+    int off = p0 - (aS + bS);
+    const int seg = (aE - aS) + (bE - bS);
+    off = off < 0 ? 0 : (off > seg ? seg : off);
+    int l2 = max(0, off - (bE - bS)), h2 = min(off, aE - aS);
+    while (l2 < h2) {
+      const int mid = (l2 + h2) >> 1;
+      if (rowA[aS + mid] <= rowB[bS + off - 1 - mid]) l2 = mid + 1; else h2 = mid;
+    }
+    int ia = aS + l2, ib = bS + off - l2;
+    bool bad_order = false;
+#pragma unroll
+    for (int k = 0; k < kMI; ++k) {
+      if (p0 + k < n) {
+        while (ia >= aE && ib >= bE && q < nc) {  // this column is done: the next one
+          ++q;
+          aS = aE;
+          bS = bE;
+          aE = q < nc ? sa(q + 1) : nAi;
+          bE = q < nc ? sb(q + 1) : nBi;
+          aE = aE < aS ? aS : aE;
+          bE = bE < bS ? bS : bE;
+        }
+        if (ia >= aE && ib >= bE) break;  // (only a malformed A)
+        const bool take_a = ib >= bE || (ia < aE && rowA[ia] <= rowB[ib]);
+        if (take_a) {
+          const int32_t r = rowA[ia];
+          if (ia > aS && rowA[ia - 1] >= r) bad_order = true;
+          const bool pair = ib < bE && rowB[ib] == r;
+          if (OP == kOpDot) {
+            if (pair) acc = fma(as_double<VT>(val[ia]), as_double<VT>(val[nA + ib]), acc);
+          } else {
+            VT v = val[ia];
+            if (pair) v = SUM ? combine_add<VT>(v, val[nA + ib]) : val[nA + ib];
+            orow[k] = r;
+            oval[k] = v;
+            if (nonzero<VT>(v)) kmask |= 1u << k;
+          }
+          ++ia;
+        } else {
+          const int32_t r = rowB[ib];
+          if (a.check_b && ib > bS && rowB[ib - 1] >= r) bad_order = true;
+          if (OP != kOpDot) {
+            const bool tail = ia > aS && rowA[ia - 1] == r;  // B's half of a combined element
+            const VT v = val[nA + ib];
+            orow[k] = r;
+            oval[k] = v;
+            if (!tail && nonzero<VT>(v)) kmask |= 1u << k;
+          }
+          ++ib;
+        }
+      }
+    }
+    if (bad_order) atomicMax(&s_bad, (int32_t)SPM_ERR_INVALID_ARG);
+  } else {
+    // Many columns start inside the tile: the column of every element from a
+    // search over the column offsets, then 64-bit linear indices.
+    const uint64_t nr = (uint64_t)a.n_rows;
+#pragma unroll
+    for (int i = 0; i < kMI; ++i) {
+      const int k = tid + i * kMT;
+      if (k < n) {
+        const bool in_a = k < nA;
+        const int32_t rel = in_a ? k : k - (int)nA;
+        const int64_t* cp = (in_a ? a.cp_a : a.cp_b) + jlo;
+        const int64_t base = (in_a ? c0.a : c0.b) + rel;
+        int lo = 0, hi = nc;
+        while (lo < hi) {
+          const int mid = (lo + hi) >> 1;
+          if (cp[mid] <= base) lo = mid + 1; else hi = mid;
+        }
+        const int32_t col = (int32_t)(jlo - 1 + lo);
+        aux[k] = col;
+        key[k] = (uint64_t)(uint32_t)col * nr + (uint64_t)(uint32_t)lr[i];
+      }
+    }
+    __syncthreads();
+    // strictly increasing linear indices inside A's part of the tile (and
+    // B's when it is an input); k_split checks the pairs on either side of each cut
+#pragma unroll
+    for (int i = 0; i < kMI; ++i) {
+      const int k = tid + i * kMT;
+      if (k > 0 && k < nA && key[k] <= key[k - 1]) atomicMax(&s_bad, (int32_t)SPM_ERR_INVALID_ARG);
+      if (a.check_b && k > nA && k < n && key[k] <= key[k - 1]) atomicMax(&s_bad, (int32_t)SPM_ERR_INVALID_ARG);
+    }
+    int lo = max(0, p0 - (int)nB), hi = min(p0, (int)nA);
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (key[mid] <= key[nA + p0 - 1 - mid]) lo = mid + 1; else hi = mid;
+    }
+    int ia = lo, ib = p0 - lo;
 #pragma unroll
     for (int k = 0; k < kMI; ++k) {
       if (p0 + k < n) {
         const bool take_a = ib >= nB || (ia < nA && key[ia] <= key[nA + ib]);
         if (take_a) {
-          if (ib < nB && key[nA + ib] == key[ia]) acc = fma(as_double<VT>(val[ia]), as_double<VT>(val[nA + ib]), acc);
+          const bool pair = ib < nB && key[nA + ib] == key[ia];
+          if (OP == kOpDot) {
+            if (pair) acc = fma(as_double<VT>(val[ia]), as_double<VT>(val[nA + ib]), acc);
+          } else {
+            VT v = val[ia];
+            if (pair) v = SUM ? combine_add<VT>(v, val[nA + ib]) : val[nA + ib];
+            orow[k] = (int32_t)(key[ia] - (uint64_t)(uint32_t)aux[ia] * nr);
+            oval[k] = v;
+            if (nonzero<VT>(v)) kmask |= 1u << k;
+          }
           ++ia;
         } else {
+          const int src = (int)nA + ib;
+          if (OP != kOpDot) {
+            const bool tail = ia > 0 && key[ia - 1] == key[src];  // B's half of a combined element
+            const VT v = val[src];
+            orow[k] = (int32_t)(key[src] - (uint64_t)(uint32_t)aux[src] * nr);
+            oval[k] = v;
+            if (!tail && nonzero<VT>(v)) kmask |= 1u << k;
+          }
           ++ib;
         }
       }
     }
+  }
+  if (OP == kOpDot) {
+    // the tile's sum of products
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kAll, acc, o);
     __shared__ double s_part[kMT / 32];
@@ -407,35 +510,6 @@ __global__ void __launch_bounds__(kMT, 5) k_merge(MergeArgs a) {
       if (s_bad) fail(a.status, s_bad);
     }
     return;
-  }
-  int32_t orow[kMI];
-  VT oval[kMI];
-  uint32_t kmask = 0;
-#pragma unroll
-  for (int k = 0; k < kMI; ++k) {
-    orow[k] = 0;
-    oval[k] = 0;
-    if (p0 + k < n) {
-      const bool take_a = ib >= nB || (ia < nA && key[ia] <= key[nA + ib]);
-      int src;
-      bool out;
-      VT v;
-      if (take_a) {
-        src = ia;
-        v = val[ia];
-        if (ib < nB && key[nA + ib] == key[ia]) v = SUM ? combine_add<VT>(v, val[nA + ib]) : val[nA + ib];
-        out = true;
-        ++ia;
-      } else {
-        src = (int)nA + ib;
-        v = val[src];
-        out = !(ia > 0 && key[ia - 1] == key[src]);  // B's half of a combined element
-        ++ib;
-      }
-      orow[k] = (int32_t)(key[src] - (uint64_t)(uint32_t)aux[src] * nr);
-      oval[k] = v;
-      if (out && nonzero<VT>(v)) kmask |= 1u << k;
-    }
   }
   // exclusive scan of the kept counts over the block
   const int cnt = __popc(kmask);
