@@ -57,6 +57,22 @@ def workload_spec(name):
                             m=20_000_000, n=100_000, dtype=np.float64, mode="sum", kind="ordered", swap=0.0),
         "quasi_n8": dict(desc="as ordered_n8 with 1 % of adjacent pairs swapped (quasi-ordered)",
                          m=100_000_000, n=100_000, dtype=np.float64, mode="sum", kind="ordered", swap=0.01),
+        "c1": dict(desc="1000 x 1000, 10^4 writes (20 % rewrites, 5 % zeros), N(0,1) float64, set mode "
+                        "(latency of one small call)", m=10_000, n=1000, dtype=np.float64, mode="set", kind="lastwrite"),
+        "n4_0.01": dict(desc="10,000 x 10,000, uniform coordinates, density 0.01 % (10^4 writes), float64, set mode",
+                        density=0.0001, n=10_000, dtype=np.float64, mode="set", kind="density"),
+        "n4_0.1": dict(desc="10,000 x 10,000, uniform coordinates, density 0.1 % (10^5 writes), float64, set mode",
+                       density=0.001, n=10_000, dtype=np.float64, mode="set", kind="density"),
+        "n4_1": dict(desc="10,000 x 10,000, uniform coordinates, density 1 % (10^6 writes), float64, set mode",
+                     density=0.01, n=10_000, dtype=np.float64, mode="set", kind="density"),
+        "n4_10": dict(desc="10,000 x 10,000, uniform coordinates, density 10 % (10^7 writes), float64, set mode",
+                      density=0.1, n=10_000, dtype=np.float64, mode="set", kind="density"),
+        "batched4096": dict(desc="4096 independent square matrices, n ~ U{64..8192}, density ~ U[0.1 %, 2 %], 10 % "
+                                 "rewrites, float32 N(0,1), set mode: one batched call vs single-matrix calls",
+                            dtype=np.float32, mode="set", kind="batched"),
+        "c5": dict(desc="Q1 FEM 512 x 512 elements (263,169 nodes, 4,194,304 writes), float32, sum mode; Y = A X "
+                        "with X 263,169 x 16: forward + backward vs assembly + SpMM",
+                   n_el=512, dtype=np.float32, mode="sum", kind="diff"),
         "update_n8": dict(desc="10^7 new writes (Zipf(1.1) columns, U(-1,1) float64) applied to the 100,000 x "
                                "100,000 CSC matrix that the 10^8-write Zipf stream assembles to, sum mode",
                           m=10_000_000, m_a=100_000_000, n=100_000, dtype=np.float64, mode="sum", kind="update"),
@@ -87,6 +103,10 @@ def make_workload(name, rank=0):
     elif s["kind"] == "ordered":
         d = workloads.quasi_ordered(m=s["m"], n=s["n"], swap_frac=s["swap"], dtype=s["dtype"],
                                     seed=workloads.SEED_BASE + 10 + 1000 * rank)
+    elif s["kind"] == "lastwrite":
+        d = workloads.last_write_1000(seed=workloads.SEED_BASE + 1 + 1000 * rank)
+    elif s["kind"] == "density":
+        d = workloads.density_sweep(s["density"], n=s["n"], dtype=s["dtype"], seed=workloads.SEED_BASE + 6 + 1000 * rank)
     else:
         d = workloads.fem_q1(n_el=s["n_el"], dtype=s["dtype"], seed=workloads.SEED_BASE + 3 + 1000 * rank)
     return d, s
@@ -482,6 +502,122 @@ def run_access(args, world, rank, local_rank):
         torch.distributed.destroy_process_group()
 
 
+def run_batched_or_diff(args, world, rank, local_rank):
+    """The batched workload (one spm_assemble_csc_batched call against the
+    same matrices assembled one call each, the latter timed on every 16th
+    matrix and scaled) or the differentiable one (AssembleMM forward +
+    backward against assembly + SpMM).  CUDA events around each call."""
+    import numpy as np
+    import torch
+
+    import paper_1805_03380_gb300 as spm
+    import workloads
+    spec = workload_spec(args.workload)
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, steps):
+        for _ in range(args.warmup):
+            fn()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        torch.cuda.synchronize()
+        for e0, e1 in ev:
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+        torch.cuda.synchronize()
+        return statistics.mean(e0.elapsed_time(e1) for e0, e1 in ev)
+
+    if spec["kind"] == "batched":
+        d = workloads.batched_uniform(seed=workloads.SEED_BASE + 4 + 1000 * rank)
+        ns, tp = np.asarray(d["n"], dtype=np.int64), np.asarray(d["trip_ptr"], dtype=np.int64)
+        rows, cols, vals = (torch.from_numpy(np.ascontiguousarray(d[k])).to(dev) for k in ("rows", "cols", "vals"))
+        rows, cols = rows.to(torch.int32), cols.to(torch.int32)
+        B, total = len(ns), int(tp[-1])
+        hr, hc, ht = torch.from_numpy(ns), torch.from_numpy(ns.copy()), torch.from_numpy(tp)
+        dr, dc, dt = hr.to(dev), hc.to(dev), ht.to(dev)
+        ws = torch.empty(spm.spm_assemble_csc_batched_workspace(hr, hc, ht, vals.dtype, spec["mode"]),
+                         dtype=torch.uint8, device=dev)
+        col_ptr = torch.empty(int((hc + 1).sum()), dtype=torch.int64, device=dev)
+        row_idx = torch.empty(total, dtype=torch.int32, device=dev)
+        out_vals = torch.empty(total, dtype=vals.dtype, device=dev)
+        d_nnz = torch.zeros(B, dtype=torch.int64, device=dev)
+        d_status = torch.zeros(1, dtype=torch.int32, device=dev)
+
+        def batched():
+            spm.spm_assemble_csc_batched(hr, hc, ht, dr, dc, dt, rows, cols, vals, None, spec["mode"], 0, col_ptr,
+                                         row_idx, out_vals, d_nnz, None, d_status, ws)
+        b_ms = timed(batched, args.steps)
+        if int(d_status.item()) != 0:
+            raise RuntimeError(f"batched status {int(d_status.item())}")
+        sample = list(range(0, B, 16))
+        asms = [spm.Assembler((int(ns[i]), int(ns[i])), int(tp[i + 1] - tp[i]), vals.dtype, spec["mode"], device=dev)
+                for i in sample]
+        views = [(rows[int(tp[i]):int(tp[i + 1])], cols[int(tp[i]):int(tp[i + 1])], vals[int(tp[i]):int(tp[i + 1])])
+                 for i in sample]
+
+        def singles():
+            for a, (r, c, v) in zip(asms, views):
+                a.run(r, c, v)
+        s_ms = timed(singles, max(1, args.steps // 5)) * B / len(sample)
+        units, ms = total, b_ms
+        metric = "assembled triplets/sec, 4096 matrices in one batched call"
+        extra = {"matrices": B, "writes": total, "nnz": int(d_nnz.sum().item()),
+                 "single_calls_ms_scaled": s_ms, "single_calls_sample": f"every 16th matrix ({len(sample)}), scaled",
+                 "batched_vs_single_speedup": s_ms / b_ms}
+        sv = 4
+        alg = total * (4 + 4 + sv) + int(d_nnz.sum().item()) * (4 + sv) + int((hc + 1).sum()) * 8
+    else:
+        f = workloads.fem_q1(n_el=spec["n_el"], dtype=spec["dtype"], seed=workloads.SEED_BASE + 5 + 1000 * rank)
+        shape = f["shape"]
+        rows, cols = (torch.from_numpy(f[k]).to(dev).to(torch.int32) for k in ("rows", "cols"))
+        vals = torch.from_numpy(f["vals"]).to(dev)
+        g = torch.Generator(device=dev)
+        g.manual_seed(workloads.SEED_BASE + 5)
+        X = torch.randn(shape[0], 16, device=dev, dtype=vals.dtype, generator=g, requires_grad=True)
+        G = torch.randn(shape[0], 16, device=dev, dtype=vals.dtype, generator=g)
+        v = vals.clone().requires_grad_(True)
+
+        def fwd_bwd():
+            Y = spm.AssembleMM.apply(rows, cols, v, shape, X, spec["mode"], True)
+            (Y * G).sum().backward()
+
+        def asm_mm():
+            A = spm.assemble_csc(rows, cols, vals, shape, mode=spec["mode"])
+            spm.csc_mm(A.col_ptr, A.row_idx, A.vals, shape, X.detach())
+        fb_ms = timed(fwd_bwd, args.steps)
+        am_ms = timed(asm_mm, args.steps)
+        units, ms = len(f["rows"]), fb_ms
+        metric = "assembled triplets/sec through assemble + SpMM forward and backward"
+        extra = {"writes": len(f["rows"]), "nodes": shape[0], "k": 16, "assembly_plus_spmm_ms": am_ms,
+                 "forward_backward_over_assembly_spmm": fb_ms / am_ms}
+        sv = 4
+        alg = None
+    tot_s, tot_units = aggregate(ms / 1000.0 * args.steps, units * args.steps, world, dev)
+    peak, peak_kind = measured_peak()
+    line = {
+        "metric": metric, "value": tot_units / tot_s, "unit": "triplets/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if sv == 4 else "f64", "data": "synthetic",
+        "config": dict({"workload": args.workload, "description": spec["desc"]}, **extra),
+        "gpu": torch.cuda.get_device_name(dev),
+    }
+    if alg is not None:
+        achieved = alg / (ms / 1000.0) / 1e9
+        line["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                            "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind + " copy bandwidth",
+                            "kernel": "whole batched call", "algorithmic_bytes_per_launch": alg,
+                            "bytes_formula": "m*(4+4+sv) + nnz*(4+sv) + sum(n_cols_i+1)*8", "launch_ms_mean": ms}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
 def run_reference(args, world, rank):
     import numpy as np  # noqa: F401
     import workloads
@@ -489,9 +625,9 @@ def run_reference(args, world, rank):
         return
     spec = workload_spec(args.workload)
     sample = args.ref_sample
-    if spec["kind"] in ("lookup", "coo", "trace"):
-        print(json.dumps({"impl": "reference", "unavailable": "the CPU reference leg times the assembly and update "
-                                                              "workloads only"}), flush=True)
+    if spec["kind"] in ("lookup", "coo", "trace", "batched", "diff"):
+        print(json.dumps({"impl": "reference", "unavailable": "the CPU reference leg times the single-matrix "
+                                                              "assembly and update workloads only"}), flush=True)
         return
     if spec["kind"] == "update":
         sample = min(sample, 200_000)
@@ -519,6 +655,9 @@ def run_reference(args, world, rank):
     elif spec["kind"] == "ordered":  # the gaps depend on m: draw the whole stream, use its prefix
         d = workloads.quasi_ordered(m=spec["m"], n=spec["n"], swap_frac=spec["swap"], dtype=spec["dtype"],
                                     seed=workloads.SEED_BASE + 10)
+    elif spec["kind"] in ("lastwrite", "density"):
+        d, _ = make_workload(args.workload)
+        sample = min(sample, len(d["rows"]))
     else:
         d = workloads.fem_q1(n_el=spec["n_el"], dtype=spec["dtype"], seed=workloads.SEED_BASE + 3)
     for _ in range(args.warmup):
@@ -551,7 +690,8 @@ def main():
     ap.add_argument("--workload", default="n8",
                     choices=["n8", "zipf3e7", "zipf1e7", "zipf1e7_f32", "fem2048", "update_n8", "update_n8_set",
                              "update_small", "lookup_n8", "coo_n8", "trace_10k", "ordered_n8",
-                             "quasi_n8", "ordered_2e7"])
+                             "quasi_n8", "ordered_2e7", "c1", "n4_0.01", "n4_0.1", "n4_1", "n4_10", "batched4096",
+                             "c5"])
     ap.add_argument("--cpu-sample", type=int, default=10_000_000, help="writes the CPU oracle baseline times")
     ap.add_argument("--ref-sample", type=int, default=1_000_000, help="writes per step of --impl reference")
     ap.add_argument("--e2e-steps", type=int, default=None)
@@ -572,6 +712,9 @@ def main():
         return
     if workload_spec(args.workload)["kind"] in ("lookup", "coo", "trace"):
         run_access(args, world, rank, local_rank)
+        return
+    if workload_spec(args.workload)["kind"] in ("batched", "diff"):
+        run_batched_or_diff(args, world, rank, local_rank)
         return
 
     import numpy as np
