@@ -489,3 +489,68 @@ def test_trace_matches_dense_and_scipy():
         assert got == np.trace(A.T @ dense_b)           # dyadic values: exact in any order
         assert got == float(sp.csc_matrix((v, ri, cp), shape=shape).multiply(B).sum())
         assert got == oracle.csc_trace_atb(B.indptr, B.indices, B.data, cp, ri, v)  # trace(A^T B) = trace(B^T A)
+
+
+def _hyp_csc(data, st, n_rows, n_cols, values):
+    """A canonical CSC matrix drawn by hypothesis: a dense pattern with values from `values`
+    (zero excluded), converted column by column."""
+    cp, ri, v = [0], [], []
+    for _ in range(n_cols):
+        rows = sorted(set(data.draw(st.lists(st.integers(0, n_rows - 1), max_size=min(n_rows, 6)))))
+        for r in rows:
+            ri.append(r)
+            v.append(data.draw(st.sampled_from(values)))
+        cp.append(len(ri))
+    return np.array(cp, dtype=np.int64), np.array(ri, dtype=np.int64), np.array(v, dtype=np.float64)
+
+
+def test_update_hypothesis():
+    """Writes to an existing matrix, drawn by hypothesis (repeats, zeros, -0.0, NaN and
+    infinities, seq ties): the oracle equals sequential writes on a dense array."""
+    hyp = pytest.importorskip("hypothesis")
+    st = pytest.importorskip("hypothesis.strategies")
+    from tests._refimpl import brute_force_update
+    a_values = [1.0, -1.0, 2.5, 0.25, np.inf, -np.inf, np.nan]
+    w_values = a_values + [0.0, -0.0]
+
+    @hyp.settings(max_examples=150, deadline=None)
+    @hyp.given(st.data())
+    def run(data):
+        n_rows = data.draw(st.integers(1, 12))
+        n_cols = data.draw(st.integers(1, 12))
+        cp, ri, v = _hyp_csc(data, st, n_rows, n_cols, a_values)
+        m = data.draw(st.integers(0, 60))
+        rows = np.array(data.draw(st.lists(st.integers(0, n_rows - 1), min_size=m, max_size=m)), dtype=np.int64)
+        cols = np.array(data.draw(st.lists(st.integers(0, n_cols - 1), min_size=m, max_size=m)), dtype=np.int64)
+        vals = np.array(data.draw(st.lists(st.sampled_from(w_values), min_size=m, max_size=m)), dtype=np.float64)
+        mode = data.draw(st.sampled_from(["set", "sum"]))
+        seq = None
+        if data.draw(st.booleans()):
+            seq = np.array(data.draw(st.lists(st.integers(0, 3), min_size=m, max_size=m)), dtype=np.uint64)
+        got = oracle.csc_update(cp, ri, v, (n_rows, n_cols), rows, cols, vals, mode=mode, seq=seq, out_f32=False)
+        want = brute_force_update(cp, ri, v, (n_rows, n_cols), rows, cols, vals, mode, seq=seq)
+        _assert_csc_equal(got, want)
+
+    run()
+
+
+def test_trace_hypothesis():
+    """trace(A^T B) of matrices drawn by hypothesis (small dyadic values, so every order
+    of summation is exact) equals the dense trace of A^T B."""
+    hyp = pytest.importorskip("hypothesis")
+    st = pytest.importorskip("hypothesis.strategies")
+    values = [1.0, -1.0, 2.5, 0.25, -0.125, 3.0]
+
+    @hyp.settings(max_examples=150, deadline=None)
+    @hyp.given(st.data())
+    def run(data):
+        n_rows = data.draw(st.integers(1, 12))
+        n_cols = data.draw(st.integers(1, 12))
+        A = _hyp_csc(data, st, n_rows, n_cols, values)
+        B = _hyp_csc(data, st, n_rows, n_cols, values)
+        got = oracle.csc_trace_atb(*A, *B)
+        DA = densify(*A, (n_rows, n_cols))
+        DB = densify(*B, (n_rows, n_cols))
+        assert got == float(np.trace(DA.T @ DB))
+
+    run()
