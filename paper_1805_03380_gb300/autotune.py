@@ -3,10 +3,10 @@
 For one workload -- a device-resident write stream and its matrix shape,
 value type and mode -- it times spm_assemble_csc under a list of candidate
 tunings (CUDA events around each call, after warm-up), keeps only the
-candidates whose CSC equals the one the default tuning produces (structure
-bit for bit; values bit for bit in last-write mode, within a few units in
-the last place in sum mode, where the bucket layout moves the binary point
-of the exact accumulator), and returns the fastest.  Results are cached in
+candidates whose CSC equals the one the default tuning produces bit for bit
+(structure and values: the reduction of an element's writes does not depend
+on how the work is split, so every tuning must give the same bytes), and
+returns the fastest.  Results are cached in
 a JSON file keyed by GPU, sizes, value type and mode: the path given, else
 the environment variable SPM_TUNE_CACHE, else no cache.
 
@@ -25,8 +25,7 @@ from . import Assembler, spm_get_tuning, spm_set_tuning
 
 # the fields of spm_tuning the search varies, and the values it tries
 SEARCH_SPACE = {
-    "bucket_target": (4096, 6144, 8192, 12288),
-    "resolve_threads": (512, 1024),
+    "bucket_target": (2048, 2560, 3072, 3584),
     "partition_threads": (512, 1024),
     "sub_bits": (10, 11),
 }
@@ -79,11 +78,7 @@ def apply_cached(shape, m, dtype, mode, flags=0, path=None):
 def _same_result(a, b, mode):
     if a.nnz != b.nnz or not torch.equal(a.col_ptr, b.col_ptr) or not torch.equal(a.row_idx, b.row_idx):
         return False
-    if mode == "set" or a.nnz == 0:
-        return torch.equal(a.vals.view(torch.uint8), b.vals.view(torch.uint8))
-    eps = torch.finfo(a.vals.dtype).eps
-    d = (a.vals - b.vals).abs()
-    return bool((d <= 4 * eps * b.vals.abs()).all())
+    return a.nnz == 0 or torch.equal(a.vals.view(torch.uint8), b.vals.view(torch.uint8))
 
 
 def _time_candidate(shape, rows, cols, vals, mode, reps, warmup):

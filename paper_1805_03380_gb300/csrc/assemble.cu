@@ -14,18 +14,14 @@
 //               level-2 cells so that skewed (Zipf) columns still split evenly
 //   hist     -> one pass over (row, col) counts writes per (block, bucket)
 //   scan     -> per-bucket and per-(block, bucket) offsets
-//   scatter  -> one pass over (row, col, value[, seq]) writes a record
-//               (key-within-bucket << 32 | stream position, value) into the
-//               bucket's contiguous range
-//   resolve  -> a persistent kernel takes buckets in order; each bucket is
-//               sorted in shared memory (counting sort on the top key bits,
-//               then a short insertion sort per sub-range by (key, seq,
-//               position)), duplicate writes are resolved (last write wins,
-//               or a float64 sum in write order), zeros are dropped, and the
-//               bucket's output offset comes from a decoupled look-back over
-//               the preceding buckets of the same matrix; the CSC arrays and
-//               the column offsets of every column that starts inside the
-//               bucket are written directly.
+//   scatter  -> one pass over (row, col, value) writes a 16-byte record
+//               {key within the bucket, stream position, value} into the
+//               bucket's contiguous range (or two passes, through groups of
+//               buckets, when one pass would leave too many partly written
+//               cache lines)
+//   resolve  -> resolve.cu: a persistent kernel loads each bucket into shared
+//               memory, sorts it, resolves repeated writes, drops zeros and
+//               writes the CSC arrays after a decoupled look-back.
 //
 // No kernel ever traps or spins without a bound: out-of-range indices and
 // expired waits are reported in the device status word.
@@ -38,7 +34,7 @@
 #include <vector>
 
 #include "spm_common.cuh"
-#include "exact_sum.cuh"
+#include "device_util.cuh"
 #include <climits>
 
 namespace spm {
@@ -46,33 +42,6 @@ namespace spm {
 // ===========================================================================
 // Small device helpers
 // ===========================================================================
-__device__ __forceinline__ void record_error(const Ctx& c, int code) { atomicCAS(c.status, 0, code); }
-
-__device__ __forceinline__ void record_fatal(const Ctx& c, int code) {
-  atomicCAS(c.status, 0, code);
-  atomicExch(&c.scal->abort, 1u);
-}
-
-__device__ __forceinline__ bool is_aborted(const Ctx& c) {
-  return *reinterpret_cast<volatile uint32_t*>(&c.scal->abort) != 0u;
-}
-
-__device__ __forceinline__ uint64_t global_timer_ns() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-__device__ __forceinline__ uint64_t ld_acquire_u64(const uint64_t* p) {
-  uint64_t v;
-  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-  return v;
-}
-
-__device__ __forceinline__ void st_release_u64(uint64_t* p, uint64_t v) {
-  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-
 __device__ __forceinline__ uint32_t mix32(uint64_t x) {
   x ^= x >> 33;
   x *= 0xff51afd7ed558ccdull;
@@ -80,36 +49,6 @@ __device__ __forceinline__ uint32_t mix32(uint64_t x) {
   x *= 0xc4ceb9fe1a85ec53ull;
   x ^= x >> 33;
   return (uint32_t)x;
-}
-
-// Exclusive scan of one value per thread over the block (blockDim a multiple
-// of 32, at most 1024).  buf needs 32 entries.  Returns the prefix; *total
-// receives the block total.  Contains __syncthreads.
-template <typename T>
-__device__ T block_scan_excl(T v, T* total, T* buf) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  T x = v;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    T y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
-  }
-  if (lane == 31) buf[warp] = x;
-  __syncthreads();
-  if (warp == 0) {
-    T w = lane < nw ? buf[lane] : T(0);
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      T y = __shfl_up_sync(0xffffffffu, w, o);
-      if (lane >= o) w += y;
-    }
-    buf[lane] = w;
-  }
-  __syncthreads();
-  T res = (warp ? buf[warp - 1] : T(0)) + x - v;
-  if (total) *total = buf[nw - 1];
-  __syncthreads();
-  return res;
 }
 
 // Largest i in [lo, hi] with key(i) <= x (requires key(lo) <= x).
@@ -127,34 +66,6 @@ __device__ __forceinline__ uint32_t isqrt_u32(uint32_t x) {
   while ((uint64_t)r * r > x) --r;
   while ((uint64_t)(r + 1) * (r + 1) <= x) ++r;
   return r;
-}
-
-// Division of 32-bit integers by an invariant divisor with a multiply and
-// shifts (Granlund and Montgomery, "Division by invariant integers using
-// multiplication", 1994, the round-up method of their Fig. 4.1): for
-// 1 <= d < 2^32 and l = ceil(log2 d), m = floor(2^32 (2^l - d) / d) + 1 and
-// n / d = (t + ((n - t) >> min(l, 1))) >> max(l - 1, 0), t = mulhi(m, n).
-struct Div32 {
-  uint32_t m, s1, s2;
-};
-
-__host__ __device__ inline Div32 div32_make(uint32_t d) {
-#ifdef __CUDA_ARCH__
-  const int l = d > 1 ? 32 - __clz((int)(d - 1)) : 0;
-#else
-  int l = 0;
-  while ((uint64_t{1} << l) < (uint64_t)d) ++l;
-#endif
-  Div32 r;
-  r.m = (uint32_t)(((uint64_t{1} << 32) * ((uint64_t{1} << l) - d)) / d + 1);
-  r.s1 = l < 1 ? (uint32_t)l : 1u;
-  r.s2 = l > 1 ? (uint32_t)(l - 1) : 0u;
-  return r;
-}
-
-__device__ __forceinline__ uint32_t div32(uint32_t n, const Div32& D) {
-  const uint32_t t = __umulhi(D.m, n);
-  return (t + ((n - t) >> D.s1)) >> D.s2;
 }
 
 // ===========================================================================
@@ -914,7 +825,7 @@ __device__ __forceinline__ bool two_pass_on(const Ctx& c) {
   return c.two_pass != 0 && (int64_t)c.scal->fronts > c.min_fronts;
 }
 
-template <bool BATCHED, bool VEC, bool F64, bool SEQ>
+template <bool BATCHED, bool VEC, bool F64>
 __global__ void __launch_bounds__(1024) k_scatter(Ctx c) {
   extern __shared__ __align__(16) uint32_t sm[];
   const CtaInfo ci = c.cta[blockIdx.x];
@@ -945,7 +856,6 @@ __global__ void __launch_bounds__(1024) k_scatter(Ctx c) {
       asm volatile("st.global.L2::cache_hint.v4.u32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(c.rec + slot), "r"(lk),
                    "r"((uint32_t)t), "r"((uint32_t)vb), "r"((uint32_t)(vb >> 32)), "l"(keep_policy)
                    : "memory");
-      if (SEQ) c.rs[slot] = c.seq[t];
     }
   };
   if (VEC) {
@@ -1352,1204 +1262,11 @@ __global__ void __launch_bounds__(1024) k_part_b(Ctx c) {
 }
 
 // ===========================================================================
-// Resolve: one bucket at a time per block (persistent)
-// ===========================================================================
-// Shared-memory layout of the resolve kernel (host and device agree on it):
-// only the keys and the sort permutation live in shared memory; values,
-// positions and results stay in the bucket's records (L2).  In window mode
-// the second half of the key array holds the record index of each key.
-struct RLayout {
-  size_t keys, perm, sub_a, sub_b, total;
-};
-
-__host__ __device__ inline RLayout resolve_layout(int cap, int sub_bits) {
-  RLayout L;
-  size_t o = 0;
-  auto take = [&](size_t bytes) {
-    const size_t at = o;
-    o = (o + bytes + 15) & ~size_t{15};
-    return at;
-  };
-  L.keys = take(4ull * cap);
-  L.perm = take(2ull * cap);
-  L.sub_a = take(4ull * ((size_t{1} << sub_bits) + 4));
-  L.sub_b = take(4ull * (size_t{1} << sub_bits));
-  L.total = o;
-  return L;
-}
-
-struct RSmem {
-  uint32_t* keys;   // key within the bucket (or window)
-  uint16_t* perm;   // sorted order
-  uint32_t* orig;   // window mode: record index of each key (else null: index = position)
-  uint32_t* sub_a;
-  uint32_t* sub_b;
-};
-
-constexpr unsigned kFull = 0xffffffffu;
-constexpr int kMaxWarps = 32;
-constexpr int kPartBytes = 80;
-
-// Per-warp exchange area of the reduction: a warp whose range of sorted
-// positions starts inside a run that began in an earlier warp's range parks
-// its part of that run here; the warp that holds the run's head merges it.
-struct WarpPart {
-  alignas(16) unsigned char part[kPartBytes];  // reduction state (Red<...>)
-  uint32_t ends;  // the run ends inside this warp's range (or there is no such run)
-  uint32_t fhp;   // sorted position of that run's head (set by the warp that owns it)
-};
-
-struct BlockShared {
-  uint32_t buf[32];
-  uint32_t tot;
-  uint32_t ticket;
-  int64_t excl;
-  uint32_t taken, cum, n_w;
-  int32_t red_i[32];
-  // column arithmetic of the current bucket or window
-  uint64_t col0, r0;  // first key = col0 * n_rows + r0
-  Div32 dv;
-  uint32_t fastdiv;   // keys relative to col0 * n_rows fit 32 bits
-  uint32_t wkept[kMaxWarps];
-  uint32_t wstart[kMaxWarps];
-  int64_t wbase[kMaxWarps];
-  WarpPart wp[kMaxWarps];
-};
-
-// Wait (bounded) for the look-back chain of bucket b to provide its exclusive
-// prefix (the number of stored elements of the same matrix in all earlier
-// buckets).  Called by one full warp: each round reads the states of 32
-// predecessors at once, adds the counts back to the nearest one that holds an
-// inclusive value, or waits while any of those nearer ones has published
-// nothing yet.  Publishes nothing.  Every lane returns the prefix.
-__device__ int64_t lookback_wait_warp(const Ctx& c, int64_t b) {
-  const int lane = threadIdx.x & 31;
-  int64_t excl = 0;
-  int64_t top = b - 1;  // nearest predecessor not yet accounted for
-  const uint64_t t_start = global_timer_ns();
-  uint32_t spins = 0;
-  while (true) {
-    const int64_t bb = top - lane;
-    const uint64_t s = bb >= 0 ? ld_acquire_u64(&c.bk_state[bb]) : kStIncl;
-    const uint64_t flag = s & ~kStMask;
-    const unsigned incl = __ballot_sync(kFull, flag == kStIncl);
-    const unsigned none = __ballot_sync(kFull, flag == 0);
-    const int first_incl = incl ? __ffs(incl) - 1 : 32;
-    const unsigned upto = first_incl >= 31 ? kFull : ((2u << first_incl) - 1u);
-    if ((none & upto) == 0) {
-      uint64_t v = (lane <= first_incl) ? (s & kStMask) : 0ull;
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-      excl += (int64_t)v;
-      if (first_incl < 32) break;
-      top -= 32;
-      continue;
-    }
-    __nanosleep(256);  // leave the issue slots to the other block on this SM meanwhile
-    // leave the wait together: lane 0 decides for the warp
-    int stop = 0;
-    if (lane == 0) {
-      if (is_aborted(c)) {
-        stop = 1;
-      } else if ((++spins & 7) == 0 && global_timer_ns() - t_start > 2000000000ull) {
-        record_fatal(c, SPM_ERR_TIMEOUT);
-        stop = 1;
-      }
-    }
-    if (__shfl_sync(kFull, stop, 0)) break;
-  }
-  return excl;
-}
-
-// Decoupled look-back: publish this bucket's count, wait for the prefix,
-// publish the inclusive value.  Called by one full warp.
-__device__ int64_t lookback_warp(const Ctx& c, int64_t b, uint32_t nnz) {
-  if ((threadIdx.x & 31) == 0) st_release_u64(&c.bk_state[b], kStAgg | nnz);
-  __syncwarp();
-  const int64_t excl = lookback_wait_warp(c, b);
-  if ((threadIdx.x & 31) == 0) st_release_u64(&c.bk_state[b], kStIncl | (uint64_t)(excl + nnz));
-  return excl;
-}
-
-__device__ __forceinline__ uint64_t f32_bits_to_f64_bits(uint64_t v) {
-  return (uint64_t)__double_as_longlong((double)__uint_as_float((uint32_t)v));
-}
-
-__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
-  if (bytes >= 16) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes & ~15u) : "memory");
-}
-
-__device__ __forceinline__ int block_max_int(int v, BlockShared& B) {
-  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(kFull, v, o));
-  if ((threadIdx.x & 31) == 0) B.red_i[threadIdx.x >> 5] = v;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    int x = threadIdx.x < (blockDim.x >> 5) ? B.red_i[threadIdx.x] : INT_MIN;
-    for (int o = 16; o > 0; o >>= 1) x = max(x, __shfl_xor_sync(kFull, x, o));
-    if (threadIdx.x == 0) B.red_i[0] = x;
-  }
-  __syncthreads();
-  const int r = B.red_i[0];
-  __syncthreads();
-  return r;
-}
-
-__device__ __forceinline__ uint64_t rec_val(const uint4& r) { return ((uint64_t)r.w << 32) | r.z; }
-
-template <bool F64>
-__device__ __forceinline__ bool bits_nonzero(uint64_t bits) {
-  return F64 ? (bits & 0x7FFFFFFFFFFFFFFFull) != 0 : (bits & 0x7FFFFFFFull) != 0;
-}
-
-// Value field of a record: the write's value before the reduction, the
-// element's value (at the run's first record) after it.
-template <bool F64>
-__device__ __forceinline__ void store_val(uint4* recs, uint32_t r, uint64_t bits) {
-  uint32_t* p = reinterpret_cast<uint32_t*>(recs + r) + 2;
-  if (F64) {
-    *reinterpret_cast<uint64_t*>(p) = bits;
-  } else {
-    *p = (uint32_t)bits;
-  }
-}
-
-template <bool F64>
-__device__ __forceinline__ uint64_t load_val(const uint4* recs, uint32_t r) {
-  const uint32_t* p = reinterpret_cast<const uint32_t*>(recs + r) + 2;
-  if (F64) return __ldcg(reinterpret_cast<const unsigned long long*>(p));
-  return __ldcg(p);
-}
-
-// Reduction state of (part of) one run of equal keys.  Add mode: the exact
-// sum rounded once -- a single write is its own value, two writes are one
-// IEEE addition (which rounds their exact sum), more writes go through the
-// exact integer accumulator (acc is zero while cnt <= 2).  Last-write mode:
-// the write with the largest (seq, position).
-template <bool F64, bool SUM, bool SEQ>
-struct Red {
-  Acc acc;
-  uint32_t cnt;       // add mode: writes so far, 3 = three or more
-  uint64_t one, two;  // add mode: the first two values while cnt <= 2
-  uint64_t seq, wval;
-  uint32_t pos, idx;  // last-write mode: best write (idx = record index), ~0u = none
-
-  __device__ __forceinline__ void clear() {
-    acc = acc_zero();
-    cnt = 0;
-    one = two = 0;
-    seq = 0;
-    wval = 0;
-    pos = 0;
-    idx = ~0u;
-  }
-  __device__ __forceinline__ static uint64_t wide(uint64_t v) { return F64 ? v : f32_bits_to_f64_bits(v); }
-  // Move the values held aside into the accumulator (cnt becomes 3).
-  __device__ __forceinline__ void spill(int emax) {
-    if (cnt >= 1 && cnt <= 2) {
-      acc_add_bits(acc, wide(one), emax);
-      if (cnt == 2) acc_add_bits(acc, wide(two), emax);
-      cnt = 3;
-    }
-  }
-  __device__ __forceinline__ bool better(uint64_t s2, uint32_t p2) const {
-    return idx == ~0u || s2 > seq || (s2 == seq && p2 > pos);
-  }
-  // One more write (add mode: only used with cnt == 3).
-  __device__ __forceinline__ void add(const uint4& r, uint32_t ridx, const Ctx& c, int64_t seg_start, int emax) {
-    if (SUM) {
-      acc_add_bits(acc, wide(rec_val(r)), emax);
-    } else {
-      const uint64_t s2 = SEQ ? c.rs[seg_start + ridx] : 0ull;
-      if (better(s2, r.y)) {
-        seq = s2;
-        pos = r.y;
-        idx = ridx;
-        wval = rec_val(r);
-      }
-    }
-  }
-  __device__ __forceinline__ void merge(const Red& o, int emax) {
-    if (SUM) {
-      if (o.cnt == 0) return;
-      if (cnt == 0) {
-        *this = o;
-        return;
-      }
-      if (cnt == 1 && o.cnt == 1) {
-        two = o.one;
-        cnt = 2;
-        return;
-      }
-      Red t = o;
-      t.spill(emax);
-      spill(emax);
-      acc_merge(acc, t.acc);
-    } else if (o.idx != ~0u && better(o.seq, o.pos)) {
-      seq = o.seq;
-      pos = o.pos;
-      idx = o.idx;
-      wval = o.wval;
-    }
-  }
-  template <class F>
-  __device__ __forceinline__ Red shuffled(F sh) const {
-    Red o;
-    if (SUM) {
-      o.acc.lo = sh(acc.lo);
-      o.acc.hi = sh(acc.hi);
-      o.acc.flags = sh(acc.flags);
-      o.cnt = sh(cnt);
-      o.one = sh(one);
-      o.two = sh(two);
-      o.seq = o.wval = 0;
-      o.pos = 0;
-      o.idx = ~0u;
-    } else {
-      o.acc = acc_zero();
-      o.cnt = 0;
-      o.one = o.two = 0;
-      o.seq = SEQ ? sh(seq) : 0ull;
-      o.wval = sh(wval);
-      o.pos = sh(pos);
-      o.idx = sh(idx);
-    }
-    return o;
-  }
-  // Final value bits of the element and whether it is stored.
-  __device__ __forceinline__ uint64_t finish(int emax, bool& keep) const {
-    if (SUM) {
-      uint64_t bits;
-      if (cnt == 1) {
-        bits = one;
-      } else if (cnt == 2) {
-        if (F64) {
-          bits = (uint64_t)__double_as_longlong(
-              __dadd_rn(__longlong_as_double((long long)one), __longlong_as_double((long long)two)));
-        } else {
-          const double sum = __dadd_rn((double)__uint_as_float((uint32_t)one), (double)__uint_as_float((uint32_t)two));
-          bits = (uint64_t)__float_as_uint(__double2float_rn(sum));
-        }
-      } else {
-        return acc_round(acc, emax, !F64, &keep);
-      }
-      keep = bits_nonzero<F64>(bits);
-      return bits;
-    }
-    keep = bits_nonzero<F64>(wval);
-    return wval;
-  }
-};
-
-// Column arithmetic of a bucket (or window) whose first key is klo; written
-// by thread 0, read after the next barrier.
-__device__ __forceinline__ void column_setup(BlockShared& B, const MatMeta& mm, uint64_t klo, uint64_t span) {
-  const uint64_t nr = (uint64_t)mm.n_rows;
-  B.col0 = klo / nr;
-  B.r0 = klo - B.col0 * nr;
-  B.fastdiv = (B.r0 + span + nr) < (uint64_t{1} << 32) ? 1u : 0u;
-  B.dv = div32_make((uint32_t)nr);
-}
-
-// floor(x / n_rows) for an offset x from col0 * n_rows
-__device__ __forceinline__ uint64_t col_div(const BlockShared& B, uint64_t x, uint64_t nr) {
-  return B.fastdiv ? (uint64_t)div32((uint32_t)x, B.dv) : x / nr;
-}
-
-// Process the n keys in shared memory (relative to klo, in [0, span)): sort
-// them, reduce each run of equal keys (values from the bucket's records),
-// drop zeros, and write the stored elements, the column offsets of every
-// column that starts inside [klo, klo + span) and the map.  The output
-// position of the first element comes from the look-back (bucket mode) or is
-// base_in (window mode).  Returns the number of stored elements.
-//
-// The reduction is warp-centric: each warp takes an equal range of sorted
-// positions and walks it 32 positions at a time, one per lane; run
-// boundaries come from neighbouring keys, sums and winners from segmented
-// warp scans.  A run that crosses a warp boundary is finished by the warp
-// holding its head, from the parts the following warps park.  Each result
-// is kept in the value field of its run's first record until the output
-// positions are known.
-template <bool F64, bool SUM, bool SEQ, bool POS>
-__device__ uint32_t resolve_records(const Ctx& c, const MatMeta& mm, int64_t b, uint64_t klo, uint64_t span,
-                                    uint32_t n, const RSmem& S, BlockShared& B, bool window, int64_t base_in,
-                                    int64_t seg_start, int emax, uint32_t key_off, int64_t seg_base) {
-  using VT = typename std::conditional<F64, uint64_t, uint32_t>::type;
-  using R = Red<F64, SUM, SEQ>;
-  static_assert(sizeof(R) <= kPartBytes, "reduction state too large");
-  const int tid = threadIdx.x, NT = blockDim.x, lane = tid & 31, w = tid >> 5, NW = NT >> 5;
-  uint4* recs = reinterpret_cast<uint4*>(c.rec + seg_start);
-  uint32_t* const keys = S.keys;
-  uint16_t* const perm = S.perm;
-  const uint32_t* const orig = S.orig;
-  if (tid == 0) column_setup(B, mm, klo, span);  // visible after the next barrier
-  // ---- counting sort on the top key bits
-  const int sbits = span <= 1 ? 0 : ceil_log2_u64(span);
-  const int sshift = sbits > c.sub_bits ? sbits - c.sub_bits : 0;
-  const uint32_t nsub = (uint32_t)(((span - 1) >> sshift) + 1);
-  for (uint32_t q = tid; q <= nsub; q += NT) S.sub_a[q] = 0u;
-  __syncthreads();
-  for (uint32_t k = tid; k < n; k += NT) atomicAdd(&S.sub_a[keys[k] >> sshift], 1u);
-  __syncthreads();
-  {
-    const uint32_t per = (nsub + NT - 1) / NT;
-    const uint32_t a = min(nsub, (uint32_t)tid * per), e = min(nsub, a + per);
-    uint32_t local = 0;
-    for (uint32_t q = a; q < e; ++q) local += S.sub_a[q];
-    uint32_t run = block_scan_excl<uint32_t>(local, &B.tot, B.buf);
-    for (uint32_t q = a; q < e; ++q) {
-      const uint32_t x = S.sub_a[q];
-      S.sub_a[q] = run;
-      S.sub_b[q] = run;
-      run += x;
-    }
-    if (tid == 0) S.sub_a[nsub] = n;
-  }
-  __syncthreads();
-  for (uint32_t k = tid; k < n; k += NT) perm[atomicAdd(&S.sub_b[keys[k] >> sshift], 1u)] = (uint16_t)k;
-  __syncthreads();
-  if (sshift > 0) {  // sub-bins hold several keys: order them by key
-    const uint32_t sa = (uint32_t)(((uint64_t)tid * nsub) / NT), sb = (uint32_t)(((uint64_t)(tid + 1) * nsub) / NT);
-    const uint32_t ea = S.sub_a[sa], eb = S.sub_a[sb];
-    for (uint32_t x = ea + 1; x < eb; ++x) {
-      const uint16_t v = perm[x];
-      const uint32_t kv = keys[v];
-      uint32_t y = x;
-      while (y > ea && keys[perm[y - 1]] > kv) {
-        perm[y] = perm[y - 1];
-        --y;
-      }
-      perm[y] = v;
-    }
-    __syncthreads();
-  }
-  auto key_at = [&](uint32_t p) -> uint32_t { return keys[perm[p]]; };
-  auto ridx_of = [&](uint32_t q) -> uint32_t { return orig ? orig[q] : q; };
-
-  // ---- pass 1: reduce every run; results go to the runs' first records
-  const uint32_t E = ((n + NW - 1) / NW + 31) & ~31u;
-  const uint32_t s = min(n, (uint32_t)w * E), e = min(n, s + E);
-  const bool fstart = s > 0 && s < e && key_at(s) == key_at(s - 1);
-  R carry;  // the run open at the end of the previous chunk (identical in all lanes)
-  carry.clear();
-  R lred;   // this lane's share of the open run from chunks that lie entirely inside it
-  lred.clear();
-  if (SUM) lred.cnt = 3;
-  bool lred_used = false;
-  auto fold = [&]() {  // move the lanes' shares into the carry (uniform again)
-    if (!lred_used) return;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) lred.merge(lred.shuffled([&](auto x) { return __shfl_xor_sync(kFull, x, o); }), emax);
-    carry.merge(lred, emax);
-    lred.clear();
-    if (SUM) lred.cnt = 3;
-    lred_used = false;
-  };
-  bool open = fstart, foreign = fstart, parked = false;
-  uint32_t ckey = fstart ? key_at(s) : 0u;
-  uint32_t chp = 0, chr = 0;  // sorted position and record index of the open run's head
-  uint32_t kept = 0;
-  const bool map_lw = POS && !SUM && c.keep_map;
-
-  // The stored elements of this warp's runs, in key order: (key, -, value)
-  // at seg[0, kept).  (With the map, results stay in the runs' first records
-  // for the positional write pass.)
-  const bool mapping = POS && c.keep_map;
-  const bool deferred = c.deferred != 0;
-  const bool kz = !SUM && c.keep_zeros;  // last-write mode, stored zeros kept
-  uint4* const seg = reinterpret_cast<uint4*>(c.tmp + seg_base) + s;
-  if (lane == 0) B.wstart[w] = s;
-  auto finish_run = [&](const R& r, uint32_t hr, uint32_t hp, bool multi, uint64_t& bits) -> bool {
-    bool keep;
-    bits = r.finish(emax, keep);
-    if (mapping) {
-      if (multi) store_val<F64>(recs, hr, bits);  // a single write's record already holds it
-      // last-write map: the winner's stream position goes to the run's second record
-      if (map_lw && multi) reinterpret_cast<uint32_t*>(recs + ridx_of(perm[hp + 1]))[2] = r.pos;
-    }
-    return keep || kz;
-  };
-  auto append = [&](bool keep, uint32_t key, uint64_t bits) {  // warp-wide
-    const unsigned km = __ballot_sync(kFull, keep);
-    if (!mapping && keep)
-      seg[kept + __popc(km & ((1u << lane) - 1u))] =
-          make_uint4(key + key_off, 0u, (uint32_t)bits, (uint32_t)(bits >> 32));
-    kept += __popc(km);
-  };
-
-  auto chunk = [&](uint32_t base, uint32_t key, uint32_t ridx, const uint4& rec, uint64_t sq) {
-    const uint32_t p = base + lane;
-    const bool valid = p < e;
-    const uint32_t pk = __shfl_up_sync(kFull, key, 1);
-    const bool head = valid && (lane == 0 ? !(open && key == ckey) : key != pk);
-    uint32_t nk = __shfl_down_sync(kFull, key, 1);
-    const bool more = p + 1 < n;
-    if (valid && (lane == 31 || p + 1 == e) && more) nk = key_at(p + 1);
-    const bool tail = valid && (!more || nk != key);
-    const unsigned vm = __ballot_sync(kFull, valid), hm = __ballot_sync(kFull, head), tm = __ballot_sync(kFull, tail);
-    if (hm == vm && tm == vm) {
-      // every write is an element of its own: its value is the result
-      const uint64_t v1 = F64 ? rec_val(rec) : (uint64_t)rec.z;
-      append(valid && (kz || bits_nonzero<F64>(v1)), key, v1);
-      open = foreign = false;
-      return;
-    }
-    if (hm == 0 && tm == 0) {
-      // the whole chunk lies inside the open run: accumulate per lane
-      if (SUM && !lred_used) {
-        carry.spill(emax);
-        carry.cnt = 3;
-      }
-      if (valid) lred.add(rec, ridx, c, seg_start, emax);
-      lred_used = true;
-      return;
-    }
-    fold();
-    const int Lv = 31 - __clz(vm);
-    const unsigned hle = hm & (kFull >> (31 - lane));
-    const int hl = hle ? 31 - __clz(hle) : -1;  // head lane of my run, -1: it began before this chunk
-    const int seg0 = hl >= 0 ? hl : 0;
-    R r;
-    if (SUM) {
-      const uint64_t v = F64 ? rec_val(rec) : (uint64_t)rec.z;
-      uint64_t vp = __shfl_up_sync(kFull, v, 1);
-      if (lane == 0) vp = carry.one;
-      const uint32_t tot = hl >= 0 ? (uint32_t)(lane - hl + 1) : (uint32_t)lane + 1u + carry.cnt;
-      r.clear();
-      r.cnt = min(tot, 3u);
-      r.one = tot == 1 ? v : vp;
-      r.two = v;
-      if (__any_sync(kFull, valid && (tail || lane == Lv) && tot >= 3)) {
-        Acc a = acc_zero();
-        if (valid) acc_add_bits(a, R::wide(v), emax);
-        if (lane == 0 && hl < 0) {
-          R t = carry;
-          t.spill(emax);
-          acc_merge(a, t.acc);
-        }
-        // segmented scan: as many steps as the longest run piece in the chunk needs
-        const uint32_t span_max = __reduce_max_sync(kFull, valid ? (uint32_t)(lane - seg0 + 1) : 0u);
-        if (__any_sync(kFull, a.flags != 0)) {
-          for (uint32_t o = 1; o < span_max; o <<= 1) {
-            const Acc y{__shfl_up_sync(kFull, a.lo, o), __shfl_up_sync(kFull, a.hi, o),
-                        __shfl_up_sync(kFull, a.flags, o)};
-            if (lane - (int)o >= seg0) acc_merge(a, y);
-          }
-        } else {
-          for (uint32_t o = 1; o < span_max; o <<= 1) {
-            const uint64_t lo2 = __shfl_up_sync(kFull, a.lo, o);
-            const int64_t hi2 = __shfl_up_sync(kFull, a.hi, o);
-            if (lane - (int)o >= seg0) acc_merge(a, Acc{lo2, hi2, 0u});
-          }
-        }
-        if (tot >= 3) r.acc = a;
-      }
-    } else {
-      uint64_t bs = SEQ ? sq : 0ull;
-      uint32_t bp = rec.y;
-      int wl = lane;
-      if (lane == 0 && hl < 0 && carry.idx != ~0u && !(bs > carry.seq || (bs == carry.seq && bp > carry.pos))) {
-        bs = carry.seq;
-        bp = carry.pos;
-        wl = 32;
-      }
-      if (!(hm == vm && tm == vm)) {  // some run has more than one write
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const uint64_t bs2 = SEQ ? __shfl_up_sync(kFull, bs, o) : 0ull;
-          const uint32_t bp2 = __shfl_up_sync(kFull, bp, o);
-          const int wl2 = __shfl_up_sync(kFull, wl, o);
-          if (lane - o >= seg0 && (bs2 > bs || (bs2 == bs && bp2 > bp))) {
-            bs = bs2;
-            bp = bp2;
-            wl = wl2;
-          }
-        }
-      }
-      const uint64_t wv = __shfl_sync(kFull, rec_val(rec), wl & 31);
-      const uint32_t wr = __shfl_sync(kFull, ridx, wl & 31);
-      r.clear();
-      r.seq = bs;
-      r.pos = bp;
-      r.idx = wl == 32 ? carry.idx : wr;
-      r.wval = wl == 32 ? carry.wval : wv;
-    }
-    const uint32_t hr = __shfl_sync(kFull, ridx, seg0);
-    const bool fpark = tail && hl < 0 && foreign;
-    bool keep = false;
-    uint64_t rbits = 0;
-    if (fpark) {
-      // the run began in an earlier warp's range: park this part of it
-      *reinterpret_cast<R*>(B.wp[w].part) = r;
-      B.wp[w].ends = 1u;
-    } else if (tail) {
-      keep = finish_run(r, hl >= 0 ? hr : chr, hl >= 0 ? base + hl : chp, hl != lane, rbits);
-    }
-    append(keep, key, rbits);
-    if (__any_sync(kFull, fpark)) parked = true;
-    if ((tm >> Lv) & 1u) {
-      open = foreign = false;
-    } else {  // the last run continues: carry its state
-      carry = r.shuffled([&](auto x) { return __shfl_sync(kFull, x, Lv); });
-      ckey = __shfl_sync(kFull, key, Lv);
-      const int hlv = __shfl_sync(kFull, hl, Lv);
-      if (hlv >= 0) {
-        foreign = false;
-        chp = base + hlv;
-        chr = __shfl_sync(kFull, ridx, hlv);
-      }
-      open = true;
-    }
-  };
-
-  auto load = [&](uint32_t base, uint32_t& key, uint32_t& ridx, uint4& rec, uint64_t& sq) {
-    const uint32_t p = base + lane;
-    key = 0;
-    ridx = 0;
-    rec = make_uint4(0u, 0u, 0u, 0u);
-    sq = 0;
-    if (p < e) {
-      const uint32_t q = perm[p];
-      key = keys[q];
-      ridx = ridx_of(q);
-      rec = __ldcg(recs + ridx);
-      if (SEQ) sq = __ldcg(reinterpret_cast<const unsigned long long*>(c.rs + seg_start + ridx));
-    }
-  };
-
-  for (uint32_t base = s; base < e; base += 64) {  // two chunks in flight
-    uint32_t k0, k1, i0, i1;
-    uint4 r0, r1;
-    uint64_t q0, q1;
-    load(base, k0, i0, r0, q0);
-    const bool second = base + 32 < e;
-    if (second) load(base + 32, k1, i1, r1, q1);
-    chunk(base, k0, i0, r0, q0);
-    if (second) chunk(base + 32, k1, i1, r1, q1);
-  }
-  fold();
-  if (lane == 0 && !parked) {
-    R* pp = reinterpret_cast<R*>(B.wp[w].part);
-    if (open && foreign) {  // the whole range lies inside one run of an earlier warp
-      *pp = carry;
-      B.wp[w].ends = 0u;
-    } else {
-      pp->clear();
-      B.wp[w].ends = 1u;
-    }
-  }
-  __syncthreads();
-  if (open && !foreign) {  // my last run continues into the following ranges
-    bool keep = false;
-    uint64_t rbits = 0;
-    if (lane == 0) {
-      R r = carry;
-      for (int w2 = w + 1; w2 < NW; ++w2) {
-        WarpPart& wp = B.wp[w2];
-        r.merge(*reinterpret_cast<const R*>(wp.part), emax);
-        wp.fhp = chp;
-        if (wp.ends) break;
-      }
-      keep = finish_run(r, chr, chp, true, rbits);
-    }
-    append(lane == 0 && keep, ckey, rbits);
-  }
-  if (lane == 0) B.wkept[w] = kept;
-  __syncthreads();
-  if (w == 0) {
-    const uint32_t x = lane < NW ? B.wkept[lane] : 0u;
-    uint32_t inc = x;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(kFull, inc, o);
-      if (lane >= o) inc += y;
-    }
-    const uint32_t nnz = __shfl_sync(kFull, inc, 31);
-    int64_t ex;
-    if (window) {
-      ex = base_in;
-    } else if (deferred) {
-      ex = 0;  // placed later by k_emit
-    } else if (b == c.withhold) {
-      ex = 0;  // fault injection: publish nothing, wait for nothing
-    } else if (klo == 0) {
-      if (lane == 0) st_release_u64(&c.bk_state[b], kStIncl | (uint64_t)nnz);
-      ex = 0;
-    } else {
-      ex = lookback_warp(c, b, nnz);
-    }
-    if (lane < NW) B.wbase[lane] = ex + (int64_t)(inc - x);
-    if (lane == 0) {
-      B.tot = nnz;
-      B.excl = ex;
-    }
-  }
-  __syncthreads();
-  const uint32_t nnz = B.tot;
-  auto own_from = [&](uint32_t p) -> uint64_t {  // first key owned by the range starting at position p
-    if (p >= n) return span;
-    const uint32_t k = key_at(p);
-    return (p > 0 && key_at(p - 1) == k) ? (uint64_t)k + 1 : (uint64_t)k;
-  };
-  const uint64_t ks = w == 0 ? 0ull : own_from(s);
-  if (deferred && !mapping) {
-    // k_emit places this warp's segment; window calls are compacted by the caller
-    if (!window && lane == 0) {
-      SegDesc d;  // (warp 0's also carries the bucket's first key as col0 * n_rows + r0)
-      d.count = kept;
-      d.pad = w == 0 ? (uint32_t)B.r0 : 0u;
-      d.ks = w == 0 ? B.col0 : 0ull;
-      c.seg_desc[b * c.res_warps + w] = d;
-    }
-    return nnz;
-  }
-
-  // ---- pass 2: write the elements of the runs whose heads lie in my range,
-  // and the offsets of the columns that start in my range of keys
-  int64_t idx = B.wbase[w];
-  const uint64_t nr = (uint64_t)mm.n_rows;
-  const uint64_t col0 = B.col0, r0 = B.r0;
-  const uint64_t ke = own_from(e);
-  uint64_t jn = col0 + col_div(B, r0 + ks + nr - 1, nr);  // first column starting at or after klo + ks
-  const uint64_t je = col0 + col_div(B, r0 + ke + nr - 1, nr);
-  int64_t* colp = c.col_ptr + mm.col_base;
-  int32_t* rowp = c.row_idx + mm.t0;
-  VT* outp = reinterpret_cast<VT*>(c.out_vals) + mm.t0;
-  int64_t mout = -2;  // map: output index of the run continuing from the previous chunk (-2: not stored)
-  uint32_t mwin = 0;  // map, last-write mode: stream position of that run's winner
-  if (mapping && fstart) {
-    const uint32_t hp = B.wp[w].fhp;
-    const uint64_t hb = load_val<F64>(recs, ridx_of(perm[hp]));
-    mout = bits_nonzero<F64>(hb) ? idx - 1 : -2;
-    if (!SUM) mwin = __ldcg(reinterpret_cast<const uint32_t*>(recs + ridx_of(perm[hp + 1])) + 2);
-  }
-  if (!mapping) {
-    // this warp's stored elements, from its segment, 32 at a time
-    for (uint32_t i0 = 0; i0 < kept; i0 += 32) {
-      const uint32_t i = i0 + lane;
-      const bool keep = i < kept;
-      uint4 rr = make_uint4(0u, 0u, 0u, 0u);
-      if (keep) rr = __ldcg(seg + i);
-      const uint32_t key = rr.x;
-      const uint64_t bits = ((uint64_t)rr.w << 32) | rr.z;
-      const unsigned km = __ballot_sync(kFull, keep);
-      uint64_t col = 0;
-      const int64_t o = idx + i0 + lane;
-      if (keep) {
-        const uint64_t x = r0 + key;
-        const uint64_t cr = col_div(B, x, nr);
-        col = col0 + cr;
-        rowp[o] = (int32_t)(x - cr * nr);
-        outp[o] = (VT)bits;
-      }
-      const uint64_t pc = __shfl_up_sync(kFull, col, 1);
-      if (keep)
-        for (uint64_t j = lane ? pc + 1 : jn; j <= col; ++j) colp[j] = o;
-      jn = __shfl_sync(kFull, col, 31 - __clz(km)) + 1;
-    }
-    idx += kept;
-  }
-  uint32_t pkey = fstart ? key_at(s) : 0u;
-  bool popen = fstart;
-  for (uint32_t base0 = s; mapping && base0 < e; base0 += 64) {
-    // two chunks at a time: both chunks' shared-memory and L2 loads are in
-    // flight before either is written out
-    uint32_t keyv[2], ridxv[2], posv[2];
-    bool validv[2], headv[2];
-    uint64_t bitsv[2];
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const uint32_t p = base0 + 32 * h + lane;
-      validv[h] = p < e;
-      keyv[h] = 0;
-      ridxv[h] = 0;
-      if (validv[h]) {
-        const uint32_t q = perm[p];
-        keyv[h] = keys[q];
-        ridxv[h] = ridx_of(q);
-      }
-    }
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const uint32_t pk = __shfl_up_sync(kFull, keyv[h], 1);
-      const uint32_t prev_last = h == 0 ? pkey : __shfl_sync(kFull, keyv[0], 31);
-      const bool prev_open = h == 0 ? popen : true;
-      headv[h] = validv[h] && (lane == 0 ? !(prev_open && keyv[h] == prev_last) : keyv[h] != pk);
-      bitsv[h] = 0;
-      posv[h] = 0;
-      if (mapping) {
-        if (validv[h]) {
-          const uint4 rr = __ldcg(recs + ridxv[h]);
-          posv[h] = rr.y;
-          bitsv[h] = F64 ? rec_val(rr) : (uint64_t)rr.z;
-        }
-      } else if (headv[h]) {
-        bitsv[h] = load_val<F64>(recs, ridxv[h]);
-      }
-    }
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const uint32_t base = base0 + 32 * h;
-      if (base >= e) break;
-      const uint32_t p = base + lane;
-      const bool valid = validv[h], head = headv[h];
-      const uint32_t key = keyv[h], mypos = posv[h];
-      const uint64_t bits = bitsv[h];
-      const bool keep = head && bits_nonzero<F64>(bits);
-      const unsigned km = __ballot_sync(kFull, keep);
-      const unsigned lt = km & ((1u << lane) - 1u);
-      const int64_t i = idx + __popc(lt);
-      uint64_t col = 0;
-      if (keep) {
-        const uint64_t x = r0 + key;
-        const uint64_t cr = col_div(B, x, nr);
-        col = col0 + cr;
-        rowp[i] = (int32_t)(x - cr * nr);
-        outp[i] = (VT)bits;
-      }
-      const uint64_t pc = __shfl_sync(kFull, col, lt ? 31 - __clz(lt) : 0);
-      if (keep)
-        for (uint64_t j = lt ? pc + 1 : jn; j <= col; ++j) colp[j] = i;
-      if (mapping) {
-        uint32_t nk = __shfl_down_sync(kFull, key, 1);
-        if (valid && (lane == 31 || p + 1 == e) && p + 1 < n) nk = key_at(p + 1);
-        const bool multi = p + 1 < n && nk == key;
-        int64_t hout = keep ? i : -2;
-        uint32_t hwin = mypos;
-        if (!SUM && head && multi) hwin = __ldcg(reinterpret_cast<const uint32_t*>(recs + ridx_of(perm[p + 1])) + 2);
-        const unsigned hm = __ballot_sync(kFull, head);
-        const unsigned hle = hm & (kFull >> (31 - lane));
-        const int hl = hle ? 31 - __clz(hle) : -1;
-        const int64_t o2 = __shfl_sync(kFull, hout, hl >= 0 ? hl : 0);
-        const uint32_t w2 = __shfl_sync(kFull, hwin, hl >= 0 ? hl : 0);
-        const int64_t out = hl >= 0 ? o2 : mout;
-        const uint32_t win = hl >= 0 ? w2 : mwin;
-        if (valid) c.map[mypos] = (!SUM && mypos != win) ? -1 : (int32_t)out;
-        const int Lv = 31 - __clz(__ballot_sync(kFull, valid));
-        mout = __shfl_sync(kFull, out, Lv);
-        mwin = __shfl_sync(kFull, win, Lv);
-      }
-      if (km) {
-        jn = __shfl_sync(kFull, col, 31 - __clz(km)) + 1;
-        idx += __popc(km);
-      }
-    }
-    pkey = __shfl_sync(kFull, keyv[1], 31);  // only read when a later pair exists (then chunk 1 is full)
-    popen = true;
-  }
-  for (uint64_t j = jn + lane; j < je; j += 32) colp[j] = idx;
-  __syncthreads();
-  return nnz;
-}
-
-// A single key with more writes than fit in shared memory: streaming
-// reduction over its records in global memory.
-template <bool F64, bool SUM, bool SEQ, bool POS>
-__device__ uint32_t resolve_single_key(const Ctx& c, const MatMeta& mm, uint64_t key, uint32_t lkey, int64_t start,
-                                       uint32_t n, BlockShared& B, int64_t base) {
-  using VT = typename std::conditional<F64, uint64_t, uint32_t>::type;
-  using R = Red<F64, SUM, SEQ>;
-  const int tid = threadIdx.x, NT = blockDim.x, lane = tid & 31, w = tid >> 5, NW = NT >> 5;
-  const uint4* recs = reinterpret_cast<const uint4*>(c.rec + start);
-  int emax = 1;
-  if (SUM) {
-    int el = 0;
-    for (uint32_t k = tid; k < n; k += NT) {
-      const uint4 r = recs[k];
-      const uint64_t v = rec_val(r);
-      if (r.x == lkey) el = max(el, f64_align_exponent(F64 ? v : f32_bits_to_f64_bits(v)));
-    }
-    emax = max(1, block_max_int(el, B));
-  }
-  R st;
-  st.clear();
-  if (SUM) st.cnt = 3;  // everything goes to the accumulator
-  for (uint32_t k = tid; k < n; k += NT) {
-    const uint4 r = recs[k];
-    if (r.x == lkey) st.add(r, k, c, start, emax);
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) st.merge(st.shuffled([&](auto x) { return __shfl_xor_sync(kFull, x, o); }), emax);
-  if (lane == 0) *reinterpret_cast<R*>(B.wp[w].part) = st;
-  __syncthreads();
-  __shared__ uint64_t s_bits;
-  __shared__ uint32_t s_keep, s_win;
-  if (tid == 0) {
-    R all = *reinterpret_cast<const R*>(B.wp[0].part);
-    for (int w2 = 1; w2 < NW; ++w2) all.merge(*reinterpret_cast<const R*>(B.wp[w2].part), emax);
-    bool keep;
-    const uint64_t bits = all.finish(emax, keep);
-    keep = keep || (!SUM && c.keep_zeros);
-    s_bits = bits;
-    s_keep = keep ? 1u : 0u;
-    s_win = SUM ? 0u : all.idx;
-    if (c.deferred) {
-      // the element joins the bucket's results (key within the bucket) for k_emit
-      if (keep) reinterpret_cast<uint4*>(c.tmp + start)[base] = make_uint4(lkey, 0u, (uint32_t)bits, (uint32_t)(bits >> 32));
-    } else {
-      const uint64_t nr = (uint64_t)mm.n_rows;
-      const uint64_t col = key / nr;
-      if (col * nr == key) c.col_ptr[mm.col_base + col] = base;
-      if (keep) {
-        c.row_idx[mm.t0 + base] = (int32_t)(key - col * nr);
-        reinterpret_cast<VT*>(c.out_vals)[mm.t0 + base] = (VT)bits;
-      }
-    }
-  }
-  __syncthreads();
-  const bool keep = s_keep != 0;
-  if (POS && c.keep_map) {
-    for (uint32_t k = tid; k < n; k += NT) {
-      const uint4 r = recs[k];
-      if (r.x != lkey) continue;
-      c.map[r.y] = (!SUM && k != s_win) ? -1 : (keep ? (int32_t)base : -2);
-    }
-  }
-  __syncthreads();
-  return keep ? 1u : 0u;
-}
-
-template <bool F64, bool SUM, bool SEQ, bool POS>
-__global__ void __launch_bounds__(1024) k_resolve(Ctx c) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  __shared__ BlockShared B;
-  __shared__ MatMeta mm;
-  const int tid = threadIdx.x, NT = blockDim.x;
-  const RLayout RL = resolve_layout(c.cap, c.sub_bits);
-  RSmem S;
-  S.keys = reinterpret_cast<uint32_t*>(smraw + RL.keys);
-  S.perm = reinterpret_cast<uint16_t*>(smraw + RL.perm);
-  S.orig = nullptr;
-  S.sub_a = reinterpret_cast<uint32_t*>(smraw + RL.sub_a);
-  S.sub_b = reinterpret_cast<uint32_t*>(smraw + RL.sub_b);
-  const uint32_t NB = c.scal->NB;
-  const uint32_t cap = (uint32_t)c.cap;
-  const uint32_t capw = cap / 2;  // window mode: keys in the first half, record indices in the second
-  while (true) {
-    if (tid == 0) {
-      // take a bucket when ready for it (tickets follow readiness, so a block
-      // waits only on buckets already being worked on); warm L2 with the
-      // bucket that will be taken about one round later
-      B.ticket = is_aborted(c) ? ~0u : atomicAdd(&c.scal->ticket, 1u);
-      const uint32_t ahead = B.ticket + gridDim.x;
-      if (B.ticket < NB && ahead < NB) {
-        const uint32_t nn = c.bk_count[ahead];
-        if (nn <= cap) prefetch_l2(c.rec + c.bk_start[ahead], nn * 16u);
-      }
-    }
-    __syncthreads();
-    const uint32_t b = B.ticket;
-    if (b >= NB) break;
-    const uint32_t info = c.bk_info[b];
-    const int64_t mi = info >> 6;
-    const int w = info & 63;
-    if (tid == 0) mm = c.meta[mi];
-    __syncthreads();
-    const uint64_t klo = c.bk_lo[b];
-    if (mm.K == 0) {
-      for (int64_t jj = tid; jj <= mm.n_cols; jj += NT) c.col_ptr[mm.col_base + jj] = 0;
-      if (tid == 0) {
-        c.d_nnz[mi] = 0;
-        st_release_u64(&c.bk_state[b], kStIncl);
-        if (c.deferred) c.bk_nnz[b] = 0u;
-      }
-      if (c.deferred && tid < c.res_warps) c.seg_desc[(int64_t)b * c.res_warps + tid] = SegDesc{0u, 0u, 0ull};
-      __syncthreads();
-      continue;
-    }
-    const uint64_t span = min(uint64_t{1} << w, mm.K - klo);
-    const int64_t start = c.bk_start[b];
-    const uint32_t n = c.bk_count[b];
-    const uint4* recs = reinterpret_cast<const uint4*>(c.rec + start);
-    int64_t total;
-    if (n <= cap) {
-      int el = 0;
-      uint32_t k = tid;
-      for (; k + 3 * NT < n; k += 4 * NT) {  // four record loads in flight per thread
-        uint4 r[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) r[u] = __ldcg(recs + k + u * NT);
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          S.keys[k + u * NT] = r[u].x;
-          if (SUM) el = max(el, f64_align_exponent(F64 ? rec_val(r[u]) : f32_bits_to_f64_bits(rec_val(r[u]))));
-        }
-      }
-      for (; k < n; k += NT) {
-        const uint4 r = __ldcg(recs + k);
-        S.keys[k] = r.x;
-        if (SUM) el = max(el, f64_align_exponent(F64 ? rec_val(r) : f32_bits_to_f64_bits(rec_val(r))));
-      }
-      S.orig = nullptr;
-      const int emax = SUM ? max(1, block_max_int(el, B)) : 1;
-      __syncthreads();
-      const uint32_t nnz =
-          resolve_records<F64, SUM, SEQ, POS>(c, mm, b, klo, span, n, S, B, false, 0, start, emax, 0u, start);
-      total = B.excl + nnz;
-      if (c.deferred && tid == 0) c.bk_nnz[b] = nnz;
-    } else {
-      // more writes than fit: windows of the key range, each sorted in shared memory
-      if (tid < 32) {
-        const int64_t ex = (klo == 0 || b == c.withhold || c.deferred) ? 0 : lookback_wait_warp(c, b);
-        if (tid == 0) B.excl = ex;
-      }
-      __syncthreads();
-      int64_t base = B.excl;  // deferred: results of this bucket so far
-      int64_t pbase = 0;      // deferred: scratch slots used by the windows so far (>= base)
-      __syncthreads();
-      uint64_t wlo = 0;
-      S.orig = S.keys + capw;
-      while (wlo < span) {
-        int hs = (span - wlo <= 1) ? 0 : max(0, ceil_log2_u64(span - wlo) - c.sub_bits);
-        uint64_t wend = span;
-        uint64_t whi = wlo + 1;
-        int mode = 0;  // 1 = window, 2 = single key
-        while (true) {
-          const uint32_t nbins = (uint32_t)(((wend - wlo - 1) >> hs) + 1);
-          for (uint32_t q = tid; q < nbins; q += NT) S.sub_a[q] = 0u;
-          __syncthreads();
-          for (uint32_t k = tid; k < n; k += NT) {
-            const uint64_t l = recs[k].x;
-            if (l >= wlo && l < wend) atomicAdd(&S.sub_a[(uint32_t)((l - wlo) >> hs)], 1u);
-          }
-          __syncthreads();
-          if (tid == 0) {
-            uint32_t cum = 0, taken = 0;
-            while (taken < nbins && cum + S.sub_a[taken] <= capw) cum += S.sub_a[taken++];
-            B.taken = taken;
-            B.cum = cum;
-          }
-          __syncthreads();
-          if (B.taken > 0) {
-            whi = min(wlo + ((uint64_t)B.taken << hs), wend);
-            mode = 1;
-            break;
-          }
-          if (hs == 0) {
-            mode = 2;
-            break;
-          }
-          wend = wlo + (uint64_t{1} << hs);
-          hs = max(0, hs - c.sub_bits);
-        }
-        __syncthreads();
-        if (mode == 1) {
-          if (tid == 0) B.n_w = 0;
-          __syncthreads();
-          int el = 0;
-          for (uint32_t k = tid; k < n; k += NT) {
-            const uint4 r = recs[k];
-            const uint64_t l = r.x;
-            if (l >= wlo && l < whi) {
-              const uint32_t q = atomicAdd(&B.n_w, 1u);
-              S.keys[q] = (uint32_t)(l - wlo);
-              S.orig[q] = k;
-              if (SUM) el = max(el, f64_align_exponent(F64 ? rec_val(r) : f32_bits_to_f64_bits(rec_val(r))));
-            }
-          }
-          const int emax = SUM ? max(1, block_max_int(el, B)) : 1;
-          __syncthreads();
-          const uint32_t nw = B.n_w;
-          const uint32_t got = resolve_records<F64, SUM, SEQ, POS>(c, mm, b, klo + wlo, whi - wlo, nw, S, B, true,
-                                                                   base, start, emax, (uint32_t)wlo, start + pbase);
-          if (c.deferred) {
-            // move the warps' segments (in order) behind the bucket's earlier
-            // results; every destination lies at or below its source
-            uint4* t4 = reinterpret_cast<uint4*>(c.tmp);
-            for (int w2 = 0; w2 < (NT >> 5); ++w2) {
-              const uint32_t cnt = B.wkept[w2];
-              const int64_t src = start + pbase + B.wstart[w2], dst = start + B.wbase[w2];
-              for (uint32_t i0 = 0; i0 < cnt; i0 += NT) {
-                uint4 v = make_uint4(0u, 0u, 0u, 0u);
-                const bool in = i0 + tid < cnt;
-                if (in) v = t4[src + i0 + tid];
-                __syncthreads();
-                if (in) t4[dst + i0 + tid] = v;
-                __syncthreads();
-              }
-            }
-          }
-          base += got;
-          pbase += nw;
-          wlo = whi;
-        } else {
-          base += resolve_single_key<F64, SUM, SEQ, POS>(c, mm, klo + wlo, (uint32_t)wlo, start, n, B, base);
-          pbase += 1;
-          wlo = wlo + 1;
-        }
-        __syncthreads();
-      }
-      total = base;
-      if (c.deferred) {
-        // one segment: all of the bucket's results, from its first slot
-        if (tid == 0) c.bk_nnz[b] = (uint32_t)total;
-        if (tid < c.res_warps) {
-          const uint64_t col0 = tid == 0 ? klo / (uint64_t)mm.n_rows : 0ull;
-          c.seg_desc[(int64_t)b * c.res_warps + tid] =
-              SegDesc{tid == 0 ? (uint32_t)total : 0u, tid == 0 ? (uint32_t)(klo - col0 * (uint64_t)mm.n_rows) : 0u,
-                      col0};
-        }
-      } else if (tid == 0 && b != c.withhold) {
-        // the inclusive value of a bucket is the matrix-relative end of its output
-        st_release_u64(&c.bk_state[b], kStIncl | (uint64_t)total);
-      }
-    }
-    if (!c.deferred && tid == 0 && klo + span == mm.K) {
-      c.col_ptr[mm.col_base + mm.n_cols] = total;
-      c.d_nnz[mi] = total;
-    }
-    __syncthreads();
-    // the bucket's records are dead now: drop the L2 lines that hold only
-    // this bucket's records, so that the results stored in them are never
-    // written back to HBM
-    {
-      const uint64_t a0 = reinterpret_cast<uint64_t>(c.rec + start);
-      const uint64_t a1 = reinterpret_cast<uint64_t>(c.rec + start + n);
-      const uint64_t l0 = (a0 + 127) & ~127ull, l1 = a1 & ~127ull;
-      for (uint64_t a = l0 + (uint64_t)tid * 128; a < l1; a += (uint64_t)NT * 128)
-        asm volatile("discard.global.L2 [%0], 128;" ::"l"(a) : "memory");
-    }
-  }
-}
-
-// ===========================================================================
-// Deferred placement: one block per bucket writes the bucket's stored
-// elements (the concatenation of its resolve warps' segments, in key order)
-// to their final positions, and the offsets of the columns that start in the
-// bucket's key range.  Each warp takes 32-element pieces of one segment;
-// every element fills the offsets of the columns after the previous
-// element's column up to its own.
-// ===========================================================================
-template <bool F64>
-__global__ void __launch_bounds__(256, 8) k_emit(Ctx c) {
-  using VT = typename std::conditional<F64, uint64_t, uint32_t>::type;
-  __shared__ uint32_t pre[kMaxWarps + 1];   // exclusive prefix of the segment counts
-  __shared__ uint32_t cpre[kMaxWarps + 1];  // exclusive prefix of the segments' 32-element pieces
-  __shared__ uint32_t sst[kMaxWarps];       // first slot of each segment (from the bucket's first)
-  __shared__ uint32_t plast[kMaxWarps];     // key of the element before each segment's first
-  __shared__ uint64_t s_col0, s_nr, s_jn, s_je, s_last;
-  __shared__ uint32_t s_r0, s_fast, s_skip, s_last_bucket;
-  __shared__ int64_t s_out, s_total, s_t0, s_col_base, s_ncols;
-  __shared__ Div32 s_dv;
-  const int tid = threadIdx.x, NT = blockDim.x, NW = c.res_warps, lane = tid & 31;
-  const int64_t b = blockIdx.x;
-  if (b >= (int64_t)c.scal->NB || is_aborted(c)) return;
-  const uint32_t info = c.bk_info[b];
-  const int64_t mi = info >> 6;
-  const uint4* base = reinterpret_cast<const uint4*>(c.tmp + c.bk_start[b]);
-  if (tid < 32) {
-    const uint32_t n = c.bk_count[b];
-    const SegDesc d = tid < NW ? c.seg_desc[b * NW + tid] : SegDesc{0u, 0u, 0ull};
-    const uint32_t E = ((n + NW - 1) / NW + 31) & ~31u;
-    const uint32_t st = min(n, (uint32_t)tid * E);
-    const uint32_t npc = (d.count + 31) >> 5;
-    uint32_t inc = d.count, cinc = npc;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o), z = __shfl_up_sync(0xffffffffu, cinc, o);
-      if (tid >= o) inc += y, cinc += z;
-    }
-    // key of each segment's last element, then of the last element before each segment
-    const uint32_t lastkey = d.count ? __ldcg(base + st + d.count - 1).x : 0u;
-    const unsigned nonempty = __ballot_sync(0xffffffffu, d.count != 0);
-    const unsigned below = nonempty & ((1u << tid) - 1u);
-    const uint32_t pk = __shfl_sync(0xffffffffu, lastkey, below ? 31 - __clz(below) : 0);
-    if (tid < NW) {
-      pre[tid] = inc - d.count;
-      cpre[tid] = cinc - npc;
-      sst[tid] = st;
-      plast[tid] = pk;
-    }
-    if (tid == 31) {
-      pre[NW] = inc;
-      cpre[NW] = cinc;
-    }
-    if (tid == 0) {
-      const MatMeta& mm = c.meta[mi];
-      const uint64_t K = mm.K;
-      s_skip = K == 0 ? 1u : 0u;
-      if (K != 0) {
-        const uint64_t klo = c.bk_lo[b];
-        const uint64_t span = min(uint64_t{1} << (info & 63), K - klo);
-        const uint64_t nr = (uint64_t)mm.n_rows;
-        const uint64_t col0 = d.ks, r0 = d.pad;  // the bucket's first key = col0 * nr + r0
-        const bool fast = (r0 + span + nr) < (uint64_t{1} << 32);
-        const Div32 dv = div32_make((uint32_t)nr);
-        s_col0 = col0;
-        s_r0 = (uint32_t)r0;
-        s_nr = nr;
-        s_fast = fast ? 1u : 0u;
-        s_dv = dv;
-        s_jn = col0 + (r0 ? 1u : 0u);  // first column starting at or after the first key
-        const uint64_t xe = r0 + span + nr - 1;
-        s_je = col0 + (fast ? (uint64_t)div32((uint32_t)xe, dv) : xe / nr);
-        const uint32_t mfirst = c.bk_out[mm.bucket_off];
-        const uint32_t ob = c.bk_out[b];
-        s_out = (int64_t)(ob - mfirst);
-        s_total = (int64_t)(ob + c.bk_nnz[b] - mfirst);
-        s_t0 = mm.t0;
-        s_col_base = mm.col_base;
-        s_ncols = mm.n_cols;
-        s_last_bucket = b == mm.bucket_off + mm.nb - 1 ? 1u : 0u;
-      }
-    }
-  }
-  __syncthreads();
-  if (s_skip) return;  // (resolve wrote the empty matrix's offsets)
-  const uint32_t nres = pre[NW], npieces = cpre[NW];
-  const uint64_t col0 = s_col0, r0 = s_r0, nr = s_nr;
-  const bool fast = s_fast != 0;
-  const Div32 dv = s_dv;
-  const int64_t out = s_out;
-  auto cdiv = [&](uint64_t x) -> uint64_t { return fast ? (uint64_t)div32((uint32_t)x, dv) : x / nr; };
-  int64_t* colp = c.col_ptr + s_col_base;
-  int32_t* rowp = c.row_idx + s_t0;
-  VT* outp = reinterpret_cast<VT*>(c.out_vals) + s_t0;
-  for (uint32_t pc0 = tid >> 5; pc0 < npieces; pc0 += NT >> 5) {
-    int w = 0;  // the segment of this piece: the last w with cpre[w] <= pc0
-    for (int s2 = 16; s2 > 0; s2 >>= 1)
-      if (w + s2 < NW && cpre[w + s2] <= pc0) w += s2;
-    const uint32_t i = (pc0 - cpre[w]) * 32 + lane;  // position in the segment
-    const uint32_t cntw = pre[w + 1] - pre[w];
-    const bool have = i < cntw;
-    const uint32_t e = pre[w] + i;                    // position in the bucket
-    uint64_t col = 0;
-    if (have) {
-      const uint4 rr = __ldcs(base + sst[w] + i);
-      const uint64_t x = r0 + rr.x;
-      const uint64_t cr = cdiv(x);
-      col = col0 + cr;
-      rowp[out + e] = (int32_t)(x - cr * nr);
-      outp[out + e] = (VT)(((uint64_t)rr.w << 32) | rr.z);
-    }
-    // the previous element's column: from the neighbouring lane, else from its key
-    uint64_t pc = __shfl_up_sync(0xffffffffu, col, 1);
-    if (have && lane == 0) {
-      if (e == 0) {
-        pc = s_jn - 1;
-      } else {
-        const uint32_t pkey = i ? __ldcg(base + sst[w] + i - 1).x : plast[w];
-        pc = col0 + cdiv(r0 + pkey);
-      }
-    }
-    if (have)
-      for (uint64_t j = pc + 1; j <= col; ++j) colp[j] = out + e;
-    if (have && e == nres - 1) s_last = col;
-  }
-  __syncthreads();
-  // columns that start after the bucket's last element (all of them if it has none)
-  const uint64_t from = nres ? s_last + 1 : s_jn;
-  for (uint64_t j = from + tid; j < s_je; j += NT) colp[j] = out + nres;
-  if (tid == 0 && s_last_bucket) {
-    colp[s_ncols] = s_total;
-    c.d_nnz[mi] = s_total;
-  }
-}
-
-// ===========================================================================
 // Host side
 // ===========================================================================
 namespace {
 
-constexpr spm_tuning kDefaultTuning = {6144, 11, 1024, 512, 1 << 22, 1 << 19, 1};
+constexpr spm_tuning kDefaultTuning = {3072, 11, 1024, 512, 1 << 22, 1 << 19, 1};
 spm_tuning g_tuning = kDefaultTuning;
 int64_t g_withhold = -1;
 std::mutex g_mutex;
@@ -2580,10 +1297,10 @@ DevState g_dev[64];
 constexpr size_t kAlign = 256;
 size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 
-// Per-mode parameters: whether the resolve kernel keeps stream positions
+// Per-mode parameters: whether the resolve kernel reads stream positions
 // (last-write mode, or the map) and seq (last-write mode with seq), the
-// bucket capacity those choices leave in shared memory, and the planner's
-// target scaled to it.
+// number of writes a bucket may hold to be resolved in shared memory, and the
+// planner's target.
 struct ModeParams {
   bool pos, seq;
   int cap;
@@ -2596,15 +1313,8 @@ ModeParams mode_params(spm_mode mode, uint32_t flags, const spm_tuning& tun) {
   p.pos = !sum || (flags & SPM_KEEP_MAP) != 0;
   p.seq = !sum && (flags & SPM_SEQ_EXPLICIT) != 0;
   p.tgt = std::max<int64_t>(256, (int64_t)tun.bucket_target);
-  // room for twice the target (the planner's estimates are sampled), at
-  // most what fits in shared memory
-  p.cap = (int)std::min<int64_t>(kCapResolve, std::max<int64_t>(1024, 2 * p.tgt) & ~int64_t{15});
+  p.cap = resolve_capacity((flags & SPM_KEEP_MAP) != 0);
   return p;
-}
-
-size_t resolve_smem_bytes(const ModeParams& mp, int threads, int sub_bits) {
-  (void)threads;
-  return resolve_layout(mp.cap, sub_bits).total;
 }
 
 size_t partition_smem_bytes() { return (size_t)(kHistCapSmem + kLutCapSmem) * 4; }
@@ -2633,27 +1343,16 @@ spm_status device_init(int& dev, DevState*& ds) {
   set_smem_attr(k_hist<false, true>, ps);
   set_smem_attr(k_hist<true, false>, ps);
   set_smem_attr(k_hist<true, true>, ps);
-#define SPM_SET_SCATTER(BA, VE)                                  \
-  set_smem_attr(k_scatter<BA, VE, false, false>, ps);            \
-  set_smem_attr(k_scatter<BA, VE, false, true>, ps);             \
-  set_smem_attr(k_scatter<BA, VE, true, false>, ps);             \
-  set_smem_attr(k_scatter<BA, VE, true, true>, ps);
+#define SPM_SET_SCATTER(BA, VE)                    \
+  set_smem_attr(k_scatter<BA, VE, false>, ps);     \
+  set_smem_attr(k_scatter<BA, VE, true>, ps);
   SPM_SET_SCATTER(false, false)
   SPM_SET_SCATTER(false, true)
   SPM_SET_SCATTER(true, false)
   SPM_SET_SCATTER(true, true)
 #undef SPM_SET_SCATTER
+  resolve_set_attributes();
   {
-    // the largest layout (1024 threads, the widest digit)
-    const size_t r = resolve_layout(kCapResolve, kSubBitsMax).total;
-    set_smem_attr(k_resolve<false, true, false, false>, r);
-    set_smem_attr(k_resolve<true, true, false, false>, r);
-    set_smem_attr(k_resolve<false, true, false, true>, r);
-    set_smem_attr(k_resolve<true, true, false, true>, r);
-    set_smem_attr(k_resolve<false, false, false, true>, r);
-    set_smem_attr(k_resolve<true, false, false, true>, r);
-    set_smem_attr(k_resolve<false, false, true, true>, r);
-    set_smem_attr(k_resolve<true, false, true, true>, r);
     set_smem_attr(k_plan, kPlanSmem);
     set_smem_attr(k_part_b, part_b_smem_bytes(1024));
     set_smem_attr(k_part_a<false, false, false>, part_a_smem_bytes(1024));
@@ -2690,7 +1389,7 @@ struct HostPlan {
 
 // Validate the sizes and compute the workspace layout.
 spm_status host_plan(int64_t B, const int64_t* h_nr, const int64_t* h_nc, const int64_t* h_tp, int sv, bool seq,
-                     int64_t tgt, int C, int64_t two_pass_min, int res_warps, HostPlan& hp) {
+                     int64_t tgt, int C, int64_t two_pass_min, HostPlan& hp) {
   if (B < 0 || (B > 0 && (!h_nr || !h_nc || !h_tp))) return SPM_ERR_INVALID_ARG;
   if (B >= (int64_t{1} << 26)) return SPM_ERR_UNSUPPORTED;
   if (B > 0 && h_tp[0] != 0) return SPM_ERR_INVALID_ARG;
@@ -2778,17 +1477,16 @@ spm_status host_plan(int64_t B, const int64_t* h_nr, const int64_t* h_nc, const 
   L.scanpart = take(4 * (size_t)std::max<int64_t>(L.scan_blocks, 1));
   L.hist = take(4 * (size_t)std::max<int64_t>(hist, 1));
   L.rec = take(sizeof(Rec) * (size_t)(m_total + 4));
-  L.rs = seq ? take(8 * (size_t)(m_total + 4)) : o;
-  L.two_pass = !seq && m_total > 0 && m_total >= two_pass_min && two_pass_groups(C, nbcap) <= kMaxGroupsA;
-  L.tmp = take(sizeof(Rec) * (size_t)(m_total + 4));
+  L.two_pass = m_total > 0 && m_total >= two_pass_min && two_pass_groups(C, nbcap) <= kMaxGroupsA;
+  // tmp: the first pass's records of the two-pass partition; otherwise only
+  // the tile states of the ordered single pass
+  L.tmp = take(L.two_pass ? sizeof(Rec) * (size_t)(m_total + 4)
+                          : 8 * (size_t)std::max<int64_t>(ordered_tiles(std::max<int64_t>(m_total, 1)), 2));
   L.rbk = L.two_pass ? take(4 * (size_t)(m_total + 4)) : o;
   L.bk_cur = take(4 * (size_t)std::max<int64_t>(nbcap, 1));
   // one matrix with level-2 tables: a sample count per level-2 cell
   L.l2h_len = (B == 1 && hp.single.H2 > 0) ? (int64_t{1} << (hp.single.L1 + kL2Bits)) : 0;
   L.l2h = L.l2h_len ? take(4 * (size_t)L.l2h_len) : o;
-  L.bk_nnz = take(4 * (size_t)std::max<int64_t>(nbcap, 1));
-  L.bk_out = take(4 * (size_t)std::max<int64_t>(nbcap, 1));
-  L.seg_desc = take(sizeof(SegDesc) * (size_t)std::max<int64_t>(nbcap, 1) * (size_t)res_warps);
   L.total = o;
   return SPM_OK;
 }
@@ -2817,7 +1515,7 @@ void launch_partition(const Ctx& ctx, const Layout& L, bool vec, cudaStream_t st
   k_scan_top<<<1, 1024, 0, st>>>(ctx, L.scan_blocks);
   k_scan_down<<<(unsigned)L.scan_blocks, kScanBlock, 0, st>>>(ctx, ctx.bk_count, ctx.bk_start);
   stage_mark(st, call, 3);
-  const bool f64 = ctx.f64 != 0, sq = ctx.has_seq != 0;
+  const bool f64 = ctx.f64 != 0;
   if (ctx.two_pass) {  // (the device picks one of the two paths; the other's blocks return at once)
     const size_t pa = part_a_smem_bytes(threads);
     if (vec) {
@@ -2834,31 +1532,16 @@ void launch_partition(const Ctx& ctx, const Layout& L, bool vec, cudaStream_t st
     const size_t pb = part_b_smem_bytes(tb);
     k_part_b<<<resident_grid(k_part_b, sms, tb, pb), tb, pb, st>>>(ctx);
   }
-#define SPM_SCATTER(VE, F6, SQ) k_scatter<BATCHED, VE, F6, SQ><<<C, threads, ps, st>>>(ctx)
+#define SPM_SCATTER(VE, F6) k_scatter<BATCHED, VE, F6><<<C, threads, ps, st>>>(ctx)
   if (vec) {
-    if (f64) { if (sq) SPM_SCATTER(true, true, true); else SPM_SCATTER(true, true, false); }
-    else { if (sq) SPM_SCATTER(true, false, true); else SPM_SCATTER(true, false, false); }
+    if (f64) SPM_SCATTER(true, true); else SPM_SCATTER(true, false);
   } else {
-    if (f64) { if (sq) SPM_SCATTER(false, true, true); else SPM_SCATTER(false, true, false); }
-    else { if (sq) SPM_SCATTER(false, false, true); else SPM_SCATTER(false, false, false); }
+    if (f64) SPM_SCATTER(false, true); else SPM_SCATTER(false, false);
   }
 #undef SPM_SCATTER
   stage_mark(st, call, 4);
 }
 
-void launch_resolve(const Ctx& ctx, const ModeParams& mp, int sms, cudaStream_t st, int threads) {
-  const size_t rs = resolve_smem_bytes(mp, threads, ctx.sub_bits);
-#define SPM_RES(F6, SU, SQ, PO) \
-  k_resolve<F6, SU, SQ, PO><<<resident_grid(k_resolve<F6, SU, SQ, PO>, sms, threads, rs), threads, rs, st>>>(ctx)
-  if (ctx.f64) {
-    if (ctx.sum_mode) { if (mp.pos) SPM_RES(true, true, false, true); else SPM_RES(true, true, false, false); }
-    else { if (mp.seq) SPM_RES(true, false, true, true); else SPM_RES(true, false, false, true); }
-  } else {
-    if (ctx.sum_mode) { if (mp.pos) SPM_RES(false, true, false, true); else SPM_RES(false, true, false, false); }
-    else { if (mp.seq) SPM_RES(false, false, true, true); else SPM_RES(false, false, false, true); }
-  }
-#undef SPM_RES
-}
 
 spm_status run_assembly(int64_t B, const int64_t* h_nr, const int64_t* h_nc, const int64_t* h_tp, const int64_t* d_nr,
                         const int64_t* d_nc, const int64_t* d_tp, const int32_t* rows, const int32_t* cols,
@@ -2887,7 +1570,7 @@ spm_status run_assembly(int64_t B, const int64_t* h_nr, const int64_t* h_nc, con
   const int sv = dtype == SPM_F64 ? 8 : 4;
   const ModeParams mp = mode_params(mode, flags, tun);
   HostPlan hp;
-  s = host_plan(B, h_nr, h_nc, h_tp, sv, mp.seq, mp.tgt, ds->sms, tun.two_pass_min_writes, tun.resolve_threads / 32, hp);
+  s = host_plan(B, h_nr, h_nc, h_tp, sv, mp.seq, mp.tgt, ds->sms, tun.two_pass_min_writes, hp);
   if (s != SPM_OK) return s;
   const Layout& L = hp.L;
   if (L.m_total > 0 && (!rows || !cols || !vals || !row_idx || !out_vals)) return SPM_ERR_INVALID_ARG;
@@ -2922,7 +1605,6 @@ spm_status run_assembly(int64_t B, const int64_t* h_nr, const int64_t* h_nc, con
   ctx.scanpart = reinterpret_cast<uint32_t*>(ws + L.scanpart);
   ctx.hist = reinterpret_cast<uint32_t*>(ws + L.hist);
   ctx.rec = reinterpret_cast<Rec*>(ws + L.rec);
-  ctx.rs = mp.seq ? reinterpret_cast<uint64_t*>(ws + L.rs) : nullptr;
   ctx.two_pass = L.two_pass ? 1 : 0;
   ctx.tmp = reinterpret_cast<Rec*>(ws + L.tmp);
   ctx.rbk = L.two_pass ? reinterpret_cast<uint32_t*>(ws + L.rbk) : nullptr;
@@ -2930,11 +1612,6 @@ spm_status run_assembly(int64_t B, const int64_t* h_nr, const int64_t* h_nc, con
   ctx.bk_cur = reinterpret_cast<uint32_t*>(ws + L.bk_cur);
   ctx.groups = (int32_t)two_pass_groups(ds->sms, L.nbcap_total);
   ctx.min_fronts = tun.two_pass_min_fronts;
-  ctx.deferred = keep_map ? 0 : 1;
-  ctx.res_warps = tun.resolve_threads / 32;
-  ctx.bk_nnz = reinterpret_cast<uint32_t*>(ws + L.bk_nnz);
-  ctx.bk_out = reinterpret_cast<uint32_t*>(ws + L.bk_out);
-  ctx.seg_desc = reinterpret_cast<SegDesc*>(ws + L.seg_desc);
   ctx.B = L.B;
   ctx.m_total = L.m_total;
   ctx.S_total = L.S_total;
@@ -2948,7 +1625,6 @@ spm_status run_assembly(int64_t B, const int64_t* h_nr, const int64_t* h_nc, con
   ctx.keep_zeros = (flags & kFlagKeepZeros) != 0 && mode == SPM_MODE_LAST_WRITE && !keep_map;
   ctx.has_seq = mp.seq;
   ctx.tgt = mp.tgt;
-  ctx.cap = mp.cap;
   ctx.sub_bits = tun.sub_bits;
   ctx.withhold = withhold;
 
@@ -2992,20 +1668,11 @@ spm_status run_assembly(int64_t B, const int64_t* h_nr, const int64_t* h_nc, con
   const bool batched = B > 1;
   if (batched) launch_partition<true>(ctx, L, vec, st, tun.partition_threads, ds->sms, call);
   else launch_partition<false>(ctx, L, vec, st, tun.partition_threads, ds->sms, call);
-  launch_resolve(ctx, mp, ds->sms, st, tun.resolve_threads);
+  launch_resolve(ctx, ds->sms, st);
   stage_mark(st, call, 5);
-  if (ctx.deferred) {
-    k_scan_reduce<<<(unsigned)L.scan_blocks, kScanBlock, 0, st>>>(ctx, ctx.bk_nnz);
-    k_scan_top<<<1, 1024, 0, st>>>(ctx, L.scan_blocks);
-    k_scan_down<<<(unsigned)L.scan_blocks, kScanBlock, 0, st>>>(ctx, ctx.bk_nnz, ctx.bk_out);
-    const unsigned blocks = (unsigned)std::max<int64_t>(L.nbcap_total, 1);  // one per bucket (NB <= nbcap)
-    if (ctx.f64) k_emit<true><<<blocks, 256, 0, st>>>(ctx);
-    else k_emit<false><<<blocks, 256, 0, st>>>(ctx);
-  }
-  stage_mark(st, call, 6);
-  // setup, plan, 2 bucket kernels, 6 partition (with room for two passes: 8), resolve,
-  // and without the map 3 scan kernels and the placement
-  g_launches += 11 + (L.S_total > 0 ? 1 : 0) + (L.two_pass ? 2 : 0) + (ctx.deferred ? 4 : 0);
+  stage_mark(st, call, 6);  // (placement is part of the resolve kernel)
+  // setup, plan, 2 bucket kernels, 6 partition (with room for two passes: 8), resolve
+  g_launches += 11 + (L.S_total > 0 ? 1 : 0) + (L.two_pass ? 2 : 0);
   if (cudaGetLastError() != cudaSuccess) return SPM_ERR_CUDA;
   return SPM_OK;
 }
@@ -3051,12 +1718,11 @@ spm_status spm_set_tuning(const spm_tuning* t) {
     g_tuning = kDefaultTuning;
     return SPM_OK;
   }
-  if (t->bucket_target < 256 || t->bucket_target > 4 * kCapResolve) return SPM_ERR_INVALID_ARG;
+  if (t->bucket_target < 256 || t->bucket_target > 65536) return SPM_ERR_INVALID_ARG;
   if (t->sub_bits < 8 || t->sub_bits > kSubBitsMax) return SPM_ERR_INVALID_ARG;
   if (t->partition_threads != 256 && t->partition_threads != 512 && t->partition_threads != 1024)
     return SPM_ERR_INVALID_ARG;
-  if (t->resolve_threads != 256 && t->resolve_threads != 512 && t->resolve_threads != 1024)
-    return SPM_ERR_INVALID_ARG;
+  if (t->resolve_threads != 512) return SPM_ERR_INVALID_ARG;
   if (t->two_pass_min_writes < 0 || t->two_pass_min_fronts < 0) return SPM_ERR_INVALID_ARG;
   if (t->ordered_path != 0 && t->ordered_path != 1) return SPM_ERR_INVALID_ARG;
   g_tuning = *t;
@@ -3119,8 +1785,7 @@ spm_status spm_debug_plan_stats(const void* workspace, size_t ws_bytes, int64_t 
   const int64_t tp[2] = {0, m};
   HostPlan hp;
   const ModeParams mp = mode_params(mode, flags, tun);
-  s = host_plan(1, &n_rows, &n_cols, tp, dtype == SPM_F64 ? 8 : 4, mp.seq, mp.tgt, ds->sms, tun.two_pass_min_writes,
-                tun.resolve_threads / 32, hp);
+  s = host_plan(1, &n_rows, &n_cols, tp, dtype == SPM_F64 ? 8 : 4, mp.seq, mp.tgt, ds->sms, tun.two_pass_min_writes, hp);
   if (s != SPM_OK) return s;
   if (ws_bytes < hp.L.total) return SPM_ERR_WORKSPACE_TOO_SMALL;
   const char* ws = static_cast<const char*>(workspace);
@@ -3167,7 +1832,7 @@ spm_status spm_assemble_csc_batched_workspace(int64_t batch, const int64_t* h_n_
   HostPlan hp;
   const ModeParams mp = mode_params(mode, flags, tun);
   const spm_status s = host_plan(batch, h_n_rows, h_n_cols, h_trip_ptr, dtype == SPM_F64 ? 8 : 4, mp.seq, mp.tgt,
-                                 num_sms_for_sizing(), tun.two_pass_min_writes, tun.resolve_threads / 32, hp);
+                                 num_sms_for_sizing(), tun.two_pass_min_writes, hp);
   if (s != SPM_OK) return s;
   *bytes = hp.L.total;
   return SPM_OK;

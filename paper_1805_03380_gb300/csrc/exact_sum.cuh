@@ -1,15 +1,19 @@
 // Exact, order-independent summation of float64 values for the add mode.
 //
-// Repeated writes to one element are accumulated as integers: every finite
-// value v = mant * 2^(e - 1075) is aligned to a fixed binary point chosen per
-// bucket (58 bits below the bucket's largest exponent) and added into a
-// signed 128-bit accumulator.  Integer addition is associative, so the result
-// does not depend on the order in which the writes arrive or on how the work
-// is split between threads; it is rounded once to the output type
-// (round-to-nearest-even).  Bits of a value that lie more than 58 bits below
-// the bucket's largest exponent are truncated (toward zero, per value): at most
-// 2^-110 of the largest value per write.  NaN and infinities are carried as
-// flags with IEEE semantics (NaN if any NaN or both infinities).
+// The writes to one element are accumulated as integers.  Every finite value
+// v = mant * 2^(e - 1075) (float32 values are first widened exactly) is
+// truncated toward zero to a multiple of 2^(E - 1075 - kAlignBits), where E is
+// the largest exponent among the writes of that element, and added into a
+// signed 128-bit accumulator; the integer sum is rounded once to the output
+// type (round-to-nearest-even).  Integer addition is associative, so the
+// result depends only on the element's values, not on their order or on how
+// the work is split.  A value loses bits only when it lies more than
+// kAlignBits binades below the element's largest value, and then less than
+// 2^-(kAlignBits + 52) of that value; when every write of the element lies
+// within kAlignBits binades of the largest, the result is the correctly
+// rounded exact sum.  Aligned values are below 2^(53 + kAlignBits) = 2^95, so
+// 2^32 of them cannot overflow the accumulator.  NaN and infinities are
+// carried as flags with IEEE semantics (NaN if any NaN or both infinities).
 //
 // GB300's float64 pipe is a small fraction of its integer pipes, so this is
 // also much faster than a chain of float64 additions.
@@ -25,7 +29,7 @@
 
 namespace spm {
 
-constexpr int kAlignBits = 58;  // binary point: 58 bits below the largest exponent
+constexpr int kAlignBits = 42;  // binary point: 42 bits below the last mantissa bit of the largest value
 
 struct Acc {
   uint64_t lo;

@@ -17,9 +17,9 @@
 // then runs as usual and overwrites everything (and reports the bad index).
 //
 // Reduction rules are those of the general path: last-write mode keeps the
-// last write of a run; add mode uses one write as it is, one IEEE addition for
-// two, and for more the exact fixed-point accumulator (binary point 58 bits
-// below the run's largest exponent) rounded once.
+// last write of a run; add mode uses one write as it is and otherwise the
+// exact fixed-point accumulator (binary point set by the run's largest
+// exponent, exact_sum.cuh) rounded once.
 #include <algorithm>
 #include <cstdint>
 #include <mutex>
@@ -71,29 +71,18 @@ __device__ uint64_t reduce_run(const uint64_t* val, int j, int e, bool keep_zero
     keep = keep_zeros || (F64 ? (b & 0x7FFFFFFFFFFFFFFFull) != 0 : (b & 0x7FFFFFFFull) != 0);
     return b;
   }
-  const int len = e - j;
-  uint64_t bits;
-  if (len == 1) {
-    bits = val[j];
-  } else if (len == 2) {
-    if (F64) {
-      bits = (uint64_t)__double_as_longlong(__dadd_rn(__longlong_as_double((long long)val[j]),
-                                                      __longlong_as_double((long long)val[j + 1])));
-    } else {
-      const double s = __dadd_rn((double)__uint_as_float((uint32_t)val[j]), (double)__uint_as_float((uint32_t)val[j + 1]));
-      bits = (uint64_t)__float_as_uint(__double2float_rn(s));
-    }
-  } else {
-    int emax = 1;
-    for (int q = j; q < e; ++q) emax = max(emax, f64_align_exponent(o_wide(val[q], F64)));
-    Acc acc = acc_zero();
-    for (int q = j; q < e; ++q) acc_add_bits(acc, o_wide(val[q], F64), emax);
-    bool nz;
-    bits = acc_round(acc, emax, !F64, &nz);
-    keep = nz;
+  if (e - j == 1) {
+    const uint64_t bits = val[j];
+    keep = F64 ? (bits & 0x7FFFFFFFFFFFFFFFull) != 0 : (bits & 0x7FFFFFFFull) != 0;
     return bits;
   }
-  keep = F64 ? (bits & 0x7FFFFFFFFFFFFFFFull) != 0 : (bits & 0x7FFFFFFFull) != 0;
+  int emax = 1;
+  for (int q = j; q < e; ++q) emax = max(emax, f64_align_exponent(o_wide(val[q], F64)));
+  Acc acc = acc_zero();
+  for (int q = j; q < e; ++q) acc_add_bits(acc, o_wide(val[q], F64), emax);
+  bool nz;
+  const uint64_t bits = acc_round(acc, emax, !F64, &nz);
+  keep = nz;
   return bits;
 }
 

@@ -1,0 +1,1160 @@
+// libspm: per-bucket resolution of the sync step (sm_103a).
+//
+// After the partition, the writes of one bucket (an aligned range of the
+// paper's linear index row + col * n_rows, Section 3.3) lie contiguously in
+// the record array as 16-byte records {key within the bucket, stream
+// position, value bits}.  One persistent kernel (two blocks per SM) takes the
+// buckets in order (a ticket, fetched one bucket ahead) and, per bucket:
+//
+//   load     one bulk copy (cp.async.bulk, completed on an mbarrier) moves the
+//            bucket's records into shared memory; the bucket one round ahead
+//            is prefetched into L2 meanwhile
+//   sort     a counting sort on the top key bits (shared-memory atomics give
+//            each write its rank in its sub-bin), then each thread orders the
+//            few keys of its sub-bins by insertion (a bitonic sort of the whole
+//            bucket when some sub-bin is large); equal keys may end up in any
+//            order, the reduction does not depend on it
+//   reduce   the sorted positions are cut into one range per warp at run
+//            boundaries, so that no run of equal keys spans two warps; each
+//            lane reduces the runs in its part of the warp's range
+//            sequentially, and runs that cross lanes are finished with
+//            segmented warp scans (shuffles, no block barrier).
+//              add mode: the exact sum of the run (exact_sum.cuh), its binary
+//              point set by the run's own largest exponent (found in a first
+//              pass); a single write is its own value
+//              last-write mode: the write with the largest (seq, position)
+//   zeros    an element whose value compares equal to zero is dropped (after
+//            rounding to the output type), as CSC stores non-zeros only
+//            (Section 3.1)
+//   place    the stored elements are numbered (block scan) and the bucket's
+//            count is published for a decoupled look-back over the buckets of
+//            the same matrix; the elements themselves are written back over
+//            the bucket's records (still in L2), and the block places them in
+//            the CSC arrays at the start of its next bucket, while that
+//            bucket's bulk copy is in flight: by then the buckets before it
+//            have published their counts, so the look-back rarely waits.  The
+//            lines are then discarded from L2, so the round trip costs no HBM
+//            traffic.
+//
+// Calls that keep the map (and buckets with more writes than fit in shared
+// memory) place their elements at once instead: a bucket that is too large is
+// resolved in windows of its key range (records gathered from global memory),
+// first to count its elements, then to write them; one key with more writes
+// than a window holds is reduced by a streaming pass.
+//
+// No kernel traps or waits without a bound: an expired wait is reported as
+// SPM_ERR_TIMEOUT in the device status word and the call stops.
+#include <climits>
+#include <cstdint>
+#include <type_traits>
+
+#include "device_util.cuh"
+#include "exact_sum.cuh"
+
+namespace spm {
+namespace {
+
+constexpr int kRT = 512;                    // threads per resolve block (two blocks per SM)
+constexpr int kRW = kRT / 32;               // warps per block
+constexpr int kRI = 8;                      // sorted positions per thread at the capacity
+constexpr int kRCap = kRT * kRI;            // writes of one bucket resolved in shared memory
+constexpr int kRCapNow = kRCap / 2;         // ... when the elements are staged in shared memory
+constexpr int kRBins = 1 << kSubBitsMax;    // sub-bins of the counting sort, at most
+constexpr uint32_t kRSmallSort = 64;        // largest sub-bin ordered by insertion
+constexpr uint16_t kKept = 0x8000u;         // perm[] flag: the run ending here is stored
+
+// Dynamic shared memory: records (the upper half doubles as the staging area
+// of elements placed at once), sorted keys, sorted record indices, sub-bin
+// counters (later the runs' largest exponents).
+struct RLay {
+  size_t R, stage_key, stage_val, skey, perm, bins, total;
+};
+__host__ __device__ constexpr RLay rlay() {
+  return RLay{0,
+              size_t{16} * kRCapNow,
+              size_t{16} * kRCapNow + size_t{4} * kRCapNow,
+              size_t{16} * kRCap,
+              size_t{20} * kRCap,
+              size_t{22} * kRCap,
+              size_t{22} * kRCap + (((size_t)(kRBins + 1) * 4 + 15) & ~size_t{15})};
+}
+
+// ---------------------------------------------------------------------------
+// Bulk copies and mbarriers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+// global -> own shared memory, 16-byte aligned addresses and a size that is a
+// multiple of 16
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for one phase of the mbarrier; false when the limit expired.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  uint64_t t0 = 0;
+  for (uint32_t spins = 0;; ++spins) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((spins & 63) == 63) {
+      const uint64_t t = global_timer_ns();
+      if (!t0) t0 = t;
+      else if (t - t0 > kWaitLimitNs) return false;
+    }
+  }
+}
+__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
+  if (bytes >= 16) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes & ~15u) : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// Values carried by the segmented warp scans
+// ---------------------------------------------------------------------------
+template <bool UP>
+__device__ __forceinline__ uint32_t sh32(uint32_t x, int o) {
+  return UP ? __shfl_up_sync(kFull, x, o) : __shfl_down_sync(kFull, x, o);
+}
+template <bool UP>
+__device__ __forceinline__ uint64_t sh64(uint64_t x, int o) {
+  return UP ? __shfl_up_sync(kFull, x, o) : __shfl_down_sync(kFull, x, o);
+}
+
+struct EV {  // largest alignment exponent of a run (so far)
+  int e;
+};
+struct AV {  // exact sum (two's complement 128-bit integer) and IEEE special flags
+  uint64_t lo, hi;
+  uint32_t f;
+};
+struct WV {  // last-write winner: largest (seq, position), its value
+  uint64_t seq, val;
+  uint32_t pos, ok;
+};
+struct OV {  // output index of a run (-2: removed; INT_MIN: none) and its winner's position
+  int32_t out;
+  uint32_t win;
+};
+
+template <bool UP>
+__device__ __forceinline__ EV shf(const EV& v, int o) {
+  return EV{(int)sh32<UP>((uint32_t)v.e, o)};
+}
+template <bool UP>
+__device__ __forceinline__ AV shf(const AV& v, int o) {
+  return AV{sh64<UP>(v.lo, o), sh64<UP>(v.hi, o), sh32<UP>(v.f, o)};
+}
+template <bool UP>
+__device__ __forceinline__ WV shf(const WV& v, int o) {
+  return WV{sh64<UP>(v.seq, o), sh64<UP>(v.val, o), sh32<UP>(v.pos, o), sh32<UP>(v.ok, o)};
+}
+template <bool UP>
+__device__ __forceinline__ OV shf(const OV& v, int o) {
+  return OV{(int32_t)sh32<UP>((uint32_t)v.out, o), sh32<UP>(v.win, o)};
+}
+
+__device__ __forceinline__ AV av_add(const AV& a, const AV& b) {
+  const uint64_t lo = a.lo + b.lo;
+  return AV{lo, a.hi + b.hi + (lo < a.lo ? 1ull : 0ull), a.f | b.f};
+}
+__device__ __forceinline__ AV av_of(const Acc& a) { return AV{a.lo, (uint64_t)a.hi, a.flags}; }
+__device__ __forceinline__ Acc acc_of(const AV& a) { return Acc{a.lo, (int64_t)a.hi, a.f}; }
+__device__ __forceinline__ bool wv_better(const WV& a, const WV& b) {  // is b later than a
+  return b.ok && (!a.ok || b.seq > a.seq || (b.seq == a.seq && b.pos > a.pos));
+}
+
+struct OpMax {
+  __device__ EV operator()(const EV& a, const EV& b) const { return EV{max(a.e, b.e)}; }
+};
+struct OpAdd {
+  __device__ AV operator()(const AV& a, const AV& b) const { return av_add(a, b); }
+};
+struct OpWin {
+  __device__ WV operator()(const WV& a, const WV& b) const { return wv_better(a, b) ? b : a; }
+};
+struct OpNear {  // the value nearer in the flow direction, unless it is empty
+  __device__ OV operator()(const OV& far, const OV& near) const { return near.out == INT_MIN ? far : near; }
+};
+
+// Segmented scan over the lanes of a warp in the direction of the flow (FWD:
+// from lower to higher lane; otherwise from higher to lower).  Lane l gives
+// (reset_l, v_l); out_l = reset_l ? v_l : op(out_prev, v_l) where out_prev is
+// the neighbour upstream.  Returns out_prev (ident for the first lane of the
+// flow).
+template <bool FWD, class T, class Op>
+__device__ __forceinline__ T warp_seg_scan(bool reset, const T& v, const T& ident, Op op) {
+  const int lane = threadIdx.x & 31;
+  bool f = reset;
+  T x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const bool f2 = sh32<FWD>(f ? 1u : 0u, o) != 0;
+    const T x2 = shf<FWD>(x, o);
+    if (FWD ? lane >= o : lane + o < 32) {
+      if (!f) x = op(x2, x);
+      f = f || f2;
+    }
+  }
+  const T xe = shf<FWD>(x, 1);
+  return (FWD ? lane == 0 : lane == 31) ? ident : xe;
+}
+
+// ---------------------------------------------------------------------------
+// Buckets, key ranges and their place in the output
+// ---------------------------------------------------------------------------
+// Column arithmetic of a key range [klo, klo + span): klo = col0 * n_rows + r0.
+struct Range {
+  uint64_t klo, span, col0, r0;
+  Div32 dv;
+  uint32_t fastdiv;  // r0 + span + n_rows < 2^32: 32-bit division by n_rows
+};
+__device__ __forceinline__ Range make_range(uint64_t nr, uint64_t klo, uint64_t span) {
+  Range r;
+  r.klo = klo;
+  r.span = span;
+  r.col0 = klo / nr;
+  r.r0 = klo - r.col0 * nr;
+  r.fastdiv = (r.r0 + span + nr) < (uint64_t{1} << 32) ? 1u : 0u;
+  r.dv = div32_make((uint32_t)nr);
+  return r;
+}
+__device__ __forceinline__ uint64_t col_of(const Range& R, uint64_t x, uint64_t nr) {
+  return R.fastdiv ? (uint64_t)div32((uint32_t)x, R.dv) : x / nr;
+}
+
+struct Desc {
+  uint32_t b, n;      // bucket, its writes
+  uint32_t nnz;       // its stored elements (after the reduction)
+  uint32_t valid;
+  int64_t start;      // first record of the bucket
+  int64_t mi;         // matrix
+  int64_t n_rows, n_cols, col_base, t0;
+  uint64_t K;
+  Range rg;           // the bucket's key range
+};
+
+// Bucket b's descriptor (one thread; reads the bucket tables and the matrix).
+__device__ __forceinline__ Desc load_desc(const Ctx& c, uint32_t b) {
+  Desc d;
+  d.b = b;
+  d.valid = 1;
+  d.nnz = 0;
+  d.n = c.bk_count[b];
+  d.start = c.bk_start[b];
+  const uint32_t info = c.bk_info[b];
+  const uint64_t klo = c.bk_lo[b];
+  d.mi = info >> 6;
+  const MatMeta& mm = c.meta[d.mi];
+  d.n_rows = mm.n_rows;
+  d.n_cols = mm.n_cols;
+  d.col_base = mm.col_base;
+  d.t0 = mm.t0;
+  d.K = mm.K;
+  const uint64_t span = mm.K == 0 ? 0 : min(uint64_t{1} << (info & 63), mm.K - klo);
+  d.rg = mm.K == 0 ? Range{0, 0, 0, 0, Div32{0, 0, 0}, 0} : make_range((uint64_t)mm.n_rows, klo, span);
+  return d;
+}
+
+struct RShared {
+  Desc cur, pend;     // the bucket being resolved; the bucket whose elements wait to be placed
+  Range win;          // window (or single key) being resolved at once
+  int64_t base, pbase;
+  uint32_t wk[32];    // per warp: stored elements
+  uint32_t buf[32];
+  uint32_t tot, maxbin, nw, taken, abort;
+  // single key: result
+  uint64_t kbits;
+  uint32_t kkeep, kwin;
+  int kmax;
+  alignas(16) unsigned char parts[kRW * 32];  // per warp partial of a single key
+  uint64_t bar;       // mbarrier of the bulk copy
+};
+
+__device__ __forceinline__ uint64_t f32_bits_to_f64_bits(uint64_t v) {
+  return (uint64_t)__double_as_longlong((double)__uint_as_float((uint32_t)v));
+}
+template <bool F64>
+__device__ __forceinline__ uint64_t wide(uint64_t v) {
+  return F64 ? v : f32_bits_to_f64_bits(v);
+}
+template <bool F64>
+__device__ __forceinline__ bool bits_nonzero(uint64_t bits) {
+  return F64 ? (bits & 0x7FFFFFFFFFFFFFFFull) != 0 : (bits & 0x7FFFFFFFull) != 0;
+}
+template <bool F64>
+__device__ __forceinline__ int align_exp(uint64_t raw) {
+  return max(0, f64_align_exponent(wide<F64>(raw)));
+}
+
+// Write the nnz stored elements of the key range R (get(li) gives the key
+// relative to R.klo and the value bits of the li-th, in key order) from
+// matrix-relative output index base, and the offsets of every column that
+// starts inside the range.  Called by the whole block.
+template <bool F64, class Get>
+__device__ void emit_range(const Ctx& c, const Desc& D, const Range& R, uint32_t nnz, int64_t base, Get get) {
+  using VT = typename std::conditional<F64, uint64_t, uint32_t>::type;
+  const int tid = threadIdx.x, lane = tid & 31;
+  const uint64_t nr = (uint64_t)D.n_rows, col0 = R.col0, r0 = R.r0;
+  int64_t* colp = c.col_ptr + D.col_base;
+  int32_t* rowp = c.row_idx + D.t0;
+  VT* outp = reinterpret_cast<VT*>(c.out_vals) + D.t0;
+  const uint64_t jn = col0 + (r0 ? 1u : 0u);                       // first column starting in the range
+  const uint64_t je = col0 + col_of(R, r0 + R.span + nr - 1, nr);  // first column starting after it
+  uint64_t lastcol = jn - 1;
+  for (uint32_t li0 = tid & ~31u; li0 < nnz; li0 += blockDim.x) {
+    const uint32_t li = li0 + lane;
+    const bool have = li < nnz;
+    uint64_t col = 0;
+    if (have) {
+      uint32_t key;
+      uint64_t bits;
+      get(li, key, bits);
+      const uint64_t x = r0 + key;
+      const uint64_t cr = col_of(R, x, nr);
+      col = col0 + cr;
+      rowp[base + li] = (int32_t)(x - cr * nr);
+      outp[base + li] = (VT)bits;
+    }
+    uint64_t pc = __shfl_up_sync(kFull, col, 1);
+    if (have && lane == 0) {
+      if (li == 0) {
+        pc = jn - 1;
+      } else {
+        uint32_t key;
+        uint64_t bits;
+        get(li - 1, key, bits);
+        pc = col0 + col_of(R, r0 + key, nr);
+      }
+    }
+    // offsets of the columns (pc, col]: this element is the first of each
+    const uint64_t gap = have ? col - pc : 0;
+    if (gap > 0 && gap <= 32)
+      for (uint64_t j = pc + 1; j <= col; ++j) colp[j] = base + li;
+    unsigned big = __ballot_sync(kFull, gap > 32);
+    while (big) {  // long gaps: the warp fills them together
+      const int L = __ffs(big) - 1;
+      big &= big - 1;
+      const uint64_t a = __shfl_sync(kFull, pc, L) + 1, e = __shfl_sync(kFull, col, L);
+      const int64_t v = base + (int64_t)__shfl_sync(kFull, li, L);
+      for (uint64_t j = a + lane; j <= e; j += 32) colp[j] = v;
+    }
+  }
+  // columns that start after the last element (all of them if there is none)
+  if (nnz) {
+    uint32_t key;
+    uint64_t bits;
+    get(nnz - 1, key, bits);
+    lastcol = col0 + col_of(R, r0 + key, nr);
+  }
+  for (uint64_t j = lastcol + 1 + tid; j < je; j += blockDim.x) colp[j] = base + nnz;
+}
+
+// ---------------------------------------------------------------------------
+// One set of records in shared memory
+// ---------------------------------------------------------------------------
+// How the stored elements leave resolve_tile.
+enum : int {
+  kCount = 0,  // only counted
+  kDefer = 1,  // written over the bucket's records, {key, -, value}, placed later
+  kNow = 2     // placed at once (output index from get_base, called by warp 0)
+};
+
+// Resolve the n records R[0, n) of bucket D (keys relative to Rg.klo, in
+// [0, Rg.span)).  Returns the number of stored elements.  kNow needs
+// n <= kRCapNow.  Ends with a barrier.
+template <bool F64, bool SUM, bool SEQ, bool MAP, class GetBase>
+__device__ __noinline__ uint32_t resolve_tile(const Ctx& c, RShared& S, unsigned char* smem, uint32_t n, const Desc& D,
+                                 const Range& Rg, int mode, GetBase get_base) {
+  constexpr RLay L = rlay();
+  uint4* const R = reinterpret_cast<uint4*>(smem + L.R);
+  const uint64_t* const RV = reinterpret_cast<const uint64_t*>(smem + L.R);
+  uint64_t* const RVw = reinterpret_cast<uint64_t*>(smem + L.R);
+  uint32_t* const skey = reinterpret_cast<uint32_t*>(smem + L.skey);
+  uint16_t* const perm = reinterpret_cast<uint16_t*>(smem + L.perm);
+  uint32_t* const bins = reinterpret_cast<uint32_t*>(smem + L.bins);
+  uint16_t* const rmax = reinterpret_cast<uint16_t*>(smem + L.bins);  // after the sort: largest exponents
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const bool keep_zeros = !SUM && c.keep_zeros;
+
+  // ---- counting sort on the top key bits (about one sub-bin per write)
+  const uint64_t span = Rg.span;
+  const int sbits = span <= 1 ? 0 : ceil_log2_u64(span);
+  const int bbits = min(c.sub_bits, max(4, n <= 1 ? 0 : ceil_log2_u64(n)));
+  const int sshift = sbits > bbits ? sbits - bbits : 0;
+  const uint32_t nbins = (uint32_t)(((span - 1) >> sshift) + 1);
+  for (uint32_t q = tid; q <= nbins; q += kRT) bins[q] = 0u;
+  if (tid == 0) S.maxbin = 0;
+  __syncthreads();
+  uint32_t rk[kRI / 2] = {};  // rank of each write in its sub-bin (< 2^16), two per word
+#pragma unroll
+  for (int k = 0; k < kRI; ++k) {
+    const uint32_t i = tid + k * kRT;
+    if (i < n) rk[k >> 1] |= atomicAdd(&bins[R[i].x >> sshift], 1u) << (16 * (k & 1));
+  }
+  __syncthreads();
+  {
+    const uint32_t per = (nbins + kRT - 1) / kRT;
+    const uint32_t a = min(nbins, tid * per), e = min(nbins, a + per);
+    uint32_t local = 0, mx = 0;
+    for (uint32_t q = a; q < e; ++q) {
+      const uint32_t x = bins[q];
+      local += x;
+      mx = max(mx, x);
+    }
+    mx = __reduce_max_sync(kFull, mx);
+    if (lane == 0 && mx) atomicMax(&S.maxbin, mx);
+    uint32_t run = block_scan_excl<uint32_t>(local, &S.tot, S.buf);
+    for (uint32_t q = a; q < e; ++q) {
+      const uint32_t x = bins[q];
+      bins[q] = run;
+      run += x;
+    }
+    if (tid == 0) bins[nbins] = n;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < kRI; ++k) {
+    const uint32_t i = tid + k * kRT;
+    if (i < n) {
+      const uint32_t kv = R[i].x;
+      const uint32_t p = bins[kv >> sshift] + ((rk[k >> 1] >> (16 * (k & 1))) & 0xffffu);
+      skey[p] = kv;
+      perm[p] = (uint16_t)i;
+    }
+  }
+  __syncthreads();
+  // ---- order the keys inside the sub-bins (each holds one key when sshift == 0)
+  if (sshift > 0 && n > 1) {
+    if (S.maxbin <= kRSmallSort) {
+      const uint32_t qa = (uint32_t)(((uint64_t)tid * nbins) / kRT), qb = (uint32_t)(((uint64_t)(tid + 1) * nbins) / kRT);
+      for (uint32_t q = qa; q < qb; ++q) {
+        const uint32_t a = bins[q], e = bins[q + 1];
+        for (uint32_t x = a + 1; x < e; ++x) {
+          const uint32_t kv = skey[x];
+          const uint16_t pv = perm[x];
+          uint32_t y = x;
+          while (y > a && skey[y - 1] > kv) {
+            skey[y] = skey[y - 1];
+            perm[y] = perm[y - 1];
+            --y;
+          }
+          skey[y] = kv;
+          perm[y] = pv;
+        }
+      }
+    } else {
+      // a large sub-bin: bitonic sort of the whole set by (key, index)
+      uint32_t N = 2;
+      while (N < n) N <<= 1;
+      for (uint32_t q = n + tid; q < N; q += kRT) {
+        skey[q] = 0xffffffffu;
+        perm[q] = 0xffffu;
+      }
+      __syncthreads();
+      for (uint32_t k = 2; k <= N; k <<= 1) {
+        for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+          for (uint32_t i = tid; i < N / 2; i += kRT) {
+            const uint32_t lo = 2 * j * (i / j) + (i % j), hi = lo + j;
+            const bool asc = (lo & k) == 0;
+            const uint64_t x = ((uint64_t)skey[lo] << 16) | perm[lo], y = ((uint64_t)skey[hi] << 16) | perm[hi];
+            if ((x > y) == asc) {
+              skey[lo] = (uint32_t)(y >> 16);
+              perm[lo] = (uint16_t)y;
+              skey[hi] = (uint32_t)(x >> 16);
+              perm[hi] = (uint16_t)x;
+            }
+          }
+          __syncthreads();
+        }
+      }
+    }
+    __syncthreads();
+  }
+
+  // ---- one range of sorted positions per warp, cut at run heads
+  auto run_head_at = [&](uint32_t p) -> uint32_t {  // first run head at or after p
+    if (p == 0 || p >= n) return p >= n ? n : 0u;
+    const uint32_t k = skey[p - 1];
+    if (skey[p] != k) return p;
+    uint32_t lo = p + 1, hi = n;  // first position holding a larger key
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (skey[mid] > k) hi = mid;
+      else lo = mid + 1;
+    }
+    return lo;
+  };
+  const uint32_t A = run_head_at((uint32_t)(((uint64_t)wid * n) / kRW));
+  const uint32_t E = wid == kRW - 1 ? n : run_head_at((uint32_t)(((uint64_t)(wid + 1) * n) / kRW));
+  // this lane's positions [a, e)
+  const uint32_t len = E > A ? E - A : 0u;
+  const uint32_t qn = (len + 31) >> 5;
+  const uint32_t a = min(E, A + lane * qn), e = min(E, a + qn);
+  const bool have = a < e;
+  const bool head_a = have && (a == A || skey[a - 1] != skey[a]);
+  const bool tail_e = have && (e == E || skey[e] != skey[e - 1]);
+  const bool cont_in = have && !head_a;   // the first run continues from the lane before
+  uint32_t ft = ~0u;                      // first tail among the positions
+  uint32_t nk = 0;                        // stored elements whose run ends here
+  // The value of a run ending at position p goes to the value field of the
+  // record perm[p]; kKept marks perm[p] when the element is stored.
+
+  if (SUM) {
+    // pass 1: largest exponent of each run piece, at its last position
+    int run = 0, vf = 0;
+    bool anyhead = false;
+    if (have) {
+      uint32_t kc = skey[a];
+      bool h = head_a;
+      for (uint32_t p = a; p < e; ++p) {
+        const uint32_t kn = p + 1 < e ? skey[p + 1] : 0u;
+        const bool t = p + 1 == e ? tail_e : kn != kc;
+        const int ex = align_exp<F64>(RV[2 * perm[p] + 1]);
+        run = h ? ex : max(run, ex);
+        if (ft == ~0u) vf = max(vf, ex);
+        anyhead = anyhead || h;
+        if (t) {
+          rmax[p] = (uint16_t)run;
+          if (ft == ~0u) ft = p;
+        }
+        h = t;
+        kc = kn;
+      }
+    }
+    const int inF = warp_seg_scan<true>(!have || anyhead, EV{run}, EV{0}, OpMax()).e;
+    const int inB = warp_seg_scan<false>(!have || ft != ~0u, EV{vf}, EV{0}, OpMax()).e;
+    // pass 2 (backward): exact sums with each run's own binary point
+    Acc acc = acc_zero(), afirst = acc_zero(), alast = acc_zero();
+    int G = 1, Gfirst = 1;
+    uint32_t pt = 0;  // last position of the piece being summed
+    if (have) {
+      uint32_t kn = 0;
+      for (uint32_t p = e; p-- > a;) {
+        const uint32_t kc = skey[p];
+        const bool t = p + 1 == e ? tail_e : kn != kc;
+        const bool h = p == a ? head_a : skey[p - 1] != kc;
+        const uint32_t ix = perm[p];
+        const uint64_t raw = RV[2 * ix + 1];
+        kn = kc;
+        if (p + 1 == e || t) {  // a piece ends at p
+          pt = p;
+          int pm = t ? (int)rmax[p] : max(run, inB);  // (run: pass 1's largest of the last piece)
+          if (cont_in && (t ? p == ft : ft == ~0u)) pm = max(pm, inF);
+          G = max(pm, 1);
+          acc = acc_zero();
+        }
+        if (h && t) {  // a single write: its own value (already in place)
+          if (bits_nonzero<F64>(raw)) {
+            perm[p] = (uint16_t)(ix | kKept);
+            ++nk;
+          }
+          continue;
+        }
+        acc_add_bits(acc, wide<F64>(raw), G);
+        if (h || p == a) {  // the piece's first position
+          const bool has_tail = pt + 1 != e || tail_e;
+          if (!has_tail) {
+            alast = acc;  // continues in the next lane
+          } else if (!h) {
+            afirst = acc;  // continued from the lane before: finished after the scan
+            Gfirst = G;
+          } else {
+            bool nz;
+            const uint32_t it = perm[pt];
+            RVw[2 * it + 1] = acc_round(acc, G, !F64, &nz);
+            if (nz) {
+              perm[pt] = (uint16_t)(it | kKept);
+              ++nk;
+            }
+          }
+        }
+      }
+    }
+    const AV inA = warp_seg_scan<true>(!have || anyhead, av_of(alast), AV{0, 0, 0}, OpAdd());
+    if (cont_in && ft != ~0u) {
+      bool nz;
+      const uint32_t it = perm[ft];
+      RVw[2 * it + 1] = acc_round(acc_of(av_add(inA, av_of(afirst))), Gfirst, !F64, &nz);
+      if (nz) {
+        perm[ft] = (uint16_t)(it | kKept);
+        ++nk;
+      }
+    }
+  } else {
+    // last write: the largest (seq, position) of each run
+    WV w{0, 0, 0, 0}, wfirst{0, 0, 0, 0};
+    bool anyhead = false;
+    if (have) {
+      uint32_t kc = skey[a];
+      bool h = head_a;
+      for (uint32_t p = a; p < e; ++p) {
+        const uint32_t kn = p + 1 < e ? skey[p + 1] : 0u;
+        const bool t = p + 1 == e ? tail_e : kn != kc;
+        const uint32_t ix = perm[p];
+        const uint4 r = R[ix];
+        const uint64_t sq = SEQ ? __ldg(c.seq + r.y) : 0ull;
+        if (h) w.ok = 0;
+        const WV cand{sq, ((uint64_t)r.w << 32) | r.z, r.y, 1};
+        if (wv_better(w, cand)) w = cand;
+        anyhead = anyhead || h;
+        if (t) {
+          if (ft == ~0u && cont_in) {
+            wfirst = w;
+          } else {
+            RVw[2 * ix + 1] = w.val;
+            if (MAP) R[ix].x = w.pos;  // (the key field is free after the sort)
+            if (keep_zeros || bits_nonzero<F64>(w.val)) {
+              perm[p] = (uint16_t)(ix | kKept);
+              ++nk;
+            }
+          }
+          if (ft == ~0u) ft = p;
+        }
+        h = t;
+        kc = kn;
+      }
+    }
+    const WV inW = warp_seg_scan<true>(!have || anyhead, w, WV{0, 0, 0, 0}, OpWin());
+    if (cont_in && ft != ~0u) {
+      const WV r = wv_better(inW, wfirst) ? wfirst : inW;
+      const uint32_t it = perm[ft];
+      RVw[2 * it + 1] = r.val;
+      if (MAP) R[it].x = r.pos;
+      if (keep_zeros || bits_nonzero<F64>(r.val)) {
+        perm[ft] = (uint16_t)(it | kKept);
+        ++nk;
+      }
+    }
+  }
+
+  // ---- number the stored elements: lanes, then warps (in key order)
+  uint32_t inc = nk;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(kFull, inc, o);
+    if (lane >= o) inc += y;
+  }
+  if (lane == 31) S.wk[wid] = inc;
+  __syncthreads();
+  uint32_t woff = 0, nnz = 0;
+#pragma unroll
+  for (int w2 = 0; w2 < kRW; ++w2) {
+    const uint32_t x = S.wk[w2];
+    woff += w2 < wid ? x : 0u;
+    nnz += x;
+  }
+  const uint32_t li0 = woff + inc - nk;
+  if (mode == kCount) {
+    __syncthreads();
+    return nnz;
+  }
+  if (mode == kDefer) {
+    uint4* const dst = reinterpret_cast<uint4*>(c.rec + D.start);
+    uint32_t li = li0;
+    for (uint32_t p = a; p < e; ++p) {
+      const uint32_t ix = perm[p];
+      if (ix & kKept) {
+        const uint64_t v = RV[2 * (ix & 0x7fffu) + 1];
+        dst[li++] = make_uint4(skey[p], 0u, (uint32_t)v, (uint32_t)(v >> 32));
+      }
+    }
+    __syncthreads();
+    return nnz;
+  }
+  // ---- kNow: output index, the map, staging, placement
+  OV inO{INT_MIN, 0};
+  if (MAP) {
+    // output index (local) and winner of the first run ending in this lane,
+    // for the positions of a run that ends in a later lane
+    OV mine{INT_MIN, 0};
+    if (ft != ~0u) {
+      const uint32_t it = perm[ft];
+      mine.out = (it & kKept) ? (int32_t)li0 : -2;
+      mine.win = SUM ? 0u : R[it & 0x7fffu].x;
+    }
+    inO = warp_seg_scan<false>(!have || ft != ~0u, mine, OV{INT_MIN, 0}, OpNear());
+  }
+  if (tid < 32) {
+    const int64_t b = get_base(nnz);
+    if (tid == 0) S.base = b;
+  }
+  __syncthreads();
+  if (S.abort) return 0;
+  const int64_t base = S.base;
+  if (MAP) {
+    // every write of a stored run maps to its element; overwritten writes to -1
+    int32_t cur_out = inO.out == INT_MIN ? -2 : (inO.out >= 0 ? (int32_t)(base + inO.out) : inO.out);
+    uint32_t cur_win = inO.win;
+    uint32_t li = li0 + nk;
+    for (uint32_t p = e; p-- > a;) {
+      const uint32_t ix = perm[p];
+      const bool t = p + 1 == e ? tail_e : skey[p + 1] != skey[p];
+      const uint4 r = R[ix & 0x7fffu];
+      if (t) {
+        if (ix & kKept) {
+          --li;
+          cur_out = (int32_t)(base + li);
+        } else {
+          cur_out = -2;
+        }
+        cur_win = SUM ? 0u : r.x;
+      }
+      c.map[r.y] = (!SUM && r.y != cur_win) ? -1 : cur_out;
+    }
+  }
+  uint32_t* const sk = reinterpret_cast<uint32_t*>(smem + L.stage_key);
+  uint64_t* const sv = reinterpret_cast<uint64_t*>(smem + L.stage_val);
+  {
+    uint32_t li = li0;
+    for (uint32_t p = a; p < e; ++p) {
+      const uint32_t ix = perm[p];
+      if (ix & kKept) {
+        sk[li] = skey[p];
+        sv[li] = RV[2 * (ix & 0x7fffu) + 1];
+        ++li;
+      }
+    }
+  }
+  __syncthreads();
+  emit_range<F64>(c, D, Rg, nnz, base, [&](uint32_t i, uint32_t& k, uint64_t& v) {
+    k = sk[i];
+    v = sv[i];
+  });
+  __syncthreads();
+  return nnz;
+}
+
+// ---------------------------------------------------------------------------
+// One key with more writes than a window holds (streaming, records in global
+// memory).  Returns 1 if its element is stored.  Ends with a barrier.
+// ---------------------------------------------------------------------------
+template <bool F64, bool SUM, bool SEQ, bool MAP>
+__device__ __noinline__ uint32_t resolve_key(const Ctx& c, RShared& S, unsigned char* smem, const Desc& D,
+                                             const uint4* recs, uint32_t lkey, uint64_t kabs, bool emit,
+                                             int64_t base) {
+  constexpr RLay L = rlay();
+  const int tid = threadIdx.x, lane = tid & 31;
+  const uint32_t n = D.n;
+  if (tid == 0) S.kmax = 0;
+  __syncthreads();
+  if (SUM) {
+    int e = 0;
+    for (uint32_t k = tid; k < n; k += kRT) {
+      const uint4 r = __ldcg(recs + k);
+      if (r.x == lkey) e = max(e, align_exp<F64>(((uint64_t)r.w << 32) | r.z));
+    }
+    e = __reduce_max_sync(kFull, e);
+    if (lane == 0) atomicMax(&S.kmax, e);
+    __syncthreads();
+    const int G = max(S.kmax, 1);
+    Acc a = acc_zero();
+    for (uint32_t k = tid; k < n; k += kRT) {
+      const uint4 r = __ldcg(recs + k);
+      if (r.x == lkey) acc_add_bits(a, wide<F64>(((uint64_t)r.w << 32) | r.z), G);
+    }
+    AV v = av_of(a);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+      v = av_add(v, AV{__shfl_xor_sync(kFull, v.lo, o), __shfl_xor_sync(kFull, v.hi, o), __shfl_xor_sync(kFull, v.f, o)});
+    AV* parts = reinterpret_cast<AV*>(S.parts);
+    if (lane == 0) parts[tid >> 5] = v;
+    __syncthreads();
+    if (tid == 0) {
+      AV t{0, 0, 0};
+      for (int w = 0; w < kRW; ++w) t = av_add(t, parts[w]);
+      bool nz;
+      S.kbits = acc_round(acc_of(t), G, !F64, &nz);
+      S.kkeep = nz ? 1u : 0u;
+      S.kwin = 0;
+    }
+  } else {
+    WV w{0, 0, 0, 0};
+    for (uint32_t k = tid; k < n; k += kRT) {
+      const uint4 r = __ldcg(recs + k);
+      if (r.x != lkey) continue;
+      const WV cand{SEQ ? __ldg(c.seq + r.y) : 0ull, ((uint64_t)r.w << 32) | r.z, r.y, 1};
+      if (wv_better(w, cand)) w = cand;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const WV x{__shfl_xor_sync(kFull, w.seq, o), __shfl_xor_sync(kFull, w.val, o), __shfl_xor_sync(kFull, w.pos, o),
+                 __shfl_xor_sync(kFull, w.ok, o)};
+      if (wv_better(w, x)) w = x;
+    }
+    WV* parts = reinterpret_cast<WV*>(S.parts);
+    if (lane == 0) parts[tid >> 5] = w;
+    __syncthreads();
+    if (tid == 0) {
+      WV t{0, 0, 0, 0};
+      for (int q = 0; q < kRW; ++q)
+        if (wv_better(t, parts[q])) t = parts[q];
+      S.kbits = t.val;
+      S.kkeep = (c.keep_zeros || bits_nonzero<F64>(t.val)) ? 1u : 0u;
+      S.kwin = t.pos;
+    }
+  }
+  __syncthreads();
+  const uint32_t keep = S.kkeep;
+  if (emit) {
+    uint32_t* sk = reinterpret_cast<uint32_t*>(smem + L.stage_key);
+    uint64_t* sv = reinterpret_cast<uint64_t*>(smem + L.stage_val);
+    if (tid == 0) {
+      sk[0] = 0u;
+      sv[0] = S.kbits;
+      S.win = make_range((uint64_t)D.n_rows, kabs, 1);
+    }
+    __syncthreads();
+    emit_range<F64>(c, D, S.win, keep, base, [&](uint32_t i, uint32_t& k, uint64_t& v) {
+      k = sk[i];
+      v = sv[i];
+    });
+    if (MAP) {
+      const uint32_t wp = S.kwin;
+      for (uint32_t k = tid; k < n; k += kRT) {
+        const uint4 r = __ldcg(recs + k);
+        if (r.x == lkey) c.map[r.y] = (!SUM && r.y != wp) ? -1 : (keep ? (int32_t)base : -2);
+      }
+    }
+  }
+  __syncthreads();
+  return keep;
+}
+
+// ---------------------------------------------------------------------------
+// A bucket with more writes than fit: windows of its key range, each gathered
+// into shared memory (at most kRCapNow writes, so that its elements can be
+// staged and placed at once).
+// ---------------------------------------------------------------------------
+template <bool F64, bool SUM, bool SEQ, bool MAP>
+__device__ __noinline__ uint32_t resolve_windows(const Ctx& c, RShared& S, unsigned char* smem, const Desc& D,
+                                                 bool emit, int64_t base) {
+  constexpr RLay L = rlay();
+  uint4* const R = reinterpret_cast<uint4*>(smem + L.R);
+  uint32_t* const bins = reinterpret_cast<uint32_t*>(smem + L.bins);
+  const uint4* recs = reinterpret_cast<const uint4*>(c.rec + D.start);
+  const int tid = threadIdx.x;
+  const uint32_t n = D.n;
+  const uint64_t span = D.rg.span;
+  uint32_t running = 0;
+  uint64_t wlo = 0;
+  while (wlo < span) {
+    int hs = (span - wlo <= 1) ? 0 : max(0, ceil_log2_u64(span - wlo) - c.sub_bits);
+    uint64_t wend = span, whi = wlo + 1;
+    int mode = 0;  // 1 = window, 2 = single key
+    while (true) {
+      const uint32_t nb = (uint32_t)(((wend - wlo - 1) >> hs) + 1);
+      for (uint32_t q = tid; q < nb; q += kRT) bins[q] = 0u;
+      __syncthreads();
+      for (uint32_t k = tid; k < n; k += kRT) {
+        const uint64_t l = __ldcg(&recs[k].x);
+        if (l >= wlo && l < wend) atomicAdd(&bins[(uint32_t)((l - wlo) >> hs)], 1u);
+      }
+      __syncthreads();
+      if (tid == 0) {
+        uint32_t cum = 0, taken = 0;
+        while (taken < nb && cum + bins[taken] <= (uint32_t)kRCapNow) cum += bins[taken++];
+        S.taken = taken;
+      }
+      __syncthreads();
+      const uint32_t taken = S.taken;
+      __syncthreads();
+      if (taken > 0) {
+        whi = min(wlo + ((uint64_t)taken << hs), wend);
+        mode = 1;
+        break;
+      }
+      if (hs == 0) {
+        mode = 2;
+        break;
+      }
+      wend = wlo + (uint64_t{1} << hs);
+      hs = max(0, hs - c.sub_bits);
+    }
+    if (mode == 1) {
+      if (tid == 0) {
+        S.nw = 0;
+        S.win = make_range((uint64_t)D.n_rows, D.rg.klo + wlo, whi - wlo);
+      }
+      __syncthreads();
+      for (uint32_t k = tid; k < n; k += kRT) {
+        const uint4 r = __ldcg(recs + k);
+        if (r.x >= wlo && r.x < whi) R[atomicAdd(&S.nw, 1u)] = make_uint4(r.x - (uint32_t)wlo, r.y, r.z, r.w);
+      }
+      __syncthreads();
+      const uint32_t nw = S.nw;
+      const int64_t b0 = base + running;
+      running += resolve_tile<F64, SUM, SEQ, MAP>(c, S, smem, nw, D, S.win, emit ? kNow : kCount,
+                                                  [&](uint32_t) { return b0; });
+      wlo = whi;
+    } else {
+      running += resolve_key<F64, SUM, SEQ, MAP>(c, S, smem, D, recs, (uint32_t)wlo, D.rg.klo + wlo, emit,
+                                                 base + running);
+      wlo += 1;
+    }
+  }
+  return running;
+}
+
+// ---------------------------------------------------------------------------
+// The persistent kernel
+// ---------------------------------------------------------------------------
+// Thread kHelper takes the tickets and reads the next bucket's descriptor
+// while the block waits for the current bucket's bulk copy.
+constexpr int kHelper = kRT - 1;
+
+// Start the bulk copy of bucket D into the record area (thread 0; the
+// previous contents are dead) and warm L2 with the bucket one round ahead.
+__device__ __forceinline__ void start_bucket(const Ctx& c, RShared& S, unsigned char* smem, const Desc& D,
+                                             uint32_t cap, uint32_t NB) {
+  if (D.n > 0 && D.n <= cap) {
+    fence_proxy_async();
+    mbar_expect_tx(&S.bar, D.n * 16u);
+    bulk_load(smem + rlay().R, c.rec + D.start, D.n * 16u, &S.bar);
+  }
+  const uint32_t ahead = D.b + gridDim.x;
+  if (ahead < NB) {
+    const uint32_t na = c.bk_count[ahead];
+    if (na <= cap) prefetch_l2(c.rec + c.bk_start[ahead], na * 16u);
+  }
+}
+
+__device__ __forceinline__ void discard_records(const Ctx& c, int64_t start, uint32_t n) {
+  // drop the L2 lines that hold only these records (dead now), so that they
+  // are never written back to HBM
+  const uint64_t a0 = reinterpret_cast<uint64_t>(c.rec + start);
+  const uint64_t a1 = reinterpret_cast<uint64_t>(c.rec + start + n);
+  const uint64_t l0 = (a0 + 127) & ~127ull, l1 = a1 & ~127ull;
+  for (uint64_t a = l0 + (uint64_t)threadIdx.x * 128; a < l1; a += (uint64_t)kRT * 128)
+    asm volatile("discard.global.L2 [%0], 128;" ::"l"(a) : "memory");
+}
+
+template <bool F64, bool SUM, bool SEQ, bool MAP>
+__global__ void __launch_bounds__(kRT, 2) k_resolve(Ctx c) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ RShared S;
+  __shared__ Desc nxt;
+  const int tid = threadIdx.x;
+  const uint32_t NB = c.scal->NB;
+  const uint32_t cap = MAP ? (uint32_t)kRCapNow : (uint32_t)kRCap;  // writes resolved from shared memory
+  uint32_t next = ~0u;  // (thread kHelper) the ticket after the current bucket's
+  if (tid == 0) {
+    mbar_init(&S.bar, 1);
+    fence_mbar_init();
+    S.abort = 0;
+    S.pend.valid = 0;
+    const uint32_t t = is_aborted(c) ? ~0u : atomicAdd(&c.scal->ticket, 1u);
+    S.cur.valid = 0;
+    S.cur.b = t;
+    if (t < NB) {
+      S.cur = load_desc(c, t);
+      start_bucket(c, S, smem, S.cur, cap, NB);
+    }
+  }
+  __syncthreads();
+  if (tid == kHelper && S.cur.valid) next = is_aborted(c) ? ~0u : atomicAdd(&c.scal->ticket, 1u);
+  uint32_t phase = 0;
+  int64_t dstart = 0;  // records to drop from L2 at the end of the iteration
+  uint32_t dn = 0;
+  bool copying = false;  // a bulk copy has been started and not yet waited for
+  while (true) {
+    copying = S.cur.valid && S.cur.n > 0 && S.cur.n <= cap;
+    // ---- place the elements of the bucket resolved last (over its records)
+    if (S.pend.valid) {
+      const Desc& P = S.pend;
+      if (tid < 32) {
+        int64_t ex = 0;
+        if (P.rg.klo != 0 && (int64_t)P.b != c.withhold) {
+          ex = lookback_wait_warp(c, P.b);
+          if (tid == 0) st_release_u64(&c.bk_state[P.b], kStIncl | (uint64_t)(ex + P.nnz));
+        }
+        if (tid == 0) {
+          S.pbase = ex;
+          if (is_aborted(c)) S.abort = 1;
+        }
+      }
+      __syncthreads();
+      if (S.abort) break;
+      const int64_t pbase = S.pbase;
+      const uint4* src = reinterpret_cast<const uint4*>(c.rec + P.start);
+      emit_range<F64>(c, P, P.rg, P.nnz, pbase, [&](uint32_t i, uint32_t& k, uint64_t& v) {
+        const uint4 r = __ldcg(src + i);
+        k = r.x;
+        v = ((uint64_t)r.w << 32) | r.z;
+      });
+      if (tid == 0 && P.rg.klo + P.rg.span == P.K) {
+        c.col_ptr[P.col_base + P.n_cols] = pbase + P.nnz;
+        c.d_nnz[P.mi] = pbase + P.nnz;
+      }
+      dstart = P.start;
+      dn = P.n;
+    }
+    if (!S.cur.valid) break;
+    const Desc& D = S.cur;
+    // the next bucket's descriptor, read while this one's copy is in flight
+    if (tid == kHelper) {
+      nxt.valid = 0;
+      nxt.b = ~0u;
+      if (next < NB) {
+        nxt = load_desc(c, next);
+        next = is_aborted(c) ? ~0u : atomicAdd(&c.scal->ticket, 1u);
+      }
+    }
+    int64_t total = -1;  // set when the bucket is placed now
+    bool deferred = false;
+    uint32_t dnnz = 0;
+    if (D.K == 0) {  // an empty matrix: all offsets are 0
+      for (int64_t j = tid; j <= D.n_cols; j += kRT) c.col_ptr[D.col_base + j] = 0;
+      if (tid == 0) {
+        c.d_nnz[D.mi] = 0;
+        st_release_u64(&c.bk_state[D.b], kStIncl);
+      }
+    } else if (D.n > cap) {
+      // more writes than fit: windows of the key range, resolved twice
+      const uint32_t cnt = resolve_windows<F64, SUM, SEQ, MAP>(c, S, smem, D, false, 0);
+      if (tid < 32) {
+        int64_t ex = 0;
+        if (D.rg.klo == 0) {
+          if (tid == 0) st_release_u64(&c.bk_state[D.b], kStIncl | (uint64_t)cnt);
+        } else if ((int64_t)D.b != c.withhold) {
+          ex = lookback_warp(c, D.b, cnt);
+        }
+        if (tid == 0) {
+          S.base = ex;
+          S.abort = is_aborted(c) ? 1u : 0u;
+        }
+      }
+      __syncthreads();
+      if (S.abort) break;
+      const int64_t base = S.base;
+      __syncthreads();
+      resolve_windows<F64, SUM, SEQ, MAP>(c, S, smem, D, true, base);
+      total = base + cnt;
+    } else {
+      bool ok = true;
+      if (D.n > 0) {
+        ok = mbar_wait_bounded(&S.bar, phase);
+        phase ^= 1u;
+        copying = false;
+      }
+      if (__syncthreads_or(!ok)) {
+        // the copy is still in flight: record the error, give it one more
+        // bounded wait, and leave
+        if (tid == 0) record_fatal(c, SPM_ERR_TIMEOUT);
+        if (!ok) mbar_wait_bounded(&S.bar, phase ^ 1u);
+        __syncthreads();
+        break;
+      }
+      if (MAP) {
+        const uint32_t b = D.b;
+        const bool first = D.rg.klo == 0;
+        const uint32_t nnz = resolve_tile<F64, SUM, SEQ, MAP>(c, S, smem, D.n, D, D.rg, kNow, [&](uint32_t cnt) {
+          int64_t ex = 0;
+          if (first) {
+            if ((threadIdx.x & 31) == 0) st_release_u64(&c.bk_state[b], kStIncl | (uint64_t)cnt);
+          } else if ((int64_t)b != c.withhold) {
+            ex = lookback_warp(c, b, cnt);  // fault injection: a withheld bucket publishes nothing
+          }
+          if (threadIdx.x == 0 && is_aborted(c)) S.abort = 1;
+          return ex;
+        });
+        if (S.abort) break;
+        total = S.base + nnz;
+      } else {
+        const uint32_t nnz = resolve_tile<F64, SUM, SEQ, MAP>(c, S, smem, D.n, D, D.rg, kDefer, [](uint32_t) {
+          return int64_t{0};
+        });
+        if (tid == 0) {
+          if (D.rg.klo == 0) st_release_u64(&c.bk_state[D.b], kStIncl | (uint64_t)nnz);
+          else if ((int64_t)D.b != c.withhold) st_release_u64(&c.bk_state[D.b], kStAgg | (uint64_t)nnz);
+        }
+        deferred = true;
+        dnnz = nnz;
+      }
+    }
+    if (total >= 0 && tid == 0 && D.rg.klo + D.rg.span == D.K) {
+      c.col_ptr[D.col_base + D.n_cols] = total;
+      c.d_nnz[D.mi] = total;
+    }
+    const int64_t cstart = D.start;
+    const uint32_t cn = D.n;
+    fence_proxy_async();  // this thread's writes to the record area come before the next bulk copy
+    __syncthreads();      // the record area, the descriptors and the staging area are free
+    if (tid == 0) {
+      S.pend = S.cur;
+      S.pend.valid = deferred ? 1u : 0u;
+      S.pend.nnz = dnnz;
+      S.cur = nxt;
+      if (S.cur.valid) start_bucket(c, S, smem, S.cur, cap, NB);
+    }
+    if (dn) discard_records(c, dstart, dn);  // the elements placed above
+    if (!deferred && cn) discard_records(c, cstart, cn);
+    dn = 0;
+    __syncthreads();
+  }
+  if (copying) mbar_wait_bounded(&S.bar, phase);  // (a call that stopped early)
+  __syncthreads();  // every thread has read the elements placed last
+  if (dn) discard_records(c, dstart, dn);
+}
+
+template <typename K>
+int resident_blocks(K kernel, int sms, size_t smem) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kRT, smem) != cudaSuccess || per_sm < 1) {
+    cudaGetLastError();
+    per_sm = 1;
+  }
+  return sms * per_sm;
+}
+
+}  // namespace
+
+int resolve_capacity(bool map) { return map ? kRCapNow : kRCap; }
+
+// Every instantiation: value type x (add mode with or without the map; last
+// write with or without seq, with or without the map).
+#define SPM_RES_ALL(X) \
+  X(true, true, false, false) X(true, true, false, true) X(true, false, false, false) X(true, false, false, true) \
+  X(true, false, true, false) X(true, false, true, true) X(false, true, false, false) X(false, true, false, true) \
+  X(false, false, false, false) X(false, false, false, true) X(false, false, true, false) X(false, false, true, true)
+
+void resolve_set_attributes() {
+  const int bytes = (int)rlay().total;
+#define SPM_ATTR(F6, SU, SQ, MP) \
+  cudaFuncSetAttribute(k_resolve<F6, SU, SQ, MP>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  SPM_RES_ALL(SPM_ATTR)
+#undef SPM_ATTR
+}
+
+void launch_resolve(const Ctx& ctx, int sms, cudaStream_t st) {
+  const size_t bytes = rlay().total;
+  const bool f64 = ctx.f64 != 0, sum = ctx.sum_mode != 0, seq = ctx.has_seq != 0, map = ctx.keep_map != 0;
+#define SPM_RES(F6, SU, SQ, MP)                                                                              \
+  if (f64 == F6 && sum == SU && seq == SQ && map == MP) {                                                   \
+    k_resolve<F6, SU, SQ, MP><<<resident_blocks(k_resolve<F6, SU, SQ, MP>, sms, bytes), kRT, bytes, st>>>(ctx); \
+    return;                                                                                                 \
+  }
+  SPM_RES_ALL(SPM_RES)
+#undef SPM_RES
+}
+#undef SPM_RES_ALL
+
+}  // namespace spm
+

@@ -29,7 +29,6 @@ constexpr int kL2Bits = 8;                // a level-2 table refines one cell in
 constexpr int kL2Size = 1 << kL2Bits;
 constexpr int kMaxL2Tables = 32;          // level-2 tables per matrix
 constexpr int kMaxKeyBits = 52;           // n_rows * n_cols <= 2^52
-constexpr int kCapResolve = 28672;        // writes of one bucket sorted in shared memory (keys + order)
 constexpr int kSubBitsMax = 11;           // counting-sort digit inside a bucket: up to 2048 sub-bins
 constexpr int64_t kSampleTotal = 1 << 19; // samples drawn per call (spread over the matrices)
 constexpr int64_t kSampleMin = 256;       // at least this many per matrix (or all of its writes)
@@ -159,7 +158,7 @@ struct Layout {
   bool seq;
   // byte offsets
   size_t meta, scal, cta, samp, cellcnt, lut, l2cell, bk_lo, bk_info, bk_count, bk_start, bk_state,
-      scanpart, hist, rec, rs, tmp, rbk, bk_cur, bk_nnz, bk_out, seg_desc, l2h, total;
+      scanpart, hist, rec, tmp, rbk, bk_cur, l2h, total;
   int64_t l2h_len;  // one matrix with level-2 tables: sample counts of all level-2 cells
   bool two_pass;   // writes reach their buckets in two passes (through tmp/rbk)
 };
@@ -184,15 +183,6 @@ struct CtaInfo {
   int64_t l0, l1;     // LUT slice
   uint32_t cb0, cb1;  // bucket range
   int32_t i0, i1;     // matrix range
-};
-
-// Where one resolve warp left the stored elements of its range of a bucket
-// (in the scratch array) when the final placement is deferred: how many, and
-// the first key from which the offsets of starting columns are its job.
-struct SegDesc {
-  uint32_t count;
-  uint32_t pad;
-  uint64_t ks;
 };
 
 // Arguments of the assembly kernels.
@@ -223,32 +213,32 @@ struct Ctx {
   uint32_t* scanpart;
   uint32_t* hist;
   Rec* rec;
-  uint64_t* rs;
   Rec* tmp;           // two-pass partition: records grouped by bucket group
   uint32_t* l2h;      // one matrix: sample counts of every level-2 cell (null: the planner counts)
   uint32_t* rbk;      // two-pass partition: bucket of each tmp record
   uint32_t* bk_cur;   // two-pass partition: next free slot of each bucket in rec
-  uint32_t* bk_nnz;   // deferred placement: stored elements per bucket
-  uint32_t* bk_out;   // deferred placement: their exclusive prefix over all buckets
-  SegDesc* seg_desc;  // deferred placement: [bucket][resolve warp]
   // sizes
   int64_t B, m_total, S_total, lut_total, nbcap_total, hist_bound, C;
   int32_t sum_mode, f64, keep_map, has_seq;
   int64_t tgt;       // planner target (writes per bucket) for this call's mode
-  int32_t cap;       // writes a bucket may hold for the in-shared-memory path
   int32_t sub_bits;
   int64_t withhold;   // bucket whose look-back publication is withheld (tests), -1 = none
   int32_t two_pass;   // partition in two passes
   int32_t groups;     // two-pass partition: number of bucket groups aimed at (>= 1)
   int64_t min_fronts; // two-pass partition: used only above this many write fronts
-  int32_t deferred;   // resolve leaves placement to k_emit (calls without the map)
-  int32_t res_warps;  // warps per resolve block
   int32_t keep_zeros; // last-write mode: elements whose value is zero are stored too
 };
 
 // Flag bit of the library's own calls (never accepted from the C ABI):
 // last-write mode keeps elements whose final value is zero.
 constexpr uint32_t kFlagKeepZeros = 1u << 30;
+
+// The per-bucket resolve kernel (resolve.cu): writes a bucket may hold to be
+// resolved from shared memory (fewer when the map is kept), its shared-memory
+// attributes (set once per device) and its launch.
+int resolve_capacity(bool map);
+void resolve_set_attributes();
+void launch_resolve(const Ctx& ctx, int sms, cudaStream_t st);
 
 // Launch counter of the library's kernels (spm_debug_launch_count).
 void count_launches(int64_t n);

@@ -37,7 +37,7 @@ def test_small_search_on_the_gpu(tmp_path):
     t0 = spm.spm_get_tuning()
     d = workloads.zipf_batch(m=400_003, n=20_000, seed=workloads.SEED_BASE + 70)
     p = str(tmp_path / "tune.json")
-    cands = [dict(bucket_target=4096, resolve_threads=512), dict(bucket_target=8192, resolve_threads=1024)]
+    cands = [dict(bucket_target=2048, sub_bits=10), dict(bucket_target=3584, partition_threads=512)]
     best = at.autotune(to_dev(d["rows"]), to_dev(d["cols"]), to_dev(d["vals"]), d["shape"], "sum",
                        candidates=cands, reps=3, warmup=2, path=p, apply=False)
     assert best["tried"] == 2 and best["rejected"] == []

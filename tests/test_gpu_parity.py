@@ -311,17 +311,17 @@ def test_single_key_with_more_writes_than_fit():
 
 
 def test_bounded_wait_reports_timeout_and_recovers():
-    # with the map, each bucket's block places its own elements and waits
-    # (bounded) for the running count of the buckets before it; without the
-    # map no block waits for another (placement is a separate kernel)
+    # every bucket's output offset comes from a bounded wait for the counts
+    # of the buckets before it (placed at once with the map, one bucket later
+    # without it); a bucket that never publishes makes that wait expire
     import paper_1805_03380_gb300 as spm
     d = workloads.density_sweep(2e-3, n=10_000)  # uniform: every bucket takes the in-shared-memory path
     spm.spm_debug_withhold_publication(1)
     try:
-        with pytest.raises(spm.SpmError) as e:
-            gpu_assemble(d, "sum", keep_map=True)
-        assert e.value.code == 6
-        _check(d, "sum")  # nothing waits without the map
+        for keep_map in (True, False):
+            with pytest.raises(spm.SpmError) as e:
+                gpu_assemble(d, "sum", keep_map=keep_map)
+            assert e.value.code == 6
     finally:
         spm.spm_debug_withhold_publication(-1)
     got = gpu_assemble(d, "set", keep_map=True)
