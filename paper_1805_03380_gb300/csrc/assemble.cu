@@ -1266,7 +1266,7 @@ __global__ void __launch_bounds__(1024) k_part_b(Ctx c) {
 // ===========================================================================
 namespace {
 
-constexpr spm_tuning kDefaultTuning = {3072, 11, 1024, 512, 1 << 22, 1 << 19, 1};
+constexpr spm_tuning kDefaultTuning = {6144, 12, 1024, 512, 1 << 22, 1 << 19, 1};
 spm_tuning g_tuning = kDefaultTuning;
 int64_t g_withhold = -1;
 std::mutex g_mutex;
@@ -1487,6 +1487,9 @@ spm_status host_plan(int64_t B, const int64_t* h_nr, const int64_t* h_nc, const 
   // one matrix with level-2 tables: a sample count per level-2 cell
   L.l2h_len = (B == 1 && hp.single.H2 > 0) ? (int64_t{1} << (hp.single.L1 + kL2Bits)) : 0;
   L.l2h = L.l2h_len ? take(4 * (size_t)L.l2h_len) : o;
+  L.bk_nnz = take(4 * (size_t)std::max<int64_t>(nbcap, 1));
+  L.bk_out = take(4 * (size_t)std::max<int64_t>(nbcap, 1));
+  L.big_list = take(4 * (size_t)std::max<int64_t>(nbcap, 1));
   L.total = o;
   return SPM_OK;
 }
@@ -1610,6 +1613,9 @@ spm_status run_assembly(int64_t B, const int64_t* h_nr, const int64_t* h_nc, con
   ctx.rbk = L.two_pass ? reinterpret_cast<uint32_t*>(ws + L.rbk) : nullptr;
   ctx.l2h = L.l2h_len ? reinterpret_cast<uint32_t*>(ws + L.l2h) : nullptr;
   ctx.bk_cur = reinterpret_cast<uint32_t*>(ws + L.bk_cur);
+  ctx.bk_nnz = reinterpret_cast<uint32_t*>(ws + L.bk_nnz);
+  ctx.bk_out = reinterpret_cast<uint32_t*>(ws + L.bk_out);
+  ctx.big_list = reinterpret_cast<uint32_t*>(ws + L.big_list);
   ctx.groups = (int32_t)two_pass_groups(ds->sms, L.nbcap_total);
   ctx.min_fronts = tun.two_pass_min_fronts;
   ctx.B = L.B;
@@ -1670,9 +1676,17 @@ spm_status run_assembly(int64_t B, const int64_t* h_nr, const int64_t* h_nc, con
   else launch_partition<false>(ctx, L, vec, st, tun.partition_threads, ds->sms, call);
   launch_resolve(ctx, ds->sms, st);
   stage_mark(st, call, 5);
-  stage_mark(st, call, 6);  // (placement is part of the resolve kernel)
-  // setup, plan, 2 bucket kernels, 6 partition (with room for two passes: 8), resolve
-  g_launches += 11 + (L.S_total > 0 ? 1 : 0) + (L.two_pass ? 2 : 0);
+  if (!keep_map) {
+    // offsets of the buckets' elements, then their placement
+    k_scan_reduce<<<(unsigned)L.scan_blocks, kScanBlock, 0, st>>>(ctx, ctx.bk_nnz);
+    k_scan_top<<<1, 1024, 0, st>>>(ctx, L.scan_blocks);
+    k_scan_down<<<(unsigned)L.scan_blocks, kScanBlock, 0, st>>>(ctx, ctx.bk_nnz, ctx.bk_out);
+    launch_place(ctx, ds->sms, L.nbcap_total, st);
+  }
+  stage_mark(st, call, 6);
+  // setup, plan, 2 bucket kernels, 6 partition (with room for two passes: 8), resolve,
+  // and without the map 3 scan kernels and 2 placement kernels
+  g_launches += 11 + (L.S_total > 0 ? 1 : 0) + (L.two_pass ? 2 : 0) + (keep_map ? 0 : 5);
   if (cudaGetLastError() != cudaSuccess) return SPM_ERR_CUDA;
   return SPM_OK;
 }

@@ -44,6 +44,7 @@
 //
 // No kernel traps or waits without a bound: an expired wait is reported as
 // SPM_ERR_TIMEOUT in the device status word and the call stops.
+#include <algorithm>
 #include <climits>
 #include <cstdint>
 #include <type_traits>
@@ -54,9 +55,9 @@
 namespace spm {
 namespace {
 
-constexpr int kRT = 512;                    // threads per resolve block (two blocks per SM)
+constexpr int kRT = 512;                    // threads per resolve block (one block per SM)
 constexpr int kRW = kRT / 32;               // warps per block
-constexpr int kRI = 8;                      // sorted positions per thread at the capacity
+constexpr int kRI = 16;                     // sorted positions per thread at the capacity
 constexpr int kRCap = kRT * kRI;            // writes of one bucket resolved in shared memory
 constexpr int kRCapNow = kRCap / 2;         // ... when the elements are staged in shared memory
 constexpr int kRBins = 1 << kSubBitsMax;    // sub-bins of the counting sort, at most
@@ -242,11 +243,10 @@ __device__ __forceinline__ uint64_t col_of(const Range& R, uint64_t x, uint64_t 
 
 struct Desc {
   uint32_t b, n;      // bucket, its writes
-  uint32_t nnz;       // its stored elements (after the reduction)
   uint32_t valid;
   int64_t start;      // first record of the bucket
   int64_t mi;         // matrix
-  int64_t n_rows, n_cols, col_base, t0;
+  int64_t n_rows, n_cols, col_base, t0, bucket_off;
   uint64_t K;
   Range rg;           // the bucket's key range
 };
@@ -256,7 +256,6 @@ __device__ __forceinline__ Desc load_desc(const Ctx& c, uint32_t b) {
   Desc d;
   d.b = b;
   d.valid = 1;
-  d.nnz = 0;
   d.n = c.bk_count[b];
   d.start = c.bk_start[b];
   const uint32_t info = c.bk_info[b];
@@ -267,6 +266,7 @@ __device__ __forceinline__ Desc load_desc(const Ctx& c, uint32_t b) {
   d.n_cols = mm.n_cols;
   d.col_base = mm.col_base;
   d.t0 = mm.t0;
+  d.bucket_off = mm.bucket_off;
   d.K = mm.K;
   const uint64_t span = mm.K == 0 ? 0 : min(uint64_t{1} << (info & 63), mm.K - klo);
   d.rg = mm.K == 0 ? Range{0, 0, 0, 0, Div32{0, 0, 0}, 0} : make_range((uint64_t)mm.n_rows, klo, span);
@@ -274,9 +274,9 @@ __device__ __forceinline__ Desc load_desc(const Ctx& c, uint32_t b) {
 }
 
 struct RShared {
-  Desc cur, pend;     // the bucket being resolved; the bucket whose elements wait to be placed
+  Desc cur;           // the bucket being resolved
   Range win;          // window (or single key) being resolved at once
-  int64_t base, pbase;
+  int64_t base;
   uint32_t wk[32];    // per warp: stored elements
   uint32_t buf[32];
   uint32_t tot, maxbin, nw, taken, abort;
@@ -302,6 +302,65 @@ __device__ __forceinline__ bool bits_nonzero(uint64_t bits) {
 template <bool F64>
 __device__ __forceinline__ int align_exp(uint64_t raw) {
   return max(0, f64_align_exponent(wide<F64>(raw)));
+}
+
+// Where the elements of a bucket wait for k_place (calls without the map):
+// over the bucket's own records, keys (relative to the bucket) from the first
+// record, values from byte 4 * n (rounded up to 8) on.  Both fit: 12 bytes per
+// element in the 16 bytes of each record.
+__device__ __forceinline__ uint32_t* res_keys(const Ctx& c, int64_t start) {
+  return reinterpret_cast<uint32_t*>(c.rec + start);
+}
+__device__ __forceinline__ uint64_t* res_vals(const Ctx& c, int64_t start, uint32_t n) {
+  return reinterpret_cast<uint64_t*>(reinterpret_cast<char*>(c.rec + start) + (((size_t)4 * n + 7) & ~size_t{7}));
+}
+
+// acc_round for results in the normal range, faster: the top 63 bits of the
+// magnitude with a sticky bit below them (set when any lower bit is) round
+// exactly like the whole, so the hardware's integer to floating-point
+// conversion (round to nearest even) gives the correctly rounded significand,
+// and scaling by a power of two is exact for a normal result.  Specials and
+// results near the subnormal or overflow range take acc_round.
+template <bool F64>
+__device__ __forceinline__ uint64_t acc_round_fast(const Acc& a, int emax, bool* nonzero) {
+  if (a.flags) return acc_round(a, emax, !F64, nonzero);
+  uint64_t lo = a.lo, hi = (uint64_t)a.hi;
+  const bool neg = a.hi < 0;
+  if (neg) {  // two's complement negate
+    lo = ~lo + 1ull;
+    hi = ~hi + (lo == 0ull ? 1ull : 0ull);
+  }
+  if ((hi | lo) == 0ull) {
+    *nonzero = false;
+    return 0ull;
+  }
+  int u = (emax - kAlignBits) - 1075;  // value = magnitude * 2^u
+  uint64_t t;
+  if (hi == 0ull && (lo >> 63) == 0ull) {
+    t = lo;
+  } else {
+    const int msb = hi ? 127 - __clzll((long long)hi) : 63;
+    const int sh = msb - 62;  // 1..64: t = magnitude >> sh keeps 63 bits
+    bool sticky;
+    if (sh == 64) {
+      t = hi;
+      sticky = lo != 0ull;
+    } else {
+      t = (lo >> sh) | (hi << (64 - sh));
+      sticky = (lo & ((1ull << sh) - 1ull)) != 0ull;
+    }
+    t |= sticky ? 1ull : 0ull;
+    u += sh;
+  }
+  const int top = 63 - __clzll((long long)t) + u;  // exponent of the leading bit
+  if (F64 ? (top < -1021 || top > 1022) : (top < -125 || top > 126)) return acc_round(a, emax, !F64, nonzero);
+  *nonzero = true;
+  if (F64) {
+    double d = scalbn(__ll2double_rn((long long)t), u);
+    return (uint64_t)__double_as_longlong(neg ? -d : d);
+  }
+  float f = scalbnf(__ll2float_rn((long long)t), u);
+  return (uint64_t)__float_as_uint(neg ? -f : f);
 }
 
 // Write the nnz stored elements of the key range R (get(li) gives the key
@@ -367,13 +426,67 @@ __device__ void emit_range(const Ctx& c, const Desc& D, const Range& R, uint32_t
   for (uint64_t j = lastcol + 1 + tid; j < je; j += blockDim.x) colp[j] = base + nnz;
 }
 
+// Sort k <= 32 (key, index) pairs in shared memory by key with one warp: a
+// bitonic network over 32 slots, one per lane (empty slots hold the largest
+// value).  Called by all lanes of the warp.
+__device__ __forceinline__ void warp_sort32(uint32_t* keys, uint16_t* idx, uint32_t k) {
+  const int lane = threadIdx.x & 31;
+  uint64_t x = (uint32_t)lane < k ? (((uint64_t)keys[lane] << 16) | idx[lane]) : ~0ull;
+#pragma unroll
+  for (int kk = 2; kk <= 32; kk <<= 1) {
+#pragma unroll
+    for (int j = kk >> 1; j > 0; j >>= 1) {
+      const uint64_t y = __shfl_xor_sync(kFull, x, j);
+      x = (((lane & j) == 0) == ((lane & kk) == 0)) ? min(x, y) : max(x, y);
+    }
+  }
+  if ((uint32_t)lane < k) {
+    keys[lane] = (uint32_t)(x >> 16);
+    idx[lane] = (uint16_t)x;
+  }
+}
+
+// Sort k <= 64 (key, index) pairs in shared memory by key with one warp: a
+// bitonic network over 64 slots, two per lane (slots lane and lane + 32;
+// empty slots hold the largest value).  Called by all lanes of the warp.
+__device__ __forceinline__ void warp_sort64(uint32_t* keys, uint16_t* idx, uint32_t k) {
+  const int lane = threadIdx.x & 31;
+  uint64_t x0 = (uint32_t)lane < k ? (((uint64_t)keys[lane] << 16) | idx[lane]) : ~0ull;
+  uint64_t x1 = (uint32_t)lane + 32u < k ? (((uint64_t)keys[lane + 32] << 16) | idx[lane + 32]) : ~0ull;
+#pragma unroll
+  for (int kk = 2; kk <= 64; kk <<= 1) {
+#pragma unroll
+    for (int j = kk >> 1; j > 0; j >>= 1) {
+      if (j == 32) {  // the partner is the lane's other slot (kk == 64: ascending)
+        const uint64_t lo = min(x0, x1), hi = max(x0, x1);
+        x0 = lo;
+        x1 = hi;
+      } else {
+        const uint64_t y0 = __shfl_xor_sync(kFull, x0, j), y1 = __shfl_xor_sync(kFull, x1, j);
+        const bool lower = (lane & j) == 0;
+        const bool asc0 = (lane & kk) == 0, asc1 = ((lane + 32) & kk) == 0;
+        x0 = (lower == asc0) ? min(x0, y0) : max(x0, y0);
+        x1 = (lower == asc1) ? min(x1, y1) : max(x1, y1);
+      }
+    }
+  }
+  if ((uint32_t)lane < k) {
+    keys[lane] = (uint32_t)(x0 >> 16);
+    idx[lane] = (uint16_t)x0;
+  }
+  if ((uint32_t)lane + 32u < k) {
+    keys[lane + 32] = (uint32_t)(x1 >> 16);
+    idx[lane + 32] = (uint16_t)x1;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // One set of records in shared memory
 // ---------------------------------------------------------------------------
 // How the stored elements leave resolve_tile.
 enum : int {
   kCount = 0,  // only counted
-  kDefer = 1,  // written over the bucket's records, {key, -, value}, placed later
+  kDefer = 1,  // written over the bucket's records (res_keys, res_vals), placed by k_place
   kNow = 2     // placed at once (output index from get_base, called by warp 0)
 };
 
@@ -443,10 +556,13 @@ __device__ __noinline__ uint32_t resolve_tile(const Ctx& c, RShared& S, unsigned
   __syncthreads();
   // ---- order the keys inside the sub-bins (each holds one key when sshift == 0)
   if (sshift > 0 && n > 1) {
-    if (S.maxbin <= kRSmallSort) {
+    if (S.maxbin <= 64u) {
+      // sub-bins of 2..8 writes: insertion by one thread; of 9..64: one warp,
+      // a bitonic network over (key, index) in registers
       const uint32_t qa = (uint32_t)(((uint64_t)tid * nbins) / kRT), qb = (uint32_t)(((uint64_t)(tid + 1) * nbins) / kRT);
       for (uint32_t q = qa; q < qb; ++q) {
         const uint32_t a = bins[q], e = bins[q + 1];
+        if (e - a > 8u) continue;
         for (uint32_t x = a + 1; x < e; ++x) {
           const uint32_t kv = skey[x];
           const uint16_t pv = perm[x];
@@ -458,6 +574,18 @@ __device__ __noinline__ uint32_t resolve_tile(const Ctx& c, RShared& S, unsigned
           }
           skey[y] = kv;
           perm[y] = pv;
+        }
+      }
+      for (uint32_t q0 = (uint32_t)wid * 32u; q0 < nbins; q0 += (uint32_t)kRW * 32u) {
+        const uint32_t q = q0 + lane;
+        const bool heavy = q < nbins && bins[q + 1] - bins[q] > 8u;
+        unsigned hv = __ballot_sync(kFull, heavy);
+        while (hv) {
+          const int L = __ffs(hv) - 1;
+          hv &= hv - 1;
+          const uint32_t a = bins[q0 + L], k = bins[q0 + L + 1] - a;
+          if (k <= 32u) warp_sort32(skey + a, perm + a, k);
+          else warp_sort64(skey + a, perm + a, k);
         }
       }
     } else {
@@ -520,17 +648,18 @@ __device__ __noinline__ uint32_t resolve_tile(const Ctx& c, RShared& S, unsigned
   if (SUM) {
     // pass 1: largest exponent of each run piece, at its last position
     int run = 0, vf = 0;
-    bool anyhead = false;
+    bool anyhead = false, multi = false;
     if (have) {
       uint32_t kc = skey[a];
       bool h = head_a;
       for (uint32_t p = a; p < e; ++p) {
         const uint32_t kn = p + 1 < e ? skey[p + 1] : 0u;
         const bool t = p + 1 == e ? tail_e : kn != kc;
-        const int ex = align_exp<F64>(RV[2 * perm[p] + 1]);
+        const int ex = (h && t) ? 0 : align_exp<F64>(RV[2 * perm[p] + 1]);  // (a single write needs none)
         run = h ? ex : max(run, ex);
         if (ft == ~0u) vf = max(vf, ex);
         anyhead = anyhead || h;
+        multi = multi || !(h && t);
         if (t) {
           rmax[p] = (uint16_t)run;
           if (ft == ~0u) ft = p;
@@ -539,6 +668,18 @@ __device__ __noinline__ uint32_t resolve_tile(const Ctx& c, RShared& S, unsigned
         kc = kn;
       }
     }
+    if (!__any_sync(kFull, multi)) {
+      // every position of the warp is an element of its own: its value is the result
+      for (uint32_t p = a; p < e; ++p) {
+        const uint32_t ix = perm[p];
+        if (bits_nonzero<F64>(RV[2 * ix + 1])) {
+          perm[p] = (uint16_t)(ix | kKept);
+          ++nk;
+        }
+      }
+      goto numbered;
+    }
+    {
     const int inF = warp_seg_scan<true>(!have || anyhead, EV{run}, EV{0}, OpMax()).e;
     const int inB = warp_seg_scan<false>(!have || ft != ~0u, EV{vf}, EV{0}, OpMax()).e;
     // pass 2 (backward): exact sums with each run's own binary point
@@ -579,7 +720,7 @@ __device__ __noinline__ uint32_t resolve_tile(const Ctx& c, RShared& S, unsigned
           } else {
             bool nz;
             const uint32_t it = perm[pt];
-            RVw[2 * it + 1] = acc_round(acc, G, !F64, &nz);
+            RVw[2 * it + 1] = acc_round_fast<F64>(acc, G, &nz);
             if (nz) {
               perm[pt] = (uint16_t)(it | kKept);
               ++nk;
@@ -592,11 +733,12 @@ __device__ __noinline__ uint32_t resolve_tile(const Ctx& c, RShared& S, unsigned
     if (cont_in && ft != ~0u) {
       bool nz;
       const uint32_t it = perm[ft];
-      RVw[2 * it + 1] = acc_round(acc_of(av_add(inA, av_of(afirst))), Gfirst, !F64, &nz);
+      RVw[2 * it + 1] = acc_round_fast<F64>(acc_of(av_add(inA, av_of(afirst))), Gfirst, &nz);
       if (nz) {
         perm[ft] = (uint16_t)(it | kKept);
         ++nk;
       }
+    }
     }
   } else {
     // last write: the largest (seq, position) of each run
@@ -646,6 +788,7 @@ __device__ __noinline__ uint32_t resolve_tile(const Ctx& c, RShared& S, unsigned
   }
 
   // ---- number the stored elements: lanes, then warps (in key order)
+numbered:
   uint32_t inc = nk;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -667,13 +810,15 @@ __device__ __noinline__ uint32_t resolve_tile(const Ctx& c, RShared& S, unsigned
     return nnz;
   }
   if (mode == kDefer) {
-    uint4* const dst = reinterpret_cast<uint4*>(c.rec + D.start);
+    uint32_t* const dk = res_keys(c, D.start);
+    uint64_t* const dv = res_vals(c, D.start, D.n);
     uint32_t li = li0;
     for (uint32_t p = a; p < e; ++p) {
       const uint32_t ix = perm[p];
       if (ix & kKept) {
-        const uint64_t v = RV[2 * (ix & 0x7fffu) + 1];
-        dst[li++] = make_uint4(skey[p], 0u, (uint32_t)v, (uint32_t)(v >> 32));
+        dk[li] = skey[p];
+        dv[li] = RV[2 * (ix & 0x7fffu) + 1];
+        ++li;
       }
     }
     __syncthreads();
@@ -914,7 +1059,7 @@ __device__ __noinline__ uint32_t resolve_windows(const Ctx& c, RShared& S, unsig
 }
 
 // ---------------------------------------------------------------------------
-// The persistent kernel
+// The kernels
 // ---------------------------------------------------------------------------
 // Thread kHelper takes the tickets and reads the next bucket's descriptor
 // while the block waits for the current bucket's bulk copy.
@@ -936,18 +1081,23 @@ __device__ __forceinline__ void start_bucket(const Ctx& c, RShared& S, unsigned 
   }
 }
 
-__device__ __forceinline__ void discard_records(const Ctx& c, int64_t start, uint32_t n) {
-  // drop the L2 lines that hold only these records (dead now), so that they
-  // are never written back to HBM
-  const uint64_t a0 = reinterpret_cast<uint64_t>(c.rec + start);
-  const uint64_t a1 = reinterpret_cast<uint64_t>(c.rec + start + n);
+// Drop the L2 lines that lie entirely inside [a0, a1) (dead data), so that
+// they are never written back to HBM.
+__device__ __forceinline__ void discard_lines(const void* p0, const void* p1) {
+  const uint64_t a0 = reinterpret_cast<uint64_t>(p0), a1 = reinterpret_cast<uint64_t>(p1);
   const uint64_t l0 = (a0 + 127) & ~127ull, l1 = a1 & ~127ull;
-  for (uint64_t a = l0 + (uint64_t)threadIdx.x * 128; a < l1; a += (uint64_t)kRT * 128)
+  for (uint64_t a = l0 + (uint64_t)threadIdx.x * 128; a < l1; a += (uint64_t)blockDim.x * 128)
     asm volatile("discard.global.L2 [%0], 128;" ::"l"(a) : "memory");
 }
 
+// Output index of a bucket's first element (relative to its matrix), from the
+// scan of the per-bucket element counts.
+__device__ __forceinline__ int64_t bucket_base(const Ctx& c, const Desc& D) {
+  return (int64_t)c.bk_out[D.b] - (int64_t)c.bk_out[D.bucket_off];
+}
+
 template <bool F64, bool SUM, bool SEQ, bool MAP>
-__global__ void __launch_bounds__(kRT, 2) k_resolve(Ctx c) {
+__global__ void __launch_bounds__(kRT, 1) k_resolve(Ctx c) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ RShared S;
   __shared__ Desc nxt;
@@ -959,7 +1109,6 @@ __global__ void __launch_bounds__(kRT, 2) k_resolve(Ctx c) {
     mbar_init(&S.bar, 1);
     fence_mbar_init();
     S.abort = 0;
-    S.pend.valid = 0;
     const uint32_t t = is_aborted(c) ? ~0u : atomicAdd(&c.scal->ticket, 1u);
     S.cur.valid = 0;
     S.cur.b = t;
@@ -971,42 +1120,10 @@ __global__ void __launch_bounds__(kRT, 2) k_resolve(Ctx c) {
   __syncthreads();
   if (tid == kHelper && S.cur.valid) next = is_aborted(c) ? ~0u : atomicAdd(&c.scal->ticket, 1u);
   uint32_t phase = 0;
-  int64_t dstart = 0;  // records to drop from L2 at the end of the iteration
-  uint32_t dn = 0;
   bool copying = false;  // a bulk copy has been started and not yet waited for
   while (true) {
-    copying = S.cur.valid && S.cur.n > 0 && S.cur.n <= cap;
-    // ---- place the elements of the bucket resolved last (over its records)
-    if (S.pend.valid) {
-      const Desc& P = S.pend;
-      if (tid < 32) {
-        int64_t ex = 0;
-        if (P.rg.klo != 0 && (int64_t)P.b != c.withhold) {
-          ex = lookback_wait_warp(c, P.b);
-          if (tid == 0) st_release_u64(&c.bk_state[P.b], kStIncl | (uint64_t)(ex + P.nnz));
-        }
-        if (tid == 0) {
-          S.pbase = ex;
-          if (is_aborted(c)) S.abort = 1;
-        }
-      }
-      __syncthreads();
-      if (S.abort) break;
-      const int64_t pbase = S.pbase;
-      const uint4* src = reinterpret_cast<const uint4*>(c.rec + P.start);
-      emit_range<F64>(c, P, P.rg, P.nnz, pbase, [&](uint32_t i, uint32_t& k, uint64_t& v) {
-        const uint4 r = __ldcg(src + i);
-        k = r.x;
-        v = ((uint64_t)r.w << 32) | r.z;
-      });
-      if (tid == 0 && P.rg.klo + P.rg.span == P.K) {
-        c.col_ptr[P.col_base + P.n_cols] = pbase + P.nnz;
-        c.d_nnz[P.mi] = pbase + P.nnz;
-      }
-      dstart = P.start;
-      dn = P.n;
-    }
     if (!S.cur.valid) break;
+    copying = S.cur.n > 0 && S.cur.n <= cap;
     const Desc& D = S.cur;
     // the next bucket's descriptor, read while this one's copy is in flight
     if (tid == kHelper) {
@@ -1017,36 +1134,44 @@ __global__ void __launch_bounds__(kRT, 2) k_resolve(Ctx c) {
         next = is_aborted(c) ? ~0u : atomicAdd(&c.scal->ticket, 1u);
       }
     }
-    int64_t total = -1;  // set when the bucket is placed now
-    bool deferred = false;
-    uint32_t dnnz = 0;
+    int64_t total = -1;  // set when the bucket is placed here
+    const void* dead0 = c.rec + D.start;  // records (or parts) dead after this bucket
     if (D.K == 0) {  // an empty matrix: all offsets are 0
       for (int64_t j = tid; j <= D.n_cols; j += kRT) c.col_ptr[D.col_base + j] = 0;
       if (tid == 0) {
-        c.d_nnz[D.mi] = 0;
-        st_release_u64(&c.bk_state[D.b], kStIncl);
+        if (MAP) st_release_u64(&c.bk_state[D.b], kStIncl);
+        else c.bk_nnz[D.b] = 0u;
       }
+      total = 0;
     } else if (D.n > cap) {
-      // more writes than fit: windows of the key range, resolved twice
+      // more writes than fit: windows of the key range
       const uint32_t cnt = resolve_windows<F64, SUM, SEQ, MAP>(c, S, smem, D, false, 0);
-      if (tid < 32) {
-        int64_t ex = 0;
-        if (D.rg.klo == 0) {
-          if (tid == 0) st_release_u64(&c.bk_state[D.b], kStIncl | (uint64_t)cnt);
-        } else if ((int64_t)D.b != c.withhold) {
-          ex = lookback_warp(c, D.b, cnt);
+      if (MAP) {
+        // resolved twice: counted, then placed after the look-back
+        if (tid < 32) {
+          int64_t ex = 0;
+          if (D.rg.klo == 0) {
+            if (tid == 0) st_release_u64(&c.bk_state[D.b], kStIncl | (uint64_t)cnt);
+          } else if ((int64_t)D.b != c.withhold) {
+            ex = lookback_warp(c, D.b, cnt);
+          }
+          if (tid == 0) {
+            S.base = ex;
+            S.abort = is_aborted(c) ? 1u : 0u;
+          }
         }
-        if (tid == 0) {
-          S.base = ex;
-          S.abort = is_aborted(c) ? 1u : 0u;
-        }
+        __syncthreads();
+        if (S.abort) break;
+        const int64_t base = S.base;
+        __syncthreads();
+        resolve_windows<F64, SUM, SEQ, MAP>(c, S, smem, D, true, base);
+        total = base + cnt;
+      } else if (tid == 0) {
+        // placed by k_big once the offsets are known
+        c.bk_nnz[D.b] = cnt;
+        c.big_list[atomicAdd(&c.scal->big_n, 1u)] = D.b;
       }
-      __syncthreads();
-      if (S.abort) break;
-      const int64_t base = S.base;
-      __syncthreads();
-      resolve_windows<F64, SUM, SEQ, MAP>(c, S, smem, D, true, base);
-      total = base + cnt;
+      dead0 = nullptr;  // (k_big reads the records again)
     } else {
       bool ok = true;
       if (D.n > 0) {
@@ -1078,40 +1203,88 @@ __global__ void __launch_bounds__(kRT, 2) k_resolve(Ctx c) {
         if (S.abort) break;
         total = S.base + nnz;
       } else {
+        // the elements wait over the bucket's records for k_place
         const uint32_t nnz = resolve_tile<F64, SUM, SEQ, MAP>(c, S, smem, D.n, D, D.rg, kDefer, [](uint32_t) {
           return int64_t{0};
         });
-        if (tid == 0) {
-          if (D.rg.klo == 0) st_release_u64(&c.bk_state[D.b], kStIncl | (uint64_t)nnz);
-          else if ((int64_t)D.b != c.withhold) st_release_u64(&c.bk_state[D.b], kStAgg | (uint64_t)nnz);
-        }
-        deferred = true;
-        dnnz = nnz;
+        if (tid == 0) c.bk_nnz[D.b] = nnz;
+        dead0 = res_vals(c, D.start, D.n) + nnz;
       }
     }
     if (total >= 0 && tid == 0 && D.rg.klo + D.rg.span == D.K) {
       c.col_ptr[D.col_base + D.n_cols] = total;
       c.d_nnz[D.mi] = total;
     }
-    const int64_t cstart = D.start;
-    const uint32_t cn = D.n;
+    const void* dead1 = c.rec + D.start + D.n;
     fence_proxy_async();  // this thread's writes to the record area come before the next bulk copy
-    __syncthreads();      // the record area, the descriptors and the staging area are free
+    __syncthreads();      // the record area and the descriptors are free
     if (tid == 0) {
-      S.pend = S.cur;
-      S.pend.valid = deferred ? 1u : 0u;
-      S.pend.nnz = dnnz;
       S.cur = nxt;
       if (S.cur.valid) start_bucket(c, S, smem, S.cur, cap, NB);
     }
-    if (dn) discard_records(c, dstart, dn);  // the elements placed above
-    if (!deferred && cn) discard_records(c, cstart, cn);
-    dn = 0;
+    if (dead0) discard_lines(dead0, dead1);
     __syncthreads();
   }
   if (copying) mbar_wait_bounded(&S.bar, phase);  // (a call that stopped early)
-  __syncthreads();  // every thread has read the elements placed last
-  if (dn) discard_records(c, dstart, dn);
+}
+
+// Calls without the map: every bucket's elements wait over its records, in
+// key order (keys relative to the bucket, values); one block per bucket writes
+// them to their place in the CSC arrays, with the offsets of the columns that
+// start in the bucket.
+template <bool F64>
+__global__ void __launch_bounds__(256) k_place(Ctx c) {
+  __shared__ Desc D;
+  __shared__ int64_t s_base;
+  __shared__ uint32_t s_nnz, s_skip;
+  const uint32_t b = blockIdx.x;
+  if (b >= c.scal->NB || is_aborted(c)) return;
+  if (threadIdx.x == 0) {
+    D = load_desc(c, b);
+    s_skip = (D.K == 0 || D.n > (uint32_t)kRCap) ? 1u : 0u;  // (placed by k_resolve / k_big)
+    s_nnz = c.bk_nnz[b];
+    s_base = bucket_base(c, D);
+  }
+  __syncthreads();
+  if (s_skip) return;
+  const uint32_t nnz = s_nnz;
+  const int64_t base = s_base;
+  const uint32_t* keys = res_keys(c, D.start);
+  const uint64_t* vals = res_vals(c, D.start, D.n);
+  emit_range<F64>(c, D, D.rg, nnz, base, [&](uint32_t i, uint32_t& k, uint64_t& v) {
+    k = __ldcs(keys + i);
+    v = __ldcs(reinterpret_cast<const unsigned long long*>(vals) + i);
+  });
+  if (threadIdx.x == 0 && D.rg.klo + D.rg.span == D.K) {
+    c.col_ptr[D.col_base + D.n_cols] = base + nnz;
+    c.d_nnz[D.mi] = base + nnz;
+  }
+}
+
+// Calls without the map: the buckets with more writes than fit (counted by
+// k_resolve), resolved again in windows and placed at once.
+template <bool F64, bool SUM, bool SEQ>
+__global__ void __launch_bounds__(kRT, 1) k_big(Ctx c) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ RShared S;
+  const uint32_t nbig = c.scal->big_n;
+  if (threadIdx.x == 0) S.abort = 0;
+  for (uint32_t i = blockIdx.x; i < nbig && !is_aborted(c); i += gridDim.x) {
+    if (threadIdx.x == 0) {
+      S.cur = load_desc(c, c.big_list[i]);
+      S.base = bucket_base(c, S.cur);
+    }
+    __syncthreads();
+    const Desc& D = S.cur;
+    const int64_t base = S.base;
+    __syncthreads();
+    const uint32_t cnt = resolve_windows<F64, SUM, SEQ, false>(c, S, smem, D, true, base);
+    if (threadIdx.x == 0 && D.rg.klo + D.rg.span == D.K) {
+      c.col_ptr[D.col_base + D.n_cols] = base + cnt;
+      c.d_nnz[D.mi] = base + cnt;
+    }
+    __syncthreads();
+  }
 }
 
 template <typename K>
@@ -1138,7 +1311,8 @@ int resolve_capacity(bool map) { return map ? kRCapNow : kRCap; }
 void resolve_set_attributes() {
   const int bytes = (int)rlay().total;
 #define SPM_ATTR(F6, SU, SQ, MP) \
-  cudaFuncSetAttribute(k_resolve<F6, SU, SQ, MP>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  cudaFuncSetAttribute(k_resolve<F6, SU, SQ, MP>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes); \
+  cudaFuncSetAttribute(k_big<F6, SU, SQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   SPM_RES_ALL(SPM_ATTR)
 #undef SPM_ATTR
 }
@@ -1153,6 +1327,21 @@ void launch_resolve(const Ctx& ctx, int sms, cudaStream_t st) {
   }
   SPM_RES_ALL(SPM_RES)
 #undef SPM_RES
+}
+
+void launch_place(const Ctx& ctx, int sms, int64_t nbcap, cudaStream_t st) {
+  const size_t bytes = rlay().total;
+  const bool f64 = ctx.f64 != 0, sum = ctx.sum_mode != 0, seq = ctx.has_seq != 0;
+  const unsigned blocks = (unsigned)std::max<int64_t>(nbcap, 1);  // one per bucket (NB <= nbcap)
+  if (f64) k_place<true><<<blocks, 256, 0, st>>>(ctx);
+  else k_place<false><<<blocks, 256, 0, st>>>(ctx);
+#define SPM_BIG(F6, SU, SQ, MP)                             \
+  if (!MP && f64 == F6 && sum == SU && seq == SQ) {         \
+    k_big<F6, SU, SQ><<<sms, kRT, bytes, st>>>(ctx);         \
+    return;                                                 \
+  }
+  SPM_RES_ALL(SPM_BIG)
+#undef SPM_BIG
 }
 #undef SPM_RES_ALL
 

@@ -29,7 +29,7 @@ constexpr int kL2Bits = 8;                // a level-2 table refines one cell in
 constexpr int kL2Size = 1 << kL2Bits;
 constexpr int kMaxL2Tables = 32;          // level-2 tables per matrix
 constexpr int kMaxKeyBits = 52;           // n_rows * n_cols <= 2^52
-constexpr int kSubBitsMax = 11;           // counting-sort digit inside a bucket: up to 2048 sub-bins
+constexpr int kSubBitsMax = 12;           // counting-sort digit inside a bucket: up to 4096 sub-bins
 constexpr int64_t kSampleTotal = 1 << 19; // samples drawn per call (spread over the matrices)
 constexpr int64_t kSampleMin = 256;       // at least this many per matrix (or all of its writes)
 // LUT entry: bit 31 = refers to a level-2 table (bits 0..30 = table id); otherwise bit 30 =
@@ -158,7 +158,7 @@ struct Layout {
   bool seq;
   // byte offsets
   size_t meta, scal, cta, samp, cellcnt, lut, l2cell, bk_lo, bk_info, bk_count, bk_start, bk_state,
-      scanpart, hist, rec, tmp, rbk, bk_cur, l2h, total;
+      scanpart, hist, rec, tmp, rbk, bk_cur, l2h, bk_nnz, bk_out, big_list, total;
   int64_t l2h_len;  // one matrix with level-2 tables: sample counts of all level-2 cells
   bool two_pass;   // writes reach their buckets in two passes (through tmp/rbk)
 };
@@ -174,6 +174,7 @@ struct Scalars {
   uint32_t ord_done;    // ordered single pass: tiles finished
   uint32_t ord_fail;    // ordered single pass: the stream is not in order (the general path runs)
   uint32_t ord_exit;    // ordered single pass: blocks that have left
+  uint32_t big_n;       // buckets with more writes than the resolve holds (in big_list)
 };
 
 // Per partition block (chunk of writes) information.
@@ -217,6 +218,9 @@ struct Ctx {
   uint32_t* l2h;      // one matrix: sample counts of every level-2 cell (null: the planner counts)
   uint32_t* rbk;      // two-pass partition: bucket of each tmp record
   uint32_t* bk_cur;   // two-pass partition: next free slot of each bucket in rec
+  uint32_t* bk_nnz;   // calls without the map: stored elements per bucket
+  uint32_t* bk_out;   // ... their exclusive prefix over all buckets
+  uint32_t* big_list; // ... the buckets placed by k_big
   // sizes
   int64_t B, m_total, S_total, lut_total, nbcap_total, hist_bound, C;
   int32_t sum_mode, f64, keep_map, has_seq;
@@ -235,10 +239,13 @@ constexpr uint32_t kFlagKeepZeros = 1u << 30;
 
 // The per-bucket resolve kernel (resolve.cu): writes a bucket may hold to be
 // resolved from shared memory (fewer when the map is kept), its shared-memory
-// attributes (set once per device) and its launch.
+// attributes (set once per device) and its launches: the resolve kernel, then
+// (calls without the map, after the scan of the per-bucket counts) the
+// placement kernels.
 int resolve_capacity(bool map);
 void resolve_set_attributes();
 void launch_resolve(const Ctx& ctx, int sms, cudaStream_t st);
+void launch_place(const Ctx& ctx, int sms, int64_t nbcap, cudaStream_t st);
 
 // Launch counter of the library's kernels (spm_debug_launch_count).
 void count_launches(int64_t n);

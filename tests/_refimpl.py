@@ -127,3 +127,77 @@ def brute_force_update(col_ptr, row_idx, vals, shape, rows, cols, wvals, mode, s
         out.extend(X[nz, c].tolist())
         cp.append(len(ri))
     return np.array(cp, dtype=np.int64), np.array(ri, dtype=np.int64), np.array(out, dtype=np.float64)
+
+
+def exact_sums(rows, cols, vals, shape):
+    """The element-wise sums of the writes computed exactly (rational
+    arithmetic on the binary values), with IEEE special-value rules: NaN when
+    a NaN or both infinities occur, otherwise the infinity that occurs.
+    Returns {linear index: (exact sum as Fraction or float special, sum of
+    |finite contributions|)} (Fig. 2: X(r,c) += v)."""
+    from fractions import Fraction
+    n_rows = shape[0]
+    acc = {}
+    for r, c, v in zip(np.asarray(rows).tolist(), np.asarray(cols).tolist(),
+                       np.asarray(vals, dtype=np.float64).tolist()):
+        k = int(r) + int(c) * n_rows
+        s, a, nan, pinf, ninf = acc.get(k, (Fraction(0), 0.0, False, False, False))
+        if v != v:
+            nan = True
+        elif v == float("inf"):
+            pinf = True
+        elif v == float("-inf"):
+            ninf = True
+        else:
+            s += Fraction(v)
+            a += abs(v)
+        acc[k] = (s, a, nan, pinf, ninf)
+    out = {}
+    for k, (s, a, nan, pinf, ninf) in acc.items():
+        if nan or (pinf and ninf):
+            out[k] = (float("nan"), a)
+        elif pinf:
+            out[k] = (float("inf"), a)
+        elif ninf:
+            out[k] = (float("-inf"), a)
+        else:
+            out[k] = (s, a)
+    return out
+
+
+def assert_sums_match_exact(got, ref, shape, tol, out_f32=False):
+    """The CSC `got` (col_ptr, row_idx, vals) against exact_sums `ref`:
+    elements whose exact sum is special, or larger than tol * sum|c| in
+    magnitude (after rounding to the output type), must be stored with a value
+    within tol * sum|c| (specials equal); elements whose exact sum lies within
+    tol * sum|c| of zero are cancellation-ambiguous (the order of additions
+    decides whether they vanish): they may be absent, and if stored their value
+    lies within that bound too.  Nothing else may be stored."""
+    col_ptr, row_idx, vals = (np.asarray(x) for x in got)
+    n_rows = shape[0]
+    col_of = np.repeat(np.arange(shape[1]), np.diff(col_ptr))
+    stored = {}
+    for j, r, v in zip(col_of.tolist(), row_idx.tolist(), vals.astype(np.float64).tolist()):
+        stored[int(r) + int(j) * n_rows] = v
+    for k, (s, a) in ref.items():
+        if isinstance(s, float):  # a special value
+            assert k in stored, f"element {k}: special sum {s} not stored"
+            g = stored.pop(k)
+            assert (g != g and s != s) or g == s, f"element {k}: {g} != {s}"
+            continue
+        try:
+            sf = float(s)
+        except OverflowError:
+            sf = float("inf") if s > 0 else float("-inf")
+        with np.errstate(over="ignore"):
+            rounded = float(np.float32(sf)) if out_f32 else sf
+        if rounded in (float("inf"), float("-inf")):  # the rounded sum overflows
+            assert stored.pop(k, None) == rounded, f"element {k}: exact sum {sf} rounds to {rounded}"
+            continue
+        ambiguous = abs(sf) <= tol * a or rounded == 0.0
+        if k in stored:
+            g = stored.pop(k)
+            assert abs(g - sf) <= tol * a, f"element {k}: {g} vs exact {sf} (sum|c| {a})"
+        else:
+            assert ambiguous, f"element {k}: exact sum {sf} (sum|c| {a}) not stored"
+    assert not stored, f"{len(stored)} elements stored that were never written"

@@ -50,11 +50,11 @@ def _check(got, want, mode, exact, dtype, scale=None):
     if mode == "set" or exact:
         assert_bit_exact(got[2], want[2])
     else:
+        assert scale is not None, "sums are checked against the sum of |contributions| of each element"
         tol = 1e-12 if dtype == np.float64 else 1e-5
         w = np.asarray(want[2], dtype=np.float64)
         g = got[2].astype(np.float64)
-        bound = tol * (scale if scale is not None else np.maximum(np.abs(w), 1.0))
-        assert np.all(np.abs(g - w) <= bound)
+        assert np.all(np.abs(g - w) <= tol * scale)
 
 
 def _scale(A, d, want, shape):
@@ -130,7 +130,7 @@ def test_degenerate_updates(mode):
     empty = (np.zeros(shape[1] + 1, dtype=np.int64), e, np.zeros(0))
     want = oracle.assemble_csc(d["rows"], d["cols"], d["vals"], shape, mode=mode)
     got = _gpu_update(empty, shape, d["rows"], d["cols"], d["vals"], mode)
-    _check(got, want, mode, mode == "set", np.float64, None if mode == "set" else np.maximum(np.abs(want[2]), 1.0))
+    _check(got, want, mode, mode == "set", np.float64, None if mode == "set" else _scale(empty, d, want, shape))
     # both empty
     got = _gpu_update(empty, shape, e, e, np.zeros(0), mode)
     assert got[0].tolist() == [0] * (shape[1] + 1) and len(got[1]) == 0
@@ -145,7 +145,7 @@ def test_degenerate_updates(mode):
         AA = _matrix_a(dd, np.float64)
         want = oracle.csc_update(*AA, shp, dd["rows"], dd["cols"], dd["vals"], mode=mode)
         got = _gpu_update(AA, shp, dd["rows"], dd["cols"], dd["vals"], mode)
-        _check(got, want, mode, False, np.float64, np.maximum(np.abs(want[2]), 1.0) * 8)
+        _check(got, want, mode, False, np.float64, None if mode == "set" else _scale(AA, dd, want, shp))
 
 
 def test_stored_zeros_in_a_are_removed():
@@ -199,4 +199,5 @@ def test_update_at_scale_sampled():
     for mode in ("set", "sum"):
         want = oracle.csc_update(*A, d["shape"], rows, cols, vals, mode=mode)
         got = _gpu_update(A, d["shape"], rows, cols, vals, mode)
-        _check(got, want, mode, False, np.float64, np.maximum(np.abs(want[2]), 1.0) * 8)
+        w = dict(rows=rows, cols=cols, vals=vals)
+        _check(got, want, mode, False, np.float64, None if mode == "set" else _scale(A, w, want, d["shape"]))

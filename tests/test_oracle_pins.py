@@ -15,7 +15,7 @@ import pytest
 import oracle
 import workloads
 from tests import _golden
-from tests._refimpl import (brute_force_csc, check_csc_invariants, contribution_abs_sums, densify,
+from tests._refimpl import (assert_sums_match_exact, brute_force_csc, check_csc_invariants, contribution_abs_sums, densify,
                             distinct_nonzero_count)
 
 
@@ -169,6 +169,34 @@ def test_last_write_1000_invariants():
 # --------------------------------------------------------------------------------------------
 # Library special cases
 # --------------------------------------------------------------------------------------------
+def test_sum_mode_is_within_tolerance_of_exact_sums():
+    """Add mode against the exact (rational) sum of each element's writes:
+    within 1e-12 * sum|contributions| (float64) or 1e-5 (float32 values,
+    float64 accumulation), special values by IEEE rules, across values far
+    apart in magnitude (1e300 next to 3.25e-300, subnormals); elements whose
+    exact sum is within that bound of zero may vanish either way."""
+    from tests._refimpl import exact_sums
+    rng = np.random.default_rng(808)
+    for out_f32 in (False, True):
+        specials = ([0.0, -0.0, np.nan, np.inf, -np.inf, 1e300, -1e300, 3.25e-300, 5e-324 * 3] if not out_f32 else
+                    [0.0, -0.0, np.nan, np.inf, -np.inf, 3e38, -3e38, 1e-40, 1.4e-45 * 3])
+        for trial in range(40):
+            n_rows, n_cols = int(rng.integers(1, 30)), int(rng.integers(1, 30))
+            m = int(rng.integers(0, 400))
+            n_coord = int(rng.integers(1, 50))
+            cr, cc = rng.integers(0, n_rows, n_coord), rng.integers(0, n_cols, n_coord)
+            pick = rng.integers(0, n_coord, m)
+            vals = rng.standard_normal(m) * np.exp(rng.uniform(-20, 20, m))
+            sel = rng.random(m) < 0.2
+            vals[sel] = np.array(specials)[rng.integers(0, len(specials), int(sel.sum()))]
+            dt = np.float32 if out_f32 else np.float64
+            rows, cols, v = cr[pick].astype(np.int32), cc[pick].astype(np.int32), vals.astype(dt)
+            got = oracle.assemble_csc(rows, cols, v, (n_rows, n_cols), mode="sum")
+            check_csc_invariants(*got, (n_rows, n_cols))
+            assert_sums_match_exact(got, exact_sums(rows, cols, v, (n_rows, n_cols)), (n_rows, n_cols),
+                                    1e-5 if out_f32 else 1e-12, out_f32=out_f32)
+
+
 def test_sum_mode_matches_scipy():
     sp = pytest.importorskip("scipy.sparse")
     d = workloads.zipf_batch(m=200_000, n=3000)

@@ -17,7 +17,7 @@ import numpy as np
 import pytest
 
 import workloads
-from tests.gpu_helpers import TOL, to_dev
+from tests.gpu_helpers import to_dev
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -57,11 +57,11 @@ def _regular_call(d, mode):
 
 
 def _compare(got, want, dtype):
+    # the same kernels on the same input: the same bytes
     np.testing.assert_array_equal(got[0], want[0])
     np.testing.assert_array_equal(got[1], want[1])
-    tol = TOL[np.float64 if dtype == np.float64 else np.float32]
-    g, w = got[2].astype(np.float64), want[2].astype(np.float64)
-    assert np.all(np.abs(g - w) <= tol * np.abs(w))
+    assert got[2].dtype == want[2].dtype == dtype
+    assert got[2].tobytes() == want[2].tobytes()
 
 
 def test_static_scratch_matches_workspace_call_twice_in_a_row():
