@@ -123,12 +123,13 @@ def measured_peak():
 
 
 def source_hash():
-    """Hash of the sources k_resolve is compiled from (its kernel file and the
-    headers it includes): a committed traffic figure is used only while they
-    are unchanged."""
+    """Hash of the library's sources (every kernel file and header): a
+    committed traffic figure is used only while they are unchanged."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1805_03380_gb300", "csrc")
-    for fn in ("assemble.cu", "exact_sum.cuh", "spm_common.cuh"):
+    for fn in sorted(os.listdir(csrc)):
+        if not fn.endswith((".cu", ".cuh", ".h")):
+            continue
         with open(os.path.join(csrc, fn), "rb") as f:
             h.update(fn.encode() + f.read())
     with open(os.path.join(ROOT, "include", "spm.h"), "rb") as f:
@@ -136,9 +137,10 @@ def source_hash():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(workload):
-    """DRAM bytes per k_resolve launch from the committed ncu summary, if it
-    was taken on the current sources (otherwise None)."""
+def profiled_traffic(workload, key="dram_bytes_per_call"):
+    """DRAM bytes (read + written) per call, or per launch of one kernel, from
+    the committed ncu summary of the workload, if it was taken on the current
+    sources (otherwise None)."""
     p = os.path.join(ROOT, "profiles", f"traffic_{workload}.md")
     if not os.path.exists(p):
         return None
@@ -151,7 +153,7 @@ def profiled_traffic(workload):
     if vals.get("source_hash", "").split(" ")[0] != source_hash():
         return None
     try:
-        return int(vals["dram_bytes_per_launch"])
+        return int(vals[key])
     except Exception:
         return None
 
@@ -347,7 +349,7 @@ def run_update(args, world, rank, local_rank):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, dt, sa, sw = update_oracle_rate(spec, min(args.ref_sample, 1_000_000))
-        cpu = {"value": rate, "unit": UPDATE_UNIT, "cores": 1, "kind": "oracle",
+        cpu = {"value": rate, "unit": UPDATE_UNIT, "cores": 1, "host_cores": os.cpu_count(), "kind": "oracle",
                "sample": f"{sa} existing elements (first writes of the matrix stream) + {sw} new writes, "
                          f"dict + two-pointer merge in Python, 1 thread, {dt:.1f} s"}
     if rank == 0:
@@ -591,12 +593,45 @@ def run_batched_or_diff(args, world, rank, local_rank):
             spm.csc_mm(A.col_ptr, A.row_idx, A.vals, shape, X.detach())
         fb_ms = timed(fwd_bwd, args.steps)
         am_ms = timed(asm_mm, args.steps)
+        # the product kernel alone: Y = A X gathered over the columns of A^T
+        A = spm.assemble_csc(rows, cols, vals, shape, mode=spec["mode"])
+        At = spm.csc_transpose(A.col_ptr, A.row_idx, A.vals, shape)
+        Xd = X.detach()
+
+        def gather():
+            spm.csc_mm(At.col_ptr, At.row_idx, At.vals, At.shape, Xd, transpose=True, check=False)
+        # the operands fit in L2: flush it (write 512 MB) before every timed launch
+        flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+        for _ in range(args.warmup):
+            gather()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(max(args.steps, 20))]
+        for e0, e1 in evs:
+            flush.zero_()
+            e0.record(stream)
+            gather()
+            e1.record(stream)
+        torch.cuda.synchronize()
+        mm_ms = statistics.mean(e0.elapsed_time(e1) for e0, e1 in evs)
+        del flush
+        nnz_a = A.nnz
+        mm_bytes = nnz_a * (4 + 4) + 2 * shape[0] * 16 * 4 + (shape[0] + 1) * 8
+        mm_ach = mm_bytes / (mm_ms / 1000.0) / 1e9
         units, ms = len(f["rows"]), fb_ms
         metric = "assembled triplets/sec through assemble + SpMM forward and backward"
-        extra = {"writes": len(f["rows"]), "nodes": shape[0], "k": 16, "assembly_plus_spmm_ms": am_ms,
+        extra = {"writes": len(f["rows"]), "nodes": shape[0], "nnz": nnz_a, "k": 16, "assembly_plus_spmm_ms": am_ms,
                  "forward_backward_over_assembly_spmm": fb_ms / am_ms}
         sv = 4
         alg = None
+        peak0, peak_kind0 = measured_peak()
+        spmm_roofline = {"bound": "hbm", "achieved": mm_ach, "peak": peak0, "unit": "GB/s", "frac": mm_ach / peak0,
+                         "traffic": None, "peak_kind": peak_kind0 + " copy bandwidth",
+                         "kernel": "k_mm_gather: Y = A X (263,169 x 16 float32) over the columns of A^T, "
+                                   "CUDA events around each launch",
+                         "algorithmic_bytes_per_launch": mm_bytes,
+                         "bytes_formula": "nnz*(4+sv) + 2*n*k*sv + (n+1)*8", "launch_ms_mean": mm_ms,
+                         "l2": "operands (about 55 MB) fit in the 129 MB L2: a 512 MB write flushes it before "
+                               "every timed launch"}
     tot_s, tot_units = aggregate(ms / 1000.0 * args.steps, units * args.steps, world, dev)
     peak, peak_kind = measured_peak()
     line = {
@@ -606,6 +641,8 @@ def run_batched_or_diff(args, world, rank, local_rank):
         "config": dict({"workload": args.workload, "description": spec["desc"]}, **extra),
         "gpu": torch.cuda.get_device_name(dev),
     }
+    if spec["kind"] == "diff":
+        line["roofline"] = spmm_roofline
     if alg is not None:
         achieved = alg / (ms / 1000.0) / 1e9
         line["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -643,7 +680,7 @@ def run_reference(args, world, rank):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.workload, "description": spec["desc"],
                        "sample": f"{sa} existing elements + {sw} new writes per step"},
-            "cpu_baseline": {"value": value, "unit": UPDATE_UNIT, "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": UPDATE_UNIT, "cores": 1, "host_cores": os.cpu_count(), "kind": "oracle",
                              "sample": f"{sa} existing elements + {sw} new writes, Python dict + merge, 1 thread"},
             "e2e": {"value": value, "unit": UPDATE_UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}),
             flush=True)
@@ -674,11 +711,101 @@ def run_reference(args, world, rank):
         "vs_baseline": None, "dtype": "f64" if spec["dtype"].__name__ == "float64" else "f32", "data": "synthetic",
         "config": {"workload": args.workload, "description": spec["desc"],
                    "sample": f"first {sample} writes of the same stream per step"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "host_cores": os.cpu_count(), "kind": "oracle",
                          "sample": f"first {sample} writes of the workload's stream, std::map build + walk, 1 thread"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def run_e2e(spm, asm0, d, rows, cols, vals, nnz, steps, args, world, dev):
+    """End-to-end rate of the single-matrix call through the public API:
+    every step copies its writes from pinned host memory to the device, runs
+    spm_assemble_csc and copies the CSC (col_ptr and the stored elements)
+    back to pinned host memory.  Two slots (device inputs, an Assembler,
+    host outputs) alternate between steps so that the copies of neighbouring
+    steps overlap the call.  Returns (writes/s, D2H bytes per step, H2D bytes
+    per step)."""
+    import torch
+    m = len(d["rows"])
+    n_cols = d["shape"][1]
+    sv = vals.element_size()
+    if args.profile or steps == 0:
+        return None, 0, m * (8 + sv)
+    h_in = [torch.from_numpy(d[k]).pin_memory() for k in ("rows", "cols", "vals")]
+    slots = []
+    for j in range(2):
+        a = asm0 if j == 0 else spm.Assembler(d["shape"], m, vals.dtype, asm0.mode, device=dev)
+        slots.append({
+            "asm": a, "d_in": [torch.empty_like(t) for t in (rows, cols, vals)],
+            "h_cp": torch.empty(n_cols + 1, dtype=torch.int64).pin_memory(),
+            "h_ri": torch.empty(m, dtype=torch.int32).pin_memory(),
+            "h_v": torch.empty(m, dtype=vals.dtype).pin_memory(),
+            "h_nnz": torch.zeros(1, dtype=torch.int64).pin_memory(),
+            "h2d": torch.cuda.Event(), "done": torch.cuda.Event(), "d2h": torch.cuda.Event(), "used": False})
+    s_in = [torch.cuda.Stream(device=dev) for _ in range(3)]
+    s_cmp = torch.cuda.Stream(device=dev)
+    s_out = torch.cuda.Stream(device=dev)
+    d2h_bytes = []
+
+    def enqueue(k):
+        sl = slots[k % 2]
+        for st, dst, src in zip(s_in, sl["d_in"], h_in):
+            if sl["used"]:
+                st.wait_event(sl["done"])  # the call two steps back has read this slot's inputs
+            with torch.cuda.stream(st):
+                dst.copy_(src, non_blocking=True)
+        ev_in = []
+        for st in s_in:
+            e = torch.cuda.Event()
+            e.record(st)
+            ev_in.append(e)
+        for e in ev_in:
+            s_cmp.wait_event(e)
+        if sl["used"]:
+            s_cmp.wait_event(sl["d2h"])  # this slot's outputs have been copied out
+        sl["asm"].run(*sl["d_in"], stream=s_cmp)
+        with torch.cuda.stream(s_cmp):
+            sl["h_nnz"].copy_(sl["asm"].d_nnz, non_blocking=True)
+        sl["done"].record(s_cmp)
+        sl["used"] = True
+
+    def drain(k):
+        sl = slots[k % 2]
+        sl["done"].synchronize()  # step k has ended (step k+1 is queued behind it)
+        k_nnz = int(sl["h_nnz"][0])
+        s_out.wait_event(sl["done"])
+        a = sl["asm"]
+        with torch.cuda.stream(s_out):
+            sl["h_cp"].copy_(a.col_ptr, non_blocking=True)
+            sl["h_ri"][:k_nnz].copy_(a.row_idx[:k_nnz], non_blocking=True)
+            sl["h_v"][:k_nnz].copy_(a.out_vals[:k_nnz], non_blocking=True)
+        sl["d2h"].record(s_out)
+        d2h_bytes.append(8 + (n_cols + 1) * 8 + k_nnz * (4 + sv))
+
+    def run(n):
+        for k in range(n):
+            enqueue(k)
+            if k >= 1:
+                drain(k - 1)
+        drain(n - 1)
+        s_out.synchronize()
+
+    run(3)  # warm-up
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    d2h_bytes.clear()
+    t0 = time.perf_counter()
+    run(steps)
+    e2e_s = time.perf_counter() - t0
+    for sl in slots:
+        spm._raise_status(sl["asm"].d_status, "spm_assemble_csc")
+    k_nnz = int(slots[(steps - 1) % 2]["h_nnz"][0])
+    if k_nnz != nnz or int(slots[(steps - 1) % 2]["h_cp"][-1]) != nnz:
+        raise RuntimeError("end-to-end result differs from the device-timed one")
+    e2e_tot_s, e2e_units = aggregate(max(e2e_s, 1e-9), m * steps, world, dev)
+    return e2e_units / e2e_tot_s, statistics.mean(d2h_bytes), m * (8 + sv)
 
 
 def main():
@@ -786,74 +913,52 @@ def main():
     value = tot_units / tot_s
     ms_per_step = 1000.0 * tot_s / args.steps
 
-    # ---- roofline of the dominant kernel (k_resolve: reads the bucketed
-    # writes, key + value, and writes the CSC), CUDA events around its launch
-    # on the call's stream; and of the whole call (the sync step) ----
+    # ---- roofline of the whole call (the sync step: one read of the writes,
+    # one write of the CSC), CUDA events around each call on its stream; and
+    # of its two largest kernels, CUDA events at their launch boundaries ----
     peak, peak_kind = measured_peak()
     stage_ms = {k: statistics.mean(v) for k, v in stages.items()}
-    res_bytes = m * (4 + sv) + nnz * (4 + sv) + (n_cols + 1) * 8
-    res_ms = stage_ms["resolve"]
-    res_achieved = res_bytes / (res_ms / 1000.0) / 1e9
-    roofline = {"bound": "hbm", "achieved": res_achieved, "peak": peak, "unit": "GB/s", "frac": res_achieved / peak,
-                "traffic": profiled_traffic(args.workload), "peak_kind": peak_kind + " copy bandwidth",
-                "kernel": "k_resolve (per bucket: sort in shared memory, reduce runs, write CSC)",
-                "algorithmic_bytes_per_launch": res_bytes,
-                "bytes_formula": "m*(4+sv) + nnz*(4+sv) + (n_cols+1)*8",
-                "launch_ms_mean": res_ms}
     alg_bytes = m * (4 + 4 + sv) + nnz * (4 + sv) + (n_cols + 1) * 8
     mean_call_s = statistics.mean(step_ms) / 1000.0
     achieved = alg_bytes / mean_call_s / 1e9
-    step_roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "kernel": f"spm_assemble_csc: the whole sync step ({launches // max(args.steps, 1)} kernel "
-                               "launches), CUDA events around each call",
-                     "algorithmic_bytes_per_call": alg_bytes,
-                     "bytes_formula": "m*(4+4+sv) + nnz*(4+sv) + (n_cols+1)*8",
-                     "call_ms_mean": 1000 * mean_call_s, "stage_ms_mean": stage_ms}
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": profiled_traffic(args.workload), "peak_kind": peak_kind + " copy bandwidth",
+                "kernel": f"spm_assemble_csc: the whole sync step ({launches // max(args.steps, 1)} kernel "
+                          "launches), CUDA events around each call",
+                "algorithmic_bytes_per_launch": alg_bytes,
+                "bytes_formula": "m*(4+4+sv) + nnz*(4+sv) + (n_cols+1)*8", "launch_ms_mean": 1000 * mean_call_s,
+                "stage_ms_mean": stage_ms}
+    # k_resolve reads the 16-byte bucketed records and writes each bucket's
+    # stored elements (row, value); k_place (with its offset scan) reads those
+    # and writes the CSC
+    res_bytes = m * 16 + nnz * (4 + sv)
+    place_bytes = 2 * nnz * (4 + sv) + (n_cols + 1) * 8
+    kernel_rooflines = []
+    for name, stage, nbytes, formula in (("k_resolve", "resolve", res_bytes, "m*16 + nnz*(4+sv)"),
+                                         ("k_place (+ offset scan)", "place", place_bytes,
+                                          "2*nnz*(4+sv) + (n_cols+1)*8")):
+        if stage in stage_ms and stage_ms[stage] > 0:
+            a = nbytes / (stage_ms[stage] / 1000.0) / 1e9
+            kernel_rooflines.append({"kernel": name, "bound": "hbm", "achieved": a, "peak": peak, "unit": "GB/s",
+                                     "frac": a / peak, "algorithmic_bytes_per_launch": nbytes,
+                                     "bytes_formula": formula, "launch_ms_mean": stage_ms[stage],
+                                     "traffic": profiled_traffic(args.workload, f"{stage}_dram_bytes_per_launch")})
 
-    # ---- end to end through the public API: pinned host buffers, copies inside ----
-    e2e_steps = args.e2e_steps or min(args.steps, 10)
-    h_rows = torch.from_numpy(d["rows"]).pin_memory()
-    h_cols = torch.from_numpy(d["cols"]).pin_memory()
-    h_vals = torch.from_numpy(d["vals"]).pin_memory()
-    o_cp = torch.empty(n_cols + 1, dtype=torch.int64).pin_memory()
-    o_ri = torch.empty(m, dtype=torch.int32).pin_memory()
-    o_v = torch.empty(m, dtype=vals.dtype).pin_memory()
-    d_rows, d_cols, d_vals = torch.empty_like(rows), torch.empty_like(cols), torch.empty_like(vals)
-    d2h = 0
-
-    def e2e_step():
-        d_rows.copy_(h_rows, non_blocking=True)
-        d_cols.copy_(h_cols, non_blocking=True)
-        d_vals.copy_(h_vals, non_blocking=True)
-        asm.run(d_rows, d_cols, d_vals)
-        k = int(asm.d_nnz.item())
-        o_cp.copy_(asm.col_ptr, non_blocking=True)
-        o_ri[:k].copy_(asm.row_idx[:k], non_blocking=True)
-        o_v[:k].copy_(asm.out_vals[:k], non_blocking=True)
-        torch.cuda.current_stream().synchronize()
-        return 8 + (n_cols + 1) * 8 + k * (4 + sv)
-
-    if args.profile:
-        e2e_steps = 0
-    else:
-        e2e_step()
-    torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        d2h = e2e_step()
-    e2e_s = time.perf_counter() - t0
-    e2e_tot_s, e2e_units = aggregate(max(e2e_s, 1e-9), m * e2e_steps, world, dev)
-    if int(asm.d_status.item()) != 0:
-        raise RuntimeError("device status not OK after the e2e steps")
+    # ---- end to end through the public API: pinned host buffers, copies
+    # inside the timed region.  Consecutive steps overlap as a user streaming
+    # batches would run them: the inputs of step k+1 travel to the device
+    # while step k assembles and the CSC of step k-1 travels back; step k-1's
+    # stored-element count is read once its call has ended, with step k
+    # already queued behind it. ----
+    e2e_steps = args.e2e_steps or min(args.steps, 20)
+    e2e_value, d2h, h2d = run_e2e(spm, asm, d, rows, cols, vals, nnz, e2e_steps, args, world, dev)
 
     # ---- CPU oracle baseline (rank 0, N = 1 only) ----
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.profile:
         sample = min(args.cpu_sample, m)
         rate, dt = oracle_rate(d, spec["mode"], sample)
-        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "host_cores": os.cpu_count(), "kind": "oracle",
                "sample": f"first {sample} of the {m} writes of this stream, std::map build + in-order walk, "
                          f"1 thread, {dt:.1f} s"}
 
@@ -868,10 +973,10 @@ def main():
                        "l2": "inputs larger than the 129 MB L2 (no flush between steps)",
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline,
-            "step_roofline": step_roofline,
+            "kernel_rooflines": kernel_rooflines,
             "cpu_baseline": cpu,
-            "e2e": {"value": e2e_units / e2e_tot_s, "unit": UNIT, "h2d_bytes_per_step": m * (8 + sv),
-                    "d2h_bytes_per_step": d2h, "steps": e2e_steps},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "steps": e2e_steps, "overlap": "H2D of step k+1, call k and D2H of step k-1 on three streams"},
             "clocks": clocks,
             "gpu_launches": launches,
             "gpu": torch.cuda.get_device_name(dev),

@@ -21,7 +21,8 @@
  *     the workspace; the library never allocates, frees or synchronises.
  *   - Work is enqueued on `stream` (a cudaStream_t; NULL = legacy default
  *     stream) and returns immediately.  spm_assemble_csc,
- *     spm_assemble_csc_batched, spm_csc_mm and spm_triplet_dvals can be
+ *     spm_assemble_csc_batched, spm_csc_transpose, spm_csc_mm and
+ *     spm_triplet_dvals can be
  *     captured in a CUDA graph once a first call on the device has returned
  *     (that first call reads device attributes).
  *   - Host-detectable errors (NULL pointers, negative sizes, index spaces that
@@ -87,11 +88,12 @@ int32_t spm_version(void);
  * spm_assemble_csc needs for these sizes, dtype, mode and flags.
  * Returns SPM_ERR_INVALID_ARG / SPM_ERR_UNSUPPORTED for sizes the call would
  * reject.  The workspace needs no initialisation and may be reused by
- * successive calls on the same stream.  It is dominated by 32 bytes per write
- * (the writes in bucket order, then a scratch copy that holds the first
- * partition pass and the per-bucket results), plus 8 per write with seq and 4
- * per write when the two-pass partition may run; it depends on the tuning
- * (spm_set_tuning).
+ * successive calls on the same stream.  It is dominated by the 16-byte
+ * record of every write in bucket order (which later also holds the
+ * per-bucket results), plus 20 bytes per write when the two-pass partition
+ * runs (the first pass's records and bucket numbers; from 2^22 writes with
+ * the default tuning), plus the planner's tables: about 24 bytes per write
+ * at 10^6 writes and 37 at 10^8.  It depends on the tuning (spm_set_tuning).
  */
 spm_status spm_assemble_csc_workspace(int64_t n_rows, int64_t n_cols, int64_t m, spm_dtype dtype,
                                       spm_mode mode, uint32_t flags, size_t* bytes);
@@ -181,7 +183,7 @@ spm_status spm_assemble_csc_batched(int64_t batch, const int64_t* h_n_rows, cons
  * this library's device image: every GPU on which the library is loaded
  * holds that array until the process exits.  The call itself allocates
  * nothing.  Sizes whose workspace (spm_assemble_csc_workspace) exceeds
- * 32 MiB -- roughly 0.75 million float64 writes -- are rejected with
+ * 32 MiB -- about 1.4 million writes -- are rejected with
  * SPM_ERR_WORKSPACE_TOO_SMALL before anything is launched.
  *
  * The first call on a device looks up the array's device address (with that
@@ -308,21 +310,63 @@ spm_status spm_csc_trace_atb(int64_t n_rows, int64_t n_cols, const int64_t* a_co
                              void* workspace, size_t ws_bytes, void* stream);
 
 /*
- * spm_csc_mm -- Y = A X (transpose = 0) or Y = A^T X (transpose = 1) for A in
- * CSC (Section 3.1; the paper's use cases (iv) "multiplication of dense
- * vectors with sparse matrices", Fig. 2 "W = V * X").
+ * spm_csc_transpose_workspace / spm_csc_transpose -- the CSC of A^T (an
+ * n_cols x n_rows matrix; equivalently the row-major CSR of A) from the CSC
+ * of A (Section 3.1's compressed column format; Table 1's transpose X.t(),
+ * one of the bulk coordinate transformations of Section 3's use case (iii)).
+ * Stored element (i, j, v) of A becomes (j, i, v)
+ * of A^T; inside each column of A^T the rows (A's columns) increase.  Built
+ * by the assembly path: every coordinate occurs once, so each value, an
+ * explicit zero included, is carried over bit for bit, and repeated calls
+ * give the same bytes.
+ *
+ *   col_ptr int64[n_cols+1], row_idx int32[nnz], vals (dtype)[nnz]   A
+ *                 (offsets 0 .. nnz and non-decreasing, otherwise *d_status
+ *                 = SPM_ERR_INVALID_ARG; a row outside [0, n_rows)
+ *                 SPM_ERR_INDEX_OUT_OF_RANGE; the output is then unspecified)
+ *   t_col_ptr int64[n_rows+1], t_row_idx int32[nnz], t_vals (dtype)[nnz]
+ *                 A^T, written; must not overlap the input
+ *   d_status int32[1]   set to SPM_OK first
+ *   workspace   at least spm_csc_transpose_workspace() bytes (about the
+ *               assembly's workspace for nnz writes, plus 4 bytes per element)
+ */
+spm_status spm_csc_transpose_workspace(int64_t n_rows, int64_t n_cols, int64_t nnz, spm_dtype dtype, size_t* bytes);
+
+spm_status spm_csc_transpose(int64_t n_rows, int64_t n_cols, int64_t nnz, const int64_t* col_ptr,
+                             const int32_t* row_idx, const void* vals, spm_dtype dtype, int64_t* t_col_ptr,
+                             int32_t* t_row_idx, void* t_vals, int32_t* d_status, void* workspace, size_t ws_bytes,
+                             void* stream);
+
+/*
+ * spm_csc_mm_workspace / spm_csc_mm -- Y = A X (transpose = 0) or Y = A^T X
+ * (transpose = 1) for A in CSC (Section 3.1; the paper's use cases (iv)
+ * "multiplication of dense vectors with sparse matrices", Fig. 2
+ * "W = V * X").
  *
  *   col_ptr int64[n_cols+1], row_idx int32[nnz], vals (dtype)[nnz]   A
  *   X   (dtype) row-major, (transpose ? n_rows : n_cols) x k, leading dim ldx
  *   Y   (dtype) row-major, (transpose ? n_cols : n_rows) x k, leading dim ldy;
  *       overwritten.  ldx, ldy >= k.  X and Y must not overlap.
- * Accumulation is in the value type.  Y = A X adds the contributions of each
- * column with atomic adds (order not fixed); Y = A^T X gathers each output row
- * in storage order.
+ *   d_status  int32[1], set to SPM_OK first; required for transpose = 0,
+ *             optional (NULL) for transpose = 1.  A row index outside the
+ *             matrix is skipped and reported as SPM_ERR_INDEX_OUT_OF_RANGE;
+ *             the offsets must be well formed for transpose = 1 (they are
+ *             checked for transpose = 0).
+ *   workspace at least spm_csc_mm_workspace() bytes: none for transpose = 1;
+ *             for transpose = 0 the CSC of A^T and the transpose's workspace.
+ * Every output row is gathered in a fixed order: Y = A^T X walks column c of
+ * A in storage order, Y = A X builds A^T (spm_csc_transpose) and walks its
+ * columns, i.e. row r of A in increasing column order.  Products and sums are
+ * in the value type with fused multiply-adds; repeated calls give the same
+ * bits.  (A caller that multiplies by the same A many times can keep A^T from
+ * spm_csc_transpose and call transpose = 1 on it.)
  */
-spm_status spm_csc_mm(int64_t n_rows, int64_t n_cols, const int64_t* col_ptr, const int32_t* row_idx,
-                      const void* vals, spm_dtype dtype, int32_t transpose, int64_t k, const void* X,
-                      int64_t ldx, void* Y, int64_t ldy, void* stream);
+spm_status spm_csc_mm_workspace(int64_t n_rows, int64_t n_cols, int64_t nnz, spm_dtype dtype, int32_t transpose,
+                                size_t* bytes);
+
+spm_status spm_csc_mm(int64_t n_rows, int64_t n_cols, int64_t nnz, const int64_t* col_ptr, const int32_t* row_idx,
+                      const void* vals, spm_dtype dtype, int32_t transpose, int64_t k, const void* X, int64_t ldx,
+                      void* Y, int64_t ldy, int32_t* d_status, void* workspace, size_t ws_bytes, void* stream);
 
 /*
  * spm_triplet_dvals -- gradient of a scalar loss L with respect to the value
@@ -409,9 +453,10 @@ spm_status spm_debug_withhold_publication(int64_t bucket);
  * spm_debug_stage_timing(1) makes every later assembly call on the current
  * device record CUDA events, on the call's stream, at the boundaries of its
  * six stages: 0 planning (sampling, lookup tables, bucket descriptors),
- * 1 histogram pass, 2 bucket offsets, 3 scatter pass (one or two kernels),
- * 4 per-bucket resolve (the k_resolve kernel alone), 5 placement of the
- * stored elements (calls without the map; empty otherwise).
+ * 1 histogram pass, 2 bucket offsets, 3 partition into bucket records (one
+ * or two kernels), 4 per-bucket resolve (the k_resolve kernel alone),
+ * 5 placement of the stored elements: the offset scan over the buckets,
+ * k_place and k_big (calls without the map; empty otherwise).
  * Events of the last 64 calls are kept.  spm_debug_stage_timing(0) stops
  * recording.  Not capturable in a CUDA graph while enabled.
  *

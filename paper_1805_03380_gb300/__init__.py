@@ -22,9 +22,11 @@ import torch
 __all__ = [
     "SpmError", "lib", "spm_assemble_csc", "spm_assemble_csc_workspace", "spm_assemble_csc_batched",
     "spm_assemble_csc_batched_workspace", "spm_csc_mm", "spm_triplet_dvals", "spm_set_tuning", "spm_get_tuning",
-    "spm_csc_update", "spm_csc_update_workspace", "spm_csc_lookup", "spm_csc_to_coo", "csc_lookup", "csc_to_coo",
+    "spm_csc_update", "spm_csc_update_workspace", "spm_csc_lookup", "spm_csc_to_coo", "csc_lookup", "csc_to_coo", "csc_transpose",
+    "spm_csc_transpose", "spm_csc_transpose_workspace", "spm_csc_mm_workspace",
     "spm_csc_trace_atb", "spm_csc_trace_atb_workspace", "csc_trace_atb",
-    "assemble_csc", "assemble_csc_batched", "csc_update", "csc_mm", "triplet_dvals", "AssembleMM", "Assembler", "CSC",
+    "assemble_csc", "assemble_csc_batched", "csc_update", "csc_mm", "triplet_dvals", "AssembleMM", "Assembler",
+    "BatchedAssembler", "CSC",
     "MODE_LAST_WRITE", "MODE_SUM", "KEEP_MAP", "SEQ_EXPLICIT", "LIB_PATH",
 ]
 
@@ -42,7 +44,8 @@ EXPORTED = ["spm_status_string", "spm_version", "spm_assemble_csc_workspace", "s
             "spm_set_tuning", "spm_get_tuning", "spm_debug_withhold_publication", "spm_debug_stage_timing",
             "spm_debug_stage_times", "spm_debug_launch_count", "spm_debug_plan_stats", "spm_assemble_csc_static",
             "spm_csc_update_workspace", "spm_csc_update", "spm_csc_lookup", "spm_csc_to_coo",
-            "spm_csc_trace_atb_workspace", "spm_csc_trace_atb"]
+            "spm_csc_trace_atb_workspace", "spm_csc_trace_atb", "spm_csc_transpose_workspace", "spm_csc_transpose",
+            "spm_csc_mm_workspace"]
 
 
 class SpmError(RuntimeError):
@@ -89,7 +92,10 @@ def lib():
     L.spm_csc_to_coo.argtypes = [i64, i64, p, p, p, ctypes.c_int, p, p, p, p, p]
     L.spm_csc_trace_atb_workspace.argtypes = [i64, i64, i64, ctypes.POINTER(sz)]
     L.spm_csc_trace_atb.argtypes = [i64, i64, p, p, p, i64, p, p, p, i64, ctypes.c_int, p, p, p, sz, p]
-    L.spm_csc_mm.argtypes = [i64, i64, p, p, p, ctypes.c_int, i32, i64, p, i64, p, i64, p]
+    L.spm_csc_transpose_workspace.argtypes = [i64, i64, i64, ctypes.c_int, ctypes.POINTER(sz)]
+    L.spm_csc_transpose.argtypes = [i64, i64, i64, p, p, p, ctypes.c_int, p, p, p, p, p, sz, p]
+    L.spm_csc_mm_workspace.argtypes = [i64, i64, i64, ctypes.c_int, i32, ctypes.POINTER(sz)]
+    L.spm_csc_mm.argtypes = [i64, i64, i64, p, p, p, ctypes.c_int, i32, i64, p, i64, p, i64, p, p, sz, p]
     L.spm_triplet_dvals.argtypes = [i64, p, p, p, ctypes.c_int, i64, p, i64, p, i64, p, p]
     L.spm_set_tuning.argtypes = [ctypes.POINTER(_Tuning)]
     L.spm_get_tuning.argtypes = [ctypes.POINTER(_Tuning)]
@@ -246,11 +252,35 @@ def spm_assemble_csc_batched(h_n_rows, h_n_cols, h_trip_ptr, d_n_rows, d_n_cols,
     _check(code, "spm_assemble_csc_batched")
 
 
-def spm_csc_mm(n_rows, n_cols, col_ptr, row_idx, vals, transpose, X, Y, stream=None):
+def spm_csc_transpose_workspace(n_rows, n_cols, nnz, dtype):
+    out = ctypes.c_size_t(0)
+    _check(lib().spm_csc_transpose_workspace(int(n_rows), int(n_cols), int(nnz), _dtype_code(dtype), ctypes.byref(out)),
+           "spm_csc_transpose_workspace")
+    return int(out.value)
+
+
+def spm_csc_transpose(n_rows, n_cols, col_ptr, row_idx, vals, t_col_ptr, t_row_idx, t_vals, d_status, workspace,
+                      stream=None):
+    code = lib().spm_csc_transpose(int(n_rows), int(n_cols), row_idx.numel(), _ptr(col_ptr), _ptr(row_idx),
+                                   _ptr(vals), _dtype_code(vals.dtype), _ptr(t_col_ptr), _ptr(t_row_idx),
+                                   _ptr(t_vals), _ptr(d_status), _ptr(workspace),
+                                   workspace.numel() * workspace.element_size(), _stream(stream))
+    _check(code, "spm_csc_transpose")
+
+
+def spm_csc_mm_workspace(n_rows, n_cols, nnz, dtype, transpose):
+    out = ctypes.c_size_t(0)
+    _check(lib().spm_csc_mm_workspace(int(n_rows), int(n_cols), int(nnz), _dtype_code(dtype), int(bool(transpose)),
+                                      ctypes.byref(out)), "spm_csc_mm_workspace")
+    return int(out.value)
+
+
+def spm_csc_mm(n_rows, n_cols, col_ptr, row_idx, vals, transpose, X, Y, d_status=None, workspace=None, stream=None):
     k = X.shape[1]
-    code = lib().spm_csc_mm(int(n_rows), int(n_cols), _ptr(col_ptr), _ptr(row_idx), _ptr(vals),
+    ws_bytes = 0 if workspace is None else workspace.numel() * workspace.element_size()
+    code = lib().spm_csc_mm(int(n_rows), int(n_cols), row_idx.numel(), _ptr(col_ptr), _ptr(row_idx), _ptr(vals),
                             _dtype_code(vals.dtype), int(bool(transpose)), int(k), _ptr(X), X.stride(0), _ptr(Y),
-                            Y.stride(0), _stream(stream))
+                            Y.stride(0), _ptr(d_status), _ptr(workspace), ws_bytes, _stream(stream))
     _check(code, "spm_csc_mm")
 
 
@@ -281,7 +311,7 @@ def spm_debug_withhold_publication(bucket):
     _check(lib().spm_debug_withhold_publication(int(bucket)), "spm_debug_withhold_publication")
 
 
-STAGES = ("plan", "hist", "offsets", "scatter", "resolve", "emit")
+STAGES = ("plan", "hist", "offsets", "partition", "resolve", "place")
 
 
 def spm_debug_stage_timing(enable):
@@ -374,6 +404,56 @@ class Assembler:
         nnz = int(self.d_nnz.item())
         return CSC(self.col_ptr, self.row_idx[:nnz], self.out_vals[:nnz], nnz,
                    self.map[:self.m] if self.map is not None else None, (self.n_rows, self.n_cols))
+
+
+class BatchedAssembler:
+    """Reusable batched assembly (many independent matrices, one call) with its
+    own size tables, workspace and output buffers, for a fixed batch layout:
+    matrix i has shape (n_rows[i], n_cols[i]) and its writes at
+    [trip_ptr[i], trip_ptr[i+1]) of the concatenated streams.
+
+    ``run()`` only enqueues the kernels (capturable in a CUDA graph; replays
+    may change the writes but not the layout); ``result()`` synchronises,
+    checks the device status and returns (col_ptr, row_idx, vals, nnz, map)
+    as assemble_csc_batched does.
+    """
+
+    def __init__(self, n_rows, n_cols, trip_ptr, dtype=torch.float64, mode="set", seq=False, keep_map=False,
+                 device="cuda"):
+        dev = torch.device(device)
+        self.device = dev
+        self.h_n_rows, self.h_n_cols, self.h_trip_ptr = _host_i64(n_rows), _host_i64(n_cols), _host_i64(trip_ptr)
+        if self.h_trip_ptr.numel() != self.h_n_rows.numel() + 1 or self.h_n_cols.numel() != self.h_n_rows.numel():
+            raise ValueError("n_rows and n_cols need one entry per matrix and trip_ptr one more")
+        self.d_n_rows, self.d_n_cols, self.d_trip_ptr = (t.to(dev) for t in (self.h_n_rows, self.h_n_cols,
+                                                                              self.h_trip_ptr))
+        self.B = self.h_n_rows.numel()
+        self.m = int(self.h_trip_ptr[-1]) if self.B else 0
+        self.dtype, self.mode = dtype, mode
+        self.flags = (SEQ_EXPLICIT if seq else 0) | (KEEP_MAP if keep_map else 0)
+        ws = spm_assemble_csc_batched_workspace(self.h_n_rows, self.h_n_cols, self.h_trip_ptr, dtype, mode,
+                                                self.flags)
+        self.workspace = torch.empty(ws, dtype=torch.uint8, device=dev)
+        self.col_ptr = torch.empty(int((self.h_n_cols + 1).sum()), dtype=torch.int64, device=dev)
+        self.row_idx = torch.empty(max(self.m, 1), dtype=torch.int32, device=dev)
+        self.out_vals = torch.empty(max(self.m, 1), dtype=dtype, device=dev)
+        self.d_nnz = torch.zeros(max(self.B, 1), dtype=torch.int64, device=dev)
+        self.d_status = torch.zeros(1, dtype=torch.int32, device=dev)
+        self.map = torch.empty(max(self.m, 1), dtype=torch.int32, device=dev) if keep_map else None
+
+    def run(self, rows, cols, vals, seq=None, stream=None):
+        if rows.numel() != self.m:
+            raise ValueError("stream length differs from the batch layout")
+        spm_assemble_csc_batched(self.h_n_rows, self.h_n_cols, self.h_trip_ptr, self.d_n_rows, self.d_n_cols,
+                                 self.d_trip_ptr, rows, cols, vals, seq, self.mode, self.flags, self.col_ptr,
+                                 self.row_idx, self.out_vals, self.d_nnz, self.map, self.d_status, self.workspace,
+                                 stream)
+
+    def result(self):
+        torch.cuda.current_stream().synchronize()
+        _raise_status(self.d_status, "spm_assemble_csc_batched")
+        return (self.col_ptr, self.row_idx[:self.m], self.out_vals[:self.m], self.d_nnz[:self.B],
+                self.map[:self.m] if self.map is not None else None)
 
 
 def assemble_csc(rows, cols, vals, shape, mode="set", seq=None, keep_map=False, stream=None):
@@ -528,14 +608,42 @@ def assemble_csc_batched(rows, cols, vals, n_rows, n_cols, trip_ptr, mode="set",
     return col_ptr, row_idx, out_vals, d_nnz[:hr.numel()], (mp[:total] if mp is not None else None)
 
 
-def csc_mm(col_ptr, row_idx, vals, shape, X, transpose=False, stream=None):
-    """Y = A X (or A^T X) for A in CSC; X row-major (inner stride 1)."""
+def csc_mm(col_ptr, row_idx, vals, shape, X, transpose=False, stream=None, check=True):
+    """Y = A X (or A^T X) for A in CSC; X row-major (inner stride 1).  Each
+    output row is gathered in a fixed order (the same bits on every call).
+    With ``check`` the call waits for the stream and raises on a malformed
+    matrix; without it nothing synchronises (A must be well formed)."""
     if X.stride(1) != 1:
         X = X.contiguous()
     out_rows = shape[1] if transpose else shape[0]
     Y = torch.empty((out_rows, X.shape[1]), dtype=X.dtype, device=X.device)
-    spm_csc_mm(shape[0], shape[1], col_ptr, row_idx, vals, transpose, X, Y, stream)
+    ws_bytes = spm_csc_mm_workspace(shape[0], shape[1], row_idx.numel(), vals.dtype, transpose)
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device=X.device) if ws_bytes else None
+    d_status = torch.zeros(1, dtype=torch.int32, device=X.device) if (check or not transpose) else None
+    spm_csc_mm(shape[0], shape[1], col_ptr, row_idx, vals, transpose, X, Y, d_status, ws, stream)
+    if check:
+        (stream or torch.cuda.current_stream()).synchronize()
+        _raise_status(d_status, "spm_csc_mm")
     return Y
+
+
+def csc_transpose(col_ptr, row_idx, vals, shape, stream=None):
+    """The CSC of A^T (shape (n_cols, n_rows)) from the CSC of A: a CSC tuple
+    whose row_idx holds A's column indices, increasing inside each column;
+    values carried over bit for bit."""
+    n_rows, n_cols = int(shape[0]), int(shape[1])
+    dev = vals.device
+    nnz = row_idx.numel()
+    ws = torch.empty(spm_csc_transpose_workspace(n_rows, n_cols, nnz, vals.dtype), dtype=torch.uint8, device=dev)
+    t_cp = torch.empty(n_rows + 1, dtype=torch.int64, device=dev)
+    t_ri = torch.empty(max(nnz, 1), dtype=torch.int32, device=dev)
+    t_v = torch.empty(max(nnz, 1), dtype=vals.dtype, device=dev)
+    d_status = torch.zeros(1, dtype=torch.int32, device=dev)
+    spm_csc_transpose(n_rows, n_cols, col_ptr, _as_index(row_idx, dev), vals.contiguous(), t_cp, t_ri, t_v, d_status,
+                      ws, stream)
+    (stream or torch.cuda.current_stream()).synchronize()
+    _raise_status(d_status, "spm_csc_transpose")
+    return CSC(t_cp, t_ri[:nnz], t_v[:nnz], nnz, None, (n_cols, n_rows))
 
 
 def triplet_dvals(rows, cols, map, dY, X, stream=None):
@@ -555,7 +663,9 @@ class AssembleMM(torch.autograd.Function):
     backward: dvals[t] = <dY[rows[t]], X[cols[t]]> for every write that feeds
     its element (in set mode only the last write; overwritten writes get 0,
     read from the kept map, or from a re-assembly when ``keep_map`` is False),
-    dX = A^T dY.
+    dX = A^T dY.  Both products are gathers in a fixed order: the forward
+    walks the columns of A^T (built once by csc_transpose), the backward those
+    of A, so every call gives the same bits.
     """
 
     @staticmethod
@@ -564,7 +674,8 @@ class AssembleMM(torch.autograd.Function):
         cols = _as_index(cols, vals.device)
         need_map = _mode_code(mode) == MODE_LAST_WRITE and keep_map
         A = assemble_csc(rows, cols, vals.detach(), shape, mode=mode, keep_map=need_map)
-        Y = csc_mm(A.col_ptr, A.row_idx, A.vals, shape, X.detach())
+        At = csc_transpose(A.col_ptr, A.row_idx, A.vals, shape)
+        Y = csc_mm(At.col_ptr, At.row_idx, At.vals, At.shape, X.detach(), transpose=True, check=False)
         ctx.save_for_backward(rows, cols, vals.detach(), X.detach(), A.col_ptr, A.row_idx, A.vals,
                               A.map if need_map else None)
         ctx.shape, ctx.mode = tuple(shape), mode
@@ -581,5 +692,5 @@ class AssembleMM(torch.autograd.Function):
                 mp = assemble_csc(rows, cols, vals, ctx.shape, mode=ctx.mode, keep_map=True).map
             dvals = triplet_dvals(rows, cols, mp if _mode_code(ctx.mode) == MODE_LAST_WRITE else None, dY, X)
         if ctx.needs_input_grad[4]:
-            dX = csc_mm(col_ptr, row_idx, avals, ctx.shape, dY, transpose=True)
+            dX = csc_mm(col_ptr, row_idx, avals, ctx.shape, dY, transpose=True, check=False)
         return None, None, dvals, None, dX, None, None

@@ -23,8 +23,9 @@
 namespace spm {
 namespace {
 
-// 32 MiB of scratch: enough for the workspace of roughly 0.75 million float64
-// writes (about 20 bytes per write plus the planner's tables).
+// 32 MiB of scratch: enough for the workspace of about 1.4 million writes
+// (a 16-byte record per write plus the planner's tables; streams that small
+// take the one-pass partition, which needs no second copy).
 constexpr size_t kStaticScratchBytes = size_t{32} << 20;
 
 __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];

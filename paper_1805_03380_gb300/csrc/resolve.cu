@@ -61,7 +61,6 @@ constexpr int kRI = 16;                     // sorted positions per thread at th
 constexpr int kRCap = kRT * kRI;            // writes of one bucket resolved in shared memory
 constexpr int kRCapNow = kRCap / 2;         // ... when the elements are staged in shared memory
 constexpr int kRBins = 1 << kSubBitsMax;    // sub-bins of the counting sort, at most
-constexpr uint32_t kRSmallSort = 64;        // largest sub-bin ordered by insertion
 constexpr uint16_t kKept = 0x8000u;         // perm[] flag: the run ending here is stored
 
 // Dynamic shared memory: records (the upper half doubles as the staging area
@@ -315,52 +314,29 @@ __device__ __forceinline__ uint64_t* res_vals(const Ctx& c, int64_t start, uint3
   return reinterpret_cast<uint64_t*>(reinterpret_cast<char*>(c.rec + start) + (((size_t)4 * n + 7) & ~size_t{7}));
 }
 
-// acc_round for results in the normal range, faster: the top 63 bits of the
-// magnitude with a sticky bit below them (set when any lower bit is) round
-// exactly like the whole, so the hardware's integer to floating-point
-// conversion (round to nearest even) gives the correctly rounded significand,
-// and scaling by a power of two is exact for a normal result.  Specials and
-// results near the subnormal or overflow range take acc_round.
-template <bool F64>
-__device__ __forceinline__ uint64_t acc_round_fast(const Acc& a, int emax, bool* nonzero) {
-  if (a.flags) return acc_round(a, emax, !F64, nonzero);
-  uint64_t lo = a.lo, hi = (uint64_t)a.hi;
-  const bool neg = a.hi < 0;
-  if (neg) {  // two's complement negate
-    lo = ~lo + 1ull;
-    hi = ~hi + (lo == 0ull ? 1ull : 0ull);
+// acc_add_bits without divergent branches for finite values (the lanes of a
+// warp add values of either sign and any exponent): the magnitude is aligned
+// and truncated in the same way, then added or, for a negative value,
+// subtracted as a two's complement 128-bit integer.  The same sum results.
+__device__ __forceinline__ void acc_add_fast(Acc& a, uint64_t bits, int emax) {
+  const uint32_t e = (uint32_t)(bits >> 52) & 0x7ffu;
+  const uint64_t frac = bits & 0xFFFFFFFFFFFFFull;
+  if (e == 0x7ffu) {  // NaN or infinity: a flag
+    a.flags |= frac ? 1u : ((bits >> 63) ? 4u : 2u);
+    return;
   }
-  if ((hi | lo) == 0ull) {
-    *nonzero = false;
-    return 0ull;
-  }
-  int u = (emax - kAlignBits) - 1075;  // value = magnitude * 2^u
-  uint64_t t;
-  if (hi == 0ull && (lo >> 63) == 0ull) {
-    t = lo;
-  } else {
-    const int msb = hi ? 127 - __clzll((long long)hi) : 63;
-    const int sh = msb - 62;  // 1..64: t = magnitude >> sh keeps 63 bits
-    bool sticky;
-    if (sh == 64) {
-      t = hi;
-      sticky = lo != 0ull;
-    } else {
-      t = (lo >> sh) | (hi << (64 - sh));
-      sticky = (lo & ((1ull << sh) - 1ull)) != 0ull;
-    }
-    t |= sticky ? 1ull : 0ull;
-    u += sh;
-  }
-  const int top = 63 - __clzll((long long)t) + u;  // exponent of the leading bit
-  if (F64 ? (top < -1021 || top > 1022) : (top < -125 || top > 126)) return acc_round(a, emax, !F64, nonzero);
-  *nonzero = true;
-  if (F64) {
-    double d = scalbn(__ll2double_rn((long long)t), u);
-    return (uint64_t)__double_as_longlong(neg ? -d : d);
-  }
-  float f = scalbnf(__ll2float_rn((long long)t), u);
-  return (uint64_t)__float_as_uint(neg ? -f : f);
+  const uint64_t mant = e ? (frac | (1ull << 52)) : frac;
+  const int sh = (int)max(e, 1u) - (emax - kAlignBits);  // <= kAlignBits
+  const uint32_t ls = (uint32_t)max(sh, 0);
+  const uint32_t rs = (uint32_t)min(max(-sh, 0), 63);
+  const uint64_t tlo = sh >= 0 ? (mant << ls) : (sh > -64 ? (mant >> rs) : 0ull);
+  const uint64_t thi = sh > 0 ? (mant >> (64u - ls)) : 0ull;
+  const uint64_t neg = (uint64_t)((int64_t)bits >> 63);  // all ones for a negative value
+  const uint64_t nlo = tlo ^ neg, lo1 = nlo + (neg & 1ull);
+  const uint64_t nhi = (thi ^ neg) + (lo1 < nlo ? 1ull : 0ull);
+  const uint64_t lo = a.lo + lo1;
+  a.hi = (int64_t)((uint64_t)a.hi + nhi + (lo < lo1 ? 1ull : 0ull));
+  a.lo = lo;
 }
 
 // Write the nnz stored elements of the key range R (get(li) gives the key
@@ -492,7 +468,8 @@ enum : int {
 
 // Resolve the n records R[0, n) of bucket D (keys relative to Rg.klo, in
 // [0, Rg.span)).  Returns the number of stored elements.  kNow needs
-// n <= kRCapNow.  Ends with a barrier.
+// n <= kRCapNow.  Ends with a barrier, except in kDefer mode (the caller's
+// next barrier ends every read of the shared arrays).
 template <bool F64, bool SUM, bool SEQ, bool MAP, class GetBase>
 __device__ __noinline__ uint32_t resolve_tile(const Ctx& c, RShared& S, unsigned char* smem, uint32_t n, const Desc& D,
                                  const Range& Rg, int mode, GetBase get_base) {
@@ -634,7 +611,9 @@ __device__ __noinline__ uint32_t resolve_tile(const Ctx& c, RShared& S, unsigned
   const uint32_t E = wid == kRW - 1 ? n : run_head_at((uint32_t)(((uint64_t)(wid + 1) * n) / kRW));
   // this lane's positions [a, e)
   const uint32_t len = E > A ? E - A : 0u;
-  const uint32_t qn = (len + 31) >> 5;
+  // (an odd strip length: the lanes' loads at the same offset in their
+  // strips fall in 32 different banks)
+  const uint32_t qn = ((len + 31) >> 5) | 1u;
   const uint32_t a = min(E, A + lane * qn), e = min(E, a + qn);
   const bool have = a < e;
   const bool head_a = have && (a == A || skey[a - 1] != skey[a]);
@@ -650,31 +629,50 @@ __device__ __noinline__ uint32_t resolve_tile(const Ctx& c, RShared& S, unsigned
     int run = 0, vf = 0;
     bool anyhead = false, multi = false;
     if (have) {
-      uint32_t kc = skey[a];
       bool h = head_a;
-      for (uint32_t p = a; p < e; ++p) {
-        const uint32_t kn = p + 1 < e ? skey[p + 1] : 0u;
-        const bool t = p + 1 == e ? tail_e : kn != kc;
-        const int ex = (h && t) ? 0 : align_exp<F64>(RV[2 * perm[p] + 1]);  // (a single write needs none)
-        run = h ? ex : max(run, ex);
-        if (ft == ~0u) vf = max(vf, ex);
-        anyhead = anyhead || h;
-        multi = multi || !(h && t);
-        if (t) {
-          rmax[p] = (uint16_t)run;
-          if (ft == ~0u) ft = p;
+      for (uint32_t p0 = a; p0 < e; p0 += 4) {  // four positions' loads in flight at once
+        uint32_t kq[5], iq[4];
+        uint64_t vq[4];
+#pragma unroll
+        for (int i = 0; i < 5; ++i) kq[i] = p0 + i < e ? skey[p0 + i] : 0u;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) iq[i] = p0 + i < e ? perm[p0 + i] : 0u;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) vq[i] = p0 + i < e ? RV[2 * iq[i] + 1] : 0ull;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const uint32_t p = p0 + i;
+          if (p < e) {
+            const bool t = p + 1 == e ? tail_e : kq[i + 1] != kq[i];
+            const int ex = (h && t) ? 0 : align_exp<F64>(vq[i]);  // (a single write needs none)
+            run = h ? ex : max(run, ex);
+            if (ft == ~0u) vf = max(vf, ex);
+            anyhead = anyhead || h;
+            multi = multi || !(h && t);
+            if (t) {
+              rmax[p] = (uint16_t)run;
+              if (ft == ~0u) ft = p;
+            }
+            h = t;
+          }
         }
-        h = t;
-        kc = kn;
       }
     }
     if (!__any_sync(kFull, multi)) {
       // every position of the warp is an element of its own: its value is the result
-      for (uint32_t p = a; p < e; ++p) {
-        const uint32_t ix = perm[p];
-        if (bits_nonzero<F64>(RV[2 * ix + 1])) {
-          perm[p] = (uint16_t)(ix | kKept);
-          ++nk;
+      for (uint32_t p0 = a; p0 < e; p0 += 4) {
+        uint32_t iq[4];
+        uint64_t vq[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) iq[i] = p0 + i < e ? perm[p0 + i] : 0u;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) vq[i] = p0 + i < e ? RV[2 * iq[i] + 1] : 0ull;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          if (p0 + i < e && bits_nonzero<F64>(vq[i])) {
+            perm[p0 + i] = (uint16_t)(iq[i] | kKept);
+            ++nk;
+          }
         }
       }
       goto numbered;
@@ -687,53 +685,70 @@ __device__ __noinline__ uint32_t resolve_tile(const Ctx& c, RShared& S, unsigned
     int G = 1, Gfirst = 1;
     uint32_t pt = 0;  // last position of the piece being summed
     if (have) {
-      uint32_t kn = 0;
-      for (uint32_t p = e; p-- > a;) {
-        const uint32_t kc = skey[p];
-        const bool t = p + 1 == e ? tail_e : kn != kc;
-        const bool h = p == a ? head_a : skey[p - 1] != kc;
-        const uint32_t ix = perm[p];
-        const uint64_t raw = RV[2 * ix + 1];
-        kn = kc;
-        if (p + 1 == e || t) {  // a piece ends at p
-          pt = p;
-          int pm = t ? (int)rmax[p] : max(run, inB);  // (run: pass 1's largest of the last piece)
-          if (cont_in && (t ? p == ft : ft == ~0u)) pm = max(pm, inF);
-          G = max(pm, 1);
-          acc = acc_zero();
+      for (uint32_t p1 = e; p1 > a;) {  // batches [p0, p1), walked backward, loads in flight at once
+        const uint32_t p0 = p1 - a >= 4u ? p1 - 4 : a;
+        uint32_t kq[6], iq[4];  // kq[i]: key at p0 - 1 + i
+        uint64_t vq[4];
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+          const uint32_t q = p0 - 1 + i;
+          kq[i] = (i > 0 || p0 > 0) && q < e && q <= p1 ? skey[q] : 0u;
         }
-        if (h && t) {  // a single write: its own value (already in place)
-          if (bits_nonzero<F64>(raw)) {
-            perm[p] = (uint16_t)(ix | kKept);
-            ++nk;
-          }
-          continue;
-        }
-        acc_add_bits(acc, wide<F64>(raw), G);
-        if (h || p == a) {  // the piece's first position
-          const bool has_tail = pt + 1 != e || tail_e;
-          if (!has_tail) {
-            alast = acc;  // continues in the next lane
-          } else if (!h) {
-            afirst = acc;  // continued from the lane before: finished after the scan
-            Gfirst = G;
-          } else {
-            bool nz;
-            const uint32_t it = perm[pt];
-            RVw[2 * it + 1] = acc_round_fast<F64>(acc, G, &nz);
-            if (nz) {
-              perm[pt] = (uint16_t)(it | kKept);
-              ++nk;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) iq[i] = p0 + i < p1 ? perm[p0 + i] : 0u;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) vq[i] = p0 + i < p1 ? RV[2 * iq[i] + 1] : 0ull;
+#pragma unroll
+        for (int i = 3; i >= 0; --i) {
+          const uint32_t p = p0 + i;
+          if (p < p1) {
+            const uint32_t kc = kq[i + 1];
+            const bool t = p + 1 == e ? tail_e : kq[i + 2] != kc;
+            const bool h = p == a ? head_a : kq[i] != kc;
+            const uint32_t ix = iq[i];
+            const uint64_t raw = vq[i];
+            if (p + 1 == e || t) {  // a piece ends at p
+              pt = p;
+              int pm = t ? (int)rmax[p] : max(run, inB);  // (run: pass 1's largest of the last piece)
+              if (cont_in && (t ? p == ft : ft == ~0u)) pm = max(pm, inF);
+              G = max(pm, 1);
+              acc = acc_zero();
+            }
+            if (h && t) {  // a single write: its own value (already in place)
+              if (bits_nonzero<F64>(raw)) {
+                perm[p] = (uint16_t)(ix | kKept);
+                ++nk;
+              }
+            } else {
+              acc_add_fast(acc, wide<F64>(raw), G);
+              if (h || p == a) {  // the piece's first position
+                const bool has_tail = pt + 1 != e || tail_e;
+                if (!has_tail) {
+                  alast = acc;  // continues in the next lane
+                } else if (!h) {
+                  afirst = acc;  // continued from the lane before: finished after the scan
+                  Gfirst = G;
+                } else {
+                  bool nz;
+                  const uint32_t it = perm[pt];
+                  RVw[2 * it + 1] = acc_round(acc, G, !F64, &nz);
+                  if (nz) {
+                    perm[pt] = (uint16_t)(it | kKept);
+                    ++nk;
+                  }
+                }
+              }
             }
           }
         }
+        p1 = p0;
       }
     }
     const AV inA = warp_seg_scan<true>(!have || anyhead, av_of(alast), AV{0, 0, 0}, OpAdd());
     if (cont_in && ft != ~0u) {
       bool nz;
       const uint32_t it = perm[ft];
-      RVw[2 * it + 1] = acc_round_fast<F64>(acc_of(av_add(inA, av_of(afirst))), Gfirst, &nz);
+      RVw[2 * it + 1] = acc_round(acc_of(av_add(inA, av_of(afirst))), Gfirst, !F64, &nz);
       if (nz) {
         perm[ft] = (uint16_t)(it | kKept);
         ++nk;
@@ -745,33 +760,44 @@ __device__ __noinline__ uint32_t resolve_tile(const Ctx& c, RShared& S, unsigned
     WV w{0, 0, 0, 0}, wfirst{0, 0, 0, 0};
     bool anyhead = false;
     if (have) {
-      uint32_t kc = skey[a];
       bool h = head_a;
-      for (uint32_t p = a; p < e; ++p) {
-        const uint32_t kn = p + 1 < e ? skey[p + 1] : 0u;
-        const bool t = p + 1 == e ? tail_e : kn != kc;
-        const uint32_t ix = perm[p];
-        const uint4 r = R[ix];
-        const uint64_t sq = SEQ ? __ldg(c.seq + r.y) : 0ull;
-        if (h) w.ok = 0;
-        const WV cand{sq, ((uint64_t)r.w << 32) | r.z, r.y, 1};
-        if (wv_better(w, cand)) w = cand;
-        anyhead = anyhead || h;
-        if (t) {
-          if (ft == ~0u && cont_in) {
-            wfirst = w;
-          } else {
-            RVw[2 * ix + 1] = w.val;
-            if (MAP) R[ix].x = w.pos;  // (the key field is free after the sort)
-            if (keep_zeros || bits_nonzero<F64>(w.val)) {
-              perm[p] = (uint16_t)(ix | kKept);
-              ++nk;
+      for (uint32_t p0 = a; p0 < e; p0 += 4) {  // four positions' loads in flight at once
+        uint32_t kq[5], iq[4];
+        uint4 rq[4];
+#pragma unroll
+        for (int i = 0; i < 5; ++i) kq[i] = p0 + i < e ? skey[p0 + i] : 0u;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) iq[i] = p0 + i < e ? perm[p0 + i] : 0u;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) rq[i] = p0 + i < e ? R[iq[i]] : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const uint32_t p = p0 + i;
+          if (p < e) {
+            const bool t = p + 1 == e ? tail_e : kq[i + 1] != kq[i];
+            const uint32_t ix = iq[i];
+            const uint4 r = rq[i];
+            const uint64_t sq = SEQ ? __ldg(c.seq + r.y) : 0ull;
+            if (h) w.ok = 0;
+            const WV cand{sq, ((uint64_t)r.w << 32) | r.z, r.y, 1};
+            if (wv_better(w, cand)) w = cand;
+            anyhead = anyhead || h;
+            if (t) {
+              if (ft == ~0u && cont_in) {
+                wfirst = w;
+              } else {
+                RVw[2 * ix + 1] = w.val;
+                if (MAP) R[ix].x = w.pos;  // (the key field is free after the sort)
+                if (keep_zeros || bits_nonzero<F64>(w.val)) {
+                  perm[p] = (uint16_t)(ix | kKept);
+                  ++nk;
+                }
+              }
+              if (ft == ~0u) ft = p;
             }
+            h = t;
           }
-          if (ft == ~0u) ft = p;
         }
-        h = t;
-        kc = kn;
       }
     }
     const WV inW = warp_seg_scan<true>(!have || anyhead, w, WV{0, 0, 0, 0}, OpWin());
@@ -810,19 +836,34 @@ numbered:
     return nnz;
   }
   if (mode == kDefer) {
+    // the warp's positions in lane order (consecutive stored elements go to
+    // consecutive words: coalesced stores, conflict-free shared loads)
     uint32_t* const dk = res_keys(c, D.start);
     uint64_t* const dv = res_vals(c, D.start, D.n);
-    uint32_t li = li0;
-    for (uint32_t p = a; p < e; ++p) {
-      const uint32_t ix = perm[p];
-      if (ix & kKept) {
-        dk[li] = skey[p];
-        dv[li] = RV[2 * (ix & 0x7fffu) + 1];
-        ++li;
+    uint32_t wl = woff;
+    for (uint32_t q0 = A; q0 < E; q0 += 64) {  // two positions per lane in flight
+      const uint32_t p = q0 + lane, p2 = p + 32;
+      const uint32_t ix = p < E ? perm[p] : 0u, ix2 = p2 < E ? perm[p2] : 0u;
+      const bool kept = (ix & kKept) != 0, kept2 = (ix2 & kKept) != 0;
+      const uint32_t k1 = kept ? skey[p] : 0u, k2 = kept2 ? skey[p2] : 0u;
+      const uint64_t v1 = kept ? RV[2 * (ix & 0x7fffu) + 1] : 0ull;
+      const uint64_t v2 = kept2 ? RV[2 * (ix2 & 0x7fffu) + 1] : 0ull;
+      const unsigned b1 = __ballot_sync(kFull, kept), b2 = __ballot_sync(kFull, kept2);
+      const unsigned lt = (1u << lane) - 1u;
+      if (kept) {
+        const uint32_t li = wl + __popc(b1 & lt);
+        dk[li] = k1;
+        dv[li] = v1;
       }
+      wl += __popc(b1);
+      if (kept2) {
+        const uint32_t li = wl + __popc(b2 & lt);
+        dk[li] = k2;
+        dv[li] = v2;
+      }
+      wl += __popc(b2);
     }
-    __syncthreads();
-    return nnz;
+    return nnz;  // (the caller's barrier ends every read of the shared arrays)
   }
   // ---- kNow: output index, the map, staging, placement
   OV inO{INT_MIN, 0};
@@ -868,14 +909,18 @@ numbered:
   uint32_t* const sk = reinterpret_cast<uint32_t*>(smem + L.stage_key);
   uint64_t* const sv = reinterpret_cast<uint64_t*>(smem + L.stage_val);
   {
-    uint32_t li = li0;
-    for (uint32_t p = a; p < e; ++p) {
-      const uint32_t ix = perm[p];
-      if (ix & kKept) {
+    uint32_t wl = woff;  // the warp's positions in lane order, as in kDefer
+    for (uint32_t q0 = A; q0 < E; q0 += 32) {
+      const uint32_t p = q0 + lane;
+      const uint32_t ix = p < E ? perm[p] : 0u;
+      const bool kept = (ix & kKept) != 0;
+      const unsigned b1 = __ballot_sync(kFull, kept);
+      if (kept) {
+        const uint32_t li = wl + __popc(b1 & ((1u << lane) - 1u));
         sk[li] = skey[p];
         sv[li] = RV[2 * (ix & 0x7fffu) + 1];
-        ++li;
       }
+      wl += __popc(b1);
     }
   }
   __syncthreads();
@@ -1066,18 +1111,13 @@ __device__ __noinline__ uint32_t resolve_windows(const Ctx& c, RShared& S, unsig
 constexpr int kHelper = kRT - 1;
 
 // Start the bulk copy of bucket D into the record area (thread 0; the
-// previous contents are dead) and warm L2 with the bucket one round ahead.
+// previous contents are dead).
 __device__ __forceinline__ void start_bucket(const Ctx& c, RShared& S, unsigned char* smem, const Desc& D,
-                                             uint32_t cap, uint32_t NB) {
+                                             uint32_t cap) {
   if (D.n > 0 && D.n <= cap) {
     fence_proxy_async();
     mbar_expect_tx(&S.bar, D.n * 16u);
     bulk_load(smem + rlay().R, c.rec + D.start, D.n * 16u, &S.bar);
-  }
-  const uint32_t ahead = D.b + gridDim.x;
-  if (ahead < NB) {
-    const uint32_t na = c.bk_count[ahead];
-    if (na <= cap) prefetch_l2(c.rec + c.bk_start[ahead], na * 16u);
   }
 }
 
@@ -1114,7 +1154,7 @@ __global__ void __launch_bounds__(kRT, 1) k_resolve(Ctx c) {
     S.cur.b = t;
     if (t < NB) {
       S.cur = load_desc(c, t);
-      start_bucket(c, S, smem, S.cur, cap, NB);
+      start_bucket(c, S, smem, S.cur, cap);
     }
   }
   __syncthreads();
@@ -1132,6 +1172,8 @@ __global__ void __launch_bounds__(kRT, 1) k_resolve(Ctx c) {
       if (next < NB) {
         nxt = load_desc(c, next);
         next = is_aborted(c) ? ~0u : atomicAdd(&c.scal->ticket, 1u);
+        // warm L2 with its records, a bucket's time before its bulk copy
+        if (nxt.n <= cap) prefetch_l2(c.rec + nxt.start, nxt.n * 16u);
       }
     }
     int64_t total = -1;  // set when the bucket is placed here
@@ -1220,7 +1262,7 @@ __global__ void __launch_bounds__(kRT, 1) k_resolve(Ctx c) {
     __syncthreads();      // the record area and the descriptors are free
     if (tid == 0) {
       S.cur = nxt;
-      if (S.cur.valid) start_bucket(c, S, smem, S.cur, cap, NB);
+      if (S.cur.valid) start_bucket(c, S, smem, S.cur, cap);
     }
     if (dead0) discard_lines(dead0, dead1);
     __syncthreads();

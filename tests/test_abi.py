@@ -104,8 +104,27 @@ def test_host_argument_validation_launches_nothing(spm):
     # KEEP_MAP without a map pointer
     assert L.spm_assemble_csc(10, 10, 0, null, null, null, null, 0, 0, 1, null, null, null, null, null, null, null,
                               0, null) == 1
-    assert L.spm_csc_mm(-1, 5, null, null, null, 0, 0, 4, null, 4, null, 4, null) == 1
-    assert L.spm_csc_mm(5, 5, null, null, null, 0, 2, 4, null, 4, null, 4, null) == 1
+    # spm_csc_mm(n_rows, n_cols, nnz, col_ptr, row_idx, vals, dtype, transpose, k, X, ldx, Y, ldy, d_status,
+    #            workspace, ws_bytes, stream)
+    assert L.spm_csc_mm(-1, 5, 0, null, null, null, 0, 0, 4, null, 4, null, 4, null, null, 0, null) == 1
+    assert L.spm_csc_mm(5, 5, 0, null, null, null, 0, 2, 4, null, 4, null, 4, null, null, 0, null) == 1
+    # A X needs a status word and the workspace; k = 0 or an empty output launches nothing
+    sz = ctypes.c_size_t(0)
+    assert L.spm_csc_mm_workspace(5, 6, 7, 0, 1, ctypes.byref(sz)) == 0 and sz.value == 0
+    assert L.spm_csc_mm_workspace(5, 6, 7, 0, 0, ctypes.byref(sz)) == 0 and sz.value > 7 * 4
+    assert L.spm_csc_mm_workspace(5, 6, 7, 0, 3, ctypes.byref(sz)) == 1
+    assert L.spm_csc_mm(5, 6, 7, 8, 8, 8, 0, 0, 4, 8, 4, 8, 4, null, 8, sz.value, null) == 1
+    assert L.spm_csc_mm(5, 6, 7, 8, 8, 8, 0, 0, 4, 8, 4, 8, 4, 8, null, 0, null) == 3
+    assert L.spm_csc_mm(5, 6, 7, 8, 8, 8, 0, 0, 4, 8, 4, 8, 4, 8, 8, sz.value - 1, null) == 3
+    assert L.spm_csc_mm(5, 6, 7, null, null, null, 0, 1, 0, null, 0, null, 0, null, null, 0, null) == 0
+    # spm_csc_transpose(n_rows, n_cols, nnz, col_ptr, row_idx, vals, dtype, t_col_ptr, t_row_idx, t_vals,
+    #                   d_status, workspace, ws_bytes, stream)
+    assert L.spm_csc_transpose_workspace(5, 6, -1, 0, ctypes.byref(sz)) == 1
+    assert L.spm_csc_transpose_workspace(5, 6, 7, 2, ctypes.byref(sz)) == 1
+    assert L.spm_csc_transpose_workspace(5, 6, 7, 1, ctypes.byref(sz)) == 0 and sz.value >= 7 * 4
+    assert L.spm_csc_transpose(5, 6, 7, 8, 8, 8, 1, 8, 8, 8, null, 8, sz.value, null) == 1
+    assert L.spm_csc_transpose(5, 6, 7, 8, null, 8, 1, 8, 8, 8, 8, 8, sz.value, null) == 1
+    assert L.spm_csc_transpose(5, 6, 7, 8, 8, 8, 1, 8, 8, 8, 8, 8, sz.value - 1, null) == 3
     assert L.spm_triplet_dvals(-3, null, null, null, 0, 4, null, 4, null, 4, null, null) == 1
     assert L.spm_triplet_dvals(0, null, null, null, 0, 4, null, 4, null, 4, null, null) == 0
     del args

@@ -120,3 +120,87 @@ def test_batched_mismatched_device_sizes_reported():
                                  out["d_nnz"], None, out["d_status"], torch.empty(ws, dtype=torch.uint8, device=dev))
     torch.cuda.synchronize()
     assert int(out["d_status"].item()) == 1
+
+
+def _redraw(d, seed, dtype):
+    """New writes for the same batch layout: the same sizes and write counts,
+    new coordinates, values and rewrites."""
+    rng = np.random.default_rng(seed)
+    n, tp = np.asarray(d["n"], np.int64), np.asarray(d["trip_ptr"], np.int64)
+    cnt = np.diff(tp)
+    lim = np.repeat(n, cnt)
+    rows = (rng.random(int(tp[-1])) * lim).astype(np.int32)
+    cols = (rng.random(int(tp[-1])) * lim).astype(np.int32)
+    # about 10 % rewrites of an earlier coordinate of the same matrix
+    rep = np.nonzero(rng.random(int(tp[-1])) < 0.1)[0]
+    start = np.repeat(tp[:-1], cnt)[rep]
+    src = start + (rng.random(len(rep)) * (rep - start + 1)).astype(np.int64)
+    rows[rep], cols[rep] = rows[src], cols[src]
+    vals = rng.standard_normal(int(tp[-1])).astype(dtype)
+    return rows, cols, vals
+
+
+@pytest.mark.parametrize("mode", ["set", "sum"])
+def test_batched_cuda_graph_capture_and_replay(mode):
+    # capture one batched call in a CUDA graph, replay it on new writes of the
+    # same layout, and compare every matrix with the oracle after each replay
+    import paper_1805_03380_gb300 as spm
+    d = workloads.batched_uniform(batch=48, n_min=64, n_max=900, seed=workloads.SEED_BASE + 44)
+    n, tp = np.asarray(d["n"], np.int64), np.asarray(d["trip_ptr"], np.int64)
+    dtype = np.float64 if mode == "sum" else np.float32
+    first = _redraw(d, 1, dtype)
+    rows, cols, vals = (to_dev(a) for a in first)
+    asm = spm.BatchedAssembler(n, n, tp, dtype=vals.dtype, mode=mode)
+    asm.run(rows, cols, vals)  # first call on the device (sets kernel attributes)
+    asm.result()
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            asm.run(rows, cols, vals, stream=s)
+    for seed in (2, 3):
+        r, c, v = _redraw(d, seed, dtype)
+        rows.copy_(to_dev(r))
+        cols.copy_(to_dev(c))
+        vals.copy_(to_dev(v))
+        g.replay()
+        torch.cuda.synchronize()
+        cp, ri, ov, nnz, _ = asm.result()
+        cp, ri, ov, nnz = cp.cpu().numpy(), ri.cpu().numpy(), ov.cpu().numpy(), nnz.cpu().numpy()
+        cbase = 0
+        for i in range(len(n)):
+            a, b = int(tp[i]), int(tp[i + 1])
+            shape = (int(n[i]), int(n[i]))
+            wc, wr, wv = oracle.assemble_csc(r[a:b], c[a:b], v[a:b], shape, mode=mode)
+            k = int(nnz[i])
+            assert k == len(wr), f"replay {seed}, matrix {i}"
+            np.testing.assert_array_equal(cp[cbase:cbase + shape[1] + 1], wc)
+            np.testing.assert_array_equal(ri[a:a + k], wr)
+            if mode == "set":
+                assert_bit_exact(ov[a:a + k], wv.astype(dtype))
+            else:
+                scale = abs_contrib_per_entry(r[a:b], c[a:b], v[a:b], shape, wc, wr)
+                assert_sum_within_tol(ov[a:a + k], wv, scale, dtype)
+            cbase += shape[1] + 1
+
+
+def test_batched_autotune_cache_and_identical_results(tmp_path):
+    import json
+
+    import paper_1805_03380_gb300 as spm
+    from paper_1805_03380_gb300 import autotune as at
+    spm.spm_set_tuning(reset=True)
+    t0 = spm.spm_get_tuning()
+    d = workloads.batched_uniform(batch=64, n_min=64, n_max=2000, seed=workloads.SEED_BASE + 45)
+    n, tp = np.asarray(d["n"], np.int64), np.asarray(d["trip_ptr"], np.int64)
+    p = str(tmp_path / "tune.json")
+    cands = [dict(bucket_target=4096, sub_bits=11), dict(bucket_target=7168, partition_threads=512)]
+    best = at.autotune_batched(to_dev(d["rows"]), to_dev(d["cols"]), to_dev(d["vals"]), n, n, tp, "set",
+                               candidates=cands, reps=3, warmup=2, path=p, apply=False)
+    # every candidate gives the default tuning's bytes
+    assert best["tried"] == 2 and best["rejected"] == []
+    assert spm.spm_get_tuning() == t0
+    key = at.batch_cache_key(n, n, tp, torch.float32, "set")
+    assert json.load(open(p))[key]["tuning"] == best["tuning"]
+    assert at.apply_cached_batched(n, n, tp, torch.float32, "set", path=p) == best["tuning"]
+    spm.spm_set_tuning(reset=True)
