@@ -62,6 +62,9 @@ constexpr int kRCap = kRT * kRI;            // writes of one bucket resolved in 
 constexpr int kRCapNow = kRCap / 2;         // ... when the elements are staged in shared memory
 constexpr int kRBins = 1 << kSubBitsMax;    // sub-bins of the counting sort, at most
 constexpr uint16_t kKept = 0x8000u;         // perm[] flag: the run ending here is stored
+constexpr uint16_t kMulti = 0x4000u;        // perm[] flag: a run of several writes ends here, its
+                                            // accumulator is parked (rounded later)
+constexpr uint16_t kIdx = 0x1fffu;          // perm[] bits of the record index (< kRCap)
 
 // Dynamic shared memory: records (the upper half doubles as the staging area
 // of elements placed at once), sorted keys, sorted record indices, sub-bin
@@ -284,6 +287,7 @@ struct RShared {
   uint32_t kkeep, kwin;
   int kmax;
   alignas(16) unsigned char parts[kRW * 32];  // per warp partial of a single key
+  uint16_t ring[kRW][64];  // per warp: positions of parked runs waiting to be rounded
   uint64_t bar;       // mbarrier of the bulk copy
 };
 
@@ -553,16 +557,28 @@ __device__ __noinline__ uint32_t resolve_tile(const Ctx& c, RShared& S, unsigned
           perm[y] = pv;
         }
       }
+      // A heavy sub-bin is sorted together with the sub-bins after it, up to
+      // 64 positions, as long as those hold at most one write or are heavy
+      // too (sub-bins of 2..8 are the threads' above): the sub-bins are in key
+      // order, so sorting a window of whole sub-bins sorts each of them.
       for (uint32_t q0 = (uint32_t)wid * 32u; q0 < nbins; q0 += (uint32_t)kRW * 32u) {
         const uint32_t q = q0 + lane;
-        const bool heavy = q < nbins && bins[q + 1] - bins[q] > 8u;
-        unsigned hv = __ballot_sync(kFull, heavy);
+        const uint32_t qa = q < nbins ? bins[q] : n, qe = q < nbins ? bins[q + 1] : n;
+        const uint32_t sz = qe - qa;
+        unsigned hv = __ballot_sync(kFull, sz > 8u);
+        const unsigned mid = __ballot_sync(kFull, (sz >= 2u && sz <= 8u) || q >= nbins);
         while (hv) {
           const int L = __ffs(hv) - 1;
-          hv &= hv - 1;
-          const uint32_t a = bins[q0 + L], k = bins[q0 + L + 1] - a;
-          if (k <= 32u) warp_sort32(skey + a, perm + a, k);
-          else warp_sort64(skey + a, perm + a, k);
+          const uint32_t P = __shfl_sync(kFull, qa, L);
+          // the window ends before the first thread-sorted sub-bin after L or
+          // the first sub-bin that ends beyond P + 64
+          const unsigned after = ~((2u << L) - 1u);
+          const unsigned stop = (mid | __ballot_sync(kFull, qe > P + 64u)) & after;
+          const int M = (stop ? __ffs(stop) - 1 : 32) - 1;
+          const uint32_t B = __shfl_sync(kFull, qe, M);
+          if (B - P <= 32u) warp_sort32(skey + P, perm + P, B - P);
+          else warp_sort64(skey + P, perm + P, B - P);
+          hv &= M >= 31 ? 0u : ~((2u << M) - 1u);
         }
       }
     } else {
@@ -680,7 +696,20 @@ __device__ __noinline__ uint32_t resolve_tile(const Ctx& c, RShared& S, unsigned
     {
     const int inF = warp_seg_scan<true>(!have || anyhead, EV{run}, EV{0}, OpMax()).e;
     const int inB = warp_seg_scan<false>(!have || ft != ~0u, EV{vf}, EV{0}, OpMax()).e;
-    // pass 2 (backward): exact sums with each run's own binary point
+    // pass 2 (backward): exact sums with each run's own binary point.  A run
+    // of several writes leaves its accumulator parked at its last position
+    // (the slot of that position's record, or for calls with the map, whose
+    // records stay in use, a slot per position in the free upper half of the
+    // record area), its binary point and flags in rmax; all lanes round the
+    // parked runs together afterwards instead of each at its own time.
+    uint4* const park = MAP ? reinterpret_cast<uint4*>(smem + L.stage_key) : R;
+    auto park_run = [&](uint32_t pos, const Acc& x, int g) {
+      const uint32_t ix = perm[pos];
+      park[MAP ? pos : (ix & kIdx)] = make_uint4((uint32_t)x.lo, (uint32_t)(x.lo >> 32), (uint32_t)x.hi,
+                                                 (uint32_t)((uint64_t)x.hi >> 32));
+      rmax[pos] = (uint16_t)(g | (int)(x.flags << 12));  // g <= 2046
+      perm[pos] = (uint16_t)(ix | kMulti);
+    };
     Acc acc = acc_zero(), afirst = acc_zero(), alast = acc_zero();
     int G = 1, Gfirst = 1;
     uint32_t pt = 0;  // last position of the piece being summed
@@ -729,13 +758,7 @@ __device__ __noinline__ uint32_t resolve_tile(const Ctx& c, RShared& S, unsigned
                   afirst = acc;  // continued from the lane before: finished after the scan
                   Gfirst = G;
                 } else {
-                  bool nz;
-                  const uint32_t it = perm[pt];
-                  RVw[2 * it + 1] = acc_round(acc, G, !F64, &nz);
-                  if (nz) {
-                    perm[pt] = (uint16_t)(it | kKept);
-                    ++nk;
-                  }
+                  park_run(pt, acc, G);
                 }
               }
             }
@@ -745,14 +768,46 @@ __device__ __noinline__ uint32_t resolve_tile(const Ctx& c, RShared& S, unsigned
       }
     }
     const AV inA = warp_seg_scan<true>(!have || anyhead, av_of(alast), AV{0, 0, 0}, OpAdd());
-    if (cont_in && ft != ~0u) {
-      bool nz;
-      const uint32_t it = perm[ft];
-      RVw[2 * it + 1] = acc_round(acc_of(av_add(inA, av_of(afirst))), Gfirst, !F64, &nz);
-      if (nz) {
-        perm[ft] = (uint16_t)(it | kKept);
-        ++nk;
+    if (cont_in && ft != ~0u) park_run(ft, acc_of(av_add(inA, av_of(afirst))), Gfirst);
+    __syncwarp();
+    // round the parked runs of the warp's positions, up to 32 at once
+    uint16_t* const rq = S.ring[wid];
+    uint32_t pend = 0, head = 0, mk = 0;
+    const unsigned lt = (1u << lane) - 1u;
+    auto round_parked = [&](uint32_t cnt) {
+      bool kept = false;
+      if ((uint32_t)lane < cnt) {
+        const uint32_t p = rq[(head + lane) & 63u];
+        const uint32_t ix = perm[p] & kIdx;
+        const uint4 sl = park[MAP ? p : ix];
+        const uint32_t gf = rmax[p];
+        const Acc x{((uint64_t)sl.y << 32) | sl.x, (int64_t)(((uint64_t)sl.w << 32) | sl.z), gf >> 12};
+        bool nz;
+        RVw[2 * ix + 1] = acc_round(x, (int)(gf & 0xfffu), !F64, &nz);
+        perm[p] = (uint16_t)(ix | (nz ? kKept : 0u));
+        kept = nz;
       }
+      mk += __popc(__ballot_sync(kFull, kept));
+      head += cnt;
+      pend -= cnt;
+      __syncwarp();
+    };
+    for (uint32_t q0 = A; q0 < E; q0 += 32) {
+      const uint32_t p = q0 + lane;
+      const bool m = p < E && (perm[p] & kMulti);
+      const unsigned bal = __ballot_sync(kFull, m);
+      if (m) rq[(head + pend + __popc(bal & lt)) & 63u] = (uint16_t)p;
+      pend += __popc(bal);
+      __syncwarp();
+      if (pend >= 32u) round_parked(32u);
+    }
+    if (pend) round_parked(pend);
+    if (MAP) {
+      // the lane's own count, for the positional map below
+      nk = 0;
+      for (uint32_t p = a; p < e; ++p) nk += (perm[p] & kKept) ? 1u : 0u;
+    } else if (lane == 0) {
+      nk += mk;  // (only the warp's total is used without the map)
     }
     }
   } else {
@@ -846,8 +901,8 @@ numbered:
       const uint32_t ix = p < E ? perm[p] : 0u, ix2 = p2 < E ? perm[p2] : 0u;
       const bool kept = (ix & kKept) != 0, kept2 = (ix2 & kKept) != 0;
       const uint32_t k1 = kept ? skey[p] : 0u, k2 = kept2 ? skey[p2] : 0u;
-      const uint64_t v1 = kept ? RV[2 * (ix & 0x7fffu) + 1] : 0ull;
-      const uint64_t v2 = kept2 ? RV[2 * (ix2 & 0x7fffu) + 1] : 0ull;
+      const uint64_t v1 = kept ? RV[2 * (ix & kIdx) + 1] : 0ull;
+      const uint64_t v2 = kept2 ? RV[2 * (ix2 & kIdx) + 1] : 0ull;
       const unsigned b1 = __ballot_sync(kFull, kept), b2 = __ballot_sync(kFull, kept2);
       const unsigned lt = (1u << lane) - 1u;
       if (kept) {
@@ -874,7 +929,7 @@ numbered:
     if (ft != ~0u) {
       const uint32_t it = perm[ft];
       mine.out = (it & kKept) ? (int32_t)li0 : -2;
-      mine.win = SUM ? 0u : R[it & 0x7fffu].x;
+      mine.win = SUM ? 0u : R[it & kIdx].x;
     }
     inO = warp_seg_scan<false>(!have || ft != ~0u, mine, OV{INT_MIN, 0}, OpNear());
   }
@@ -893,7 +948,7 @@ numbered:
     for (uint32_t p = e; p-- > a;) {
       const uint32_t ix = perm[p];
       const bool t = p + 1 == e ? tail_e : skey[p + 1] != skey[p];
-      const uint4 r = R[ix & 0x7fffu];
+      const uint4 r = R[ix & kIdx];
       if (t) {
         if (ix & kKept) {
           --li;
@@ -918,7 +973,7 @@ numbered:
       if (kept) {
         const uint32_t li = wl + __popc(b1 & ((1u << lane) - 1u));
         sk[li] = skey[p];
-        sv[li] = RV[2 * (ix & 0x7fffu) + 1];
+        sv[li] = RV[2 * (ix & kIdx) + 1];
       }
       wl += __popc(b1);
     }
