@@ -322,13 +322,11 @@ __device__ __forceinline__ uint64_t* res_vals(const Ctx& c, int64_t start, uint3
 // warp add values of either sign and any exponent): the magnitude is aligned
 // and truncated in the same way, then added or, for a negative value,
 // subtracted as a two's complement 128-bit integer.  The same sum results.
-__device__ __forceinline__ void acc_add_fast(Acc& a, uint64_t bits, int emax) {
+// The 128-bit two's complement fixed-point value of the finite float64 `bits`
+// with the binary point of exponent emax (as acc_add_bits aligns it).
+__device__ __forceinline__ void fixed_of(uint64_t bits, int emax, uint64_t& xlo, uint64_t& xhi) {
   const uint32_t e = (uint32_t)(bits >> 52) & 0x7ffu;
   const uint64_t frac = bits & 0xFFFFFFFFFFFFFull;
-  if (e == 0x7ffu) {  // NaN or infinity: a flag
-    a.flags |= frac ? 1u : ((bits >> 63) ? 4u : 2u);
-    return;
-  }
   const uint64_t mant = e ? (frac | (1ull << 52)) : frac;
   const int sh = (int)max(e, 1u) - (emax - kAlignBits);  // <= kAlignBits
   const uint32_t ls = (uint32_t)max(sh, 0);
@@ -336,10 +334,21 @@ __device__ __forceinline__ void acc_add_fast(Acc& a, uint64_t bits, int emax) {
   const uint64_t tlo = sh >= 0 ? (mant << ls) : (sh > -64 ? (mant >> rs) : 0ull);
   const uint64_t thi = sh > 0 ? (mant >> (64u - ls)) : 0ull;
   const uint64_t neg = (uint64_t)((int64_t)bits >> 63);  // all ones for a negative value
-  const uint64_t nlo = tlo ^ neg, lo1 = nlo + (neg & 1ull);
-  const uint64_t nhi = (thi ^ neg) + (lo1 < nlo ? 1ull : 0ull);
-  const uint64_t lo = a.lo + lo1;
-  a.hi = (int64_t)((uint64_t)a.hi + nhi + (lo < lo1 ? 1ull : 0ull));
+  const uint64_t nlo = tlo ^ neg;
+  xlo = nlo + (neg & 1ull);
+  xhi = (thi ^ neg) + (xlo < nlo ? 1ull : 0ull);
+}
+
+__device__ __forceinline__ void acc_add_fast(Acc& a, uint64_t bits, int emax) {
+  const uint32_t e = (uint32_t)(bits >> 52) & 0x7ffu;
+  if (e == 0x7ffu) {  // NaN or infinity: a flag
+    a.flags |= (bits & 0xFFFFFFFFFFFFFull) ? 1u : ((bits >> 63) ? 4u : 2u);
+    return;
+  }
+  uint64_t xlo, xhi;
+  fixed_of(bits, emax, xlo, xhi);
+  const uint64_t lo = a.lo + xlo;
+  a.hi = (int64_t)((uint64_t)a.hi + xhi + (lo < xlo ? 1ull : 0ull));
   a.lo = lo;
 }
 
@@ -458,6 +467,119 @@ __device__ __forceinline__ void warp_sort64(uint32_t* keys, uint16_t* idx, uint3
     keys[lane + 32] = (uint32_t)(x1 >> 16);
     idx[lane + 32] = (uint16_t)x1;
   }
+}
+
+// ---------------------------------------------------------------------------
+// A bucket whose key range is narrow: one table slot per key
+// ---------------------------------------------------------------------------
+// When a bucket's keys span at most kDense values (the crowded columns of a
+// skewed stream, where many writes share few keys), the records are reduced
+// into a table indexed by the key itself, with shared-memory atomics, and no
+// sort is needed: the table is already in key order.  Sum mode: pass 1 takes
+// each key's largest exponent (atomic max), pass 2 adds every write's
+// fixed-point value at that binary point into the key's 128-bit slot (two
+// 64-bit atomic adds, the carry of the low word passed to the high one:
+// integer addition, so the order of the adds does not matter) -- the same
+// integer the run reduction forms, hence the same rounded sum.  Last-write
+// mode (positions only): the largest position per key, then its value.  The
+// table lies in the shared arrays that the sort would use; the records stay
+// untouched, so a sum bucket holding a NaN or an infinity returns kDenseNo
+// and is resolved by resolve_tile.
+constexpr uint32_t kDense = 3072;      // table slots (20 bytes each in sum mode)
+constexpr uint32_t kDenseNo = ~0u;
+
+template <bool F64, bool SUM>
+__device__ __noinline__ uint32_t resolve_dense(const Ctx& c, RShared& S, unsigned char* smem, uint32_t n,
+                                               const Desc& D) {
+  constexpr RLay L = rlay();
+  const uint4* const R = reinterpret_cast<const uint4*>(smem + L.R);
+  uint32_t* const tag = reinterpret_cast<uint32_t*>(smem + L.skey);  // 1 + largest exponent / 1 + position
+  uint64_t* const tlo = reinterpret_cast<uint64_t*>(smem + L.skey + 4 * kDense);  // low words / values
+  uint64_t* const thi = tlo + kDense;                                              // high words (sum)
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const uint32_t span = (uint32_t)D.rg.span;
+  for (uint32_t q = tid; q < span; q += kRT) {
+    tag[q] = 0u;
+    tlo[q] = 0ull;
+    if (SUM) thi[q] = 0ull;
+  }
+  __syncthreads();
+  bool odd = false;
+  for (uint32_t i = tid; i < n; i += kRT) {
+    const uint4 r = R[i];
+    if (SUM) {
+      const uint64_t w = wide<F64>(((uint64_t)r.w << 32) | r.z);
+      odd |= ((w >> 52) & 0x7ffu) == 0x7ffu;
+      atomicMax(&tag[r.x], (uint32_t)align_exp<F64>(((uint64_t)r.w << 32) | r.z) + 1u);
+    } else {
+      atomicMax(&tag[r.x], r.y + 1u);
+    }
+  }
+  if (SUM) {
+    if (__syncthreads_or(odd)) return kDenseNo;
+  } else {
+    __syncthreads();
+  }
+  for (uint32_t i = tid; i < n; i += kRT) {
+    const uint4 r = R[i];
+    const uint64_t raw = ((uint64_t)r.w << 32) | r.z;
+    if (SUM) {
+      const int G = max((int)tag[r.x] - 1, 1);
+      uint64_t xlo, xhi;
+      fixed_of(wide<F64>(raw), G, xlo, xhi);
+      const unsigned long long old = atomicAdd(reinterpret_cast<unsigned long long*>(&tlo[r.x]), xlo);
+      atomicAdd(reinterpret_cast<unsigned long long*>(&thi[r.x]), xhi + ((uint64_t)old + xlo < xlo ? 1ull : 0ull));
+    } else if (r.y + 1u == tag[r.x]) {
+      tlo[r.x] = raw;
+    }
+  }
+  __syncthreads();
+  // results: each warp a contiguous share of the slots, counted, then written
+  // in key order with coalesced stores over the bucket's records
+  const bool keep_zeros = !SUM && c.keep_zeros;
+  const uint32_t per = ((span + kRW - 1) / kRW + 31) & ~31u;
+  const uint32_t s0 = min(span, (uint32_t)wid * per), s1 = min(span, s0 + per);
+  uint32_t cnt = 0;
+  for (uint32_t q0 = s0; q0 < s1; q0 += 32) {
+    const uint32_t q = q0 + lane;
+    bool kept = false;
+    if (q < s1 && tag[q] != 0u) {
+      if (SUM) {
+        bool nz;
+        const Acc x{tlo[q], (int64_t)thi[q], 0u};
+        tlo[q] = acc_round(x, max((int)tag[q] - 1, 1), !F64, &nz);
+        kept = nz;
+      } else {
+        kept = keep_zeros || bits_nonzero<F64>(tlo[q]);
+      }
+      if (!kept) tag[q] = 0u;
+    }
+    cnt += __popc(__ballot_sync(kFull, kept));
+  }
+  if (lane == 0) S.wk[wid] = cnt;
+  __syncthreads();
+  uint32_t wl = 0, nnz = 0;
+#pragma unroll
+  for (int w2 = 0; w2 < kRW; ++w2) {
+    const uint32_t x = S.wk[w2];
+    wl += w2 < wid ? x : 0u;
+    nnz += x;
+  }
+  uint32_t* const dk = res_keys(c, D.start);
+  uint64_t* const dv = res_vals(c, D.start, D.n);
+  const unsigned lt = (1u << lane) - 1u;
+  for (uint32_t q0 = s0; q0 < s1; q0 += 32) {
+    const uint32_t q = q0 + lane;
+    const bool kept = q < s1 && tag[q] != 0u;
+    const unsigned b = __ballot_sync(kFull, kept);
+    if (kept) {
+      const uint32_t li = wl + __popc(b & lt);
+      dk[li] = q;
+      dv[li] = tlo[q];
+    }
+    wl += __popc(b);
+  }
+  return nnz;  // (the caller's barrier ends every read of the shared arrays)
 }
 
 // ---------------------------------------------------------------------------
@@ -1301,9 +1423,13 @@ __global__ void __launch_bounds__(kRT, 1) k_resolve(Ctx c) {
         total = S.base + nnz;
       } else {
         // the elements wait over the bucket's records for k_place
-        const uint32_t nnz = resolve_tile<F64, SUM, SEQ, MAP>(c, S, smem, D.n, D, D.rg, kDefer, [](uint32_t) {
-          return int64_t{0};
-        });
+        uint32_t nnz = kDenseNo;
+        if (!SEQ && D.rg.span <= kDense) nnz = resolve_dense<F64, SUM>(c, S, smem, D.n, D);
+        if (nnz == kDenseNo) {
+          nnz = resolve_tile<F64, SUM, SEQ, MAP>(c, S, smem, D.n, D, D.rg, kDefer, [](uint32_t) {
+            return int64_t{0};
+          });
+        }
         if (tid == 0) c.bk_nnz[D.b] = nnz;
         dead0 = res_vals(c, D.start, D.n) + nnz;
       }

@@ -148,3 +148,53 @@ def test_long_runs_across_lanes_and_warps(dtype):
     d = dict(rows=np.array(rows, dtype=np.int32)[order], cols=np.array(cols, dtype=np.int32)[order],
              vals=np.array(vals, dtype=dtype)[order], shape=(100, 50))
     _compare(d, dtype)
+
+
+def _narrow_stream(dtype, seed, m=40_000, n_rows=2000):
+    """m writes into an n_rows x 1 matrix: every bucket's key range is narrow
+    (the direct-addressed table path); values of wide dynamic range."""
+    rng = np.random.default_rng(seed)
+    rows = rng.integers(0, n_rows, m).astype(np.int32)
+    vals = (rng.standard_normal(m) * np.exp(rng.uniform(-20, 20, m))).astype(dtype)
+    vals[rng.random(m) < 0.02] = 0.0
+    return dict(rows=rows, cols=np.zeros(m, np.int32), vals=vals, shape=(n_rows, 1))
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_narrow_buckets_table_path_matches_exact_and_sorted_path(dtype):
+    # the table path (narrow key ranges) against the exact sums and the oracle,
+    # and bit for bit against the same elements spread over a key range wide
+    # enough that the sort path resolves them
+    d = _narrow_stream(dtype, 21)
+    got = _compare(d, dtype)
+    wide = dict(rows=d["rows"] * 997, cols=d["cols"], vals=d["vals"], shape=(2000 * 997, 1))
+    g2 = gpu_assemble(wide, "sum")
+    assert np.array_equal(got[0], g2[0])
+    np.testing.assert_array_equal(got[1] * 997, g2[1])
+    assert got[2].tobytes() == g2[2].tobytes()
+
+
+def test_narrow_buckets_with_nan_and_infinity_fall_back():
+    d = _narrow_stream(np.float64, 22, m=20_000)
+    d["vals"][5] = np.nan
+    d["vals"][17] = np.inf
+    d["vals"][18] = -np.inf
+    got = gpu_assemble(d, "sum")
+    want = oracle.assemble_csc(d["rows"], d["cols"], d["vals"], d["shape"], mode="sum")
+    assert_same_structure(got, want)
+    both_nan = np.isnan(got[2]) & np.isnan(want[2])
+    fin = ~both_nan
+    assert np.array_equal(np.isnan(got[2]), np.isnan(want[2]))
+    scale = abs_contrib_per_entry(d["rows"], d["cols"], np.nan_to_num(d["vals"], nan=0.0, posinf=0.0, neginf=0.0),
+                                  d["shape"], want[0], want[1])
+    g, w = got[2][fin], want[2][fin]
+    ok = (g == w) | (np.abs(g - w) <= 1e-12 * scale[fin])
+    assert np.all(ok)
+
+
+def test_narrow_buckets_last_write_bit_exact():
+    d = _narrow_stream(np.float64, 23)
+    got = gpu_assemble(d, "set")
+    want = oracle.assemble_csc(d["rows"], d["cols"], d["vals"], d["shape"], mode="set")
+    assert_same_structure(got, want)
+    assert got[2].tobytes() == want[2].tobytes()
