@@ -477,8 +477,8 @@ __device__ __forceinline__ void warp_sort64(uint32_t* keys, uint16_t* idx, uint3
 // into a table indexed by the key itself, with shared-memory atomics, and no
 // sort is needed: the table is already in key order.  Sum mode: pass 1 takes
 // each key's largest exponent (atomic max), pass 2 adds every write's
-// fixed-point value at that binary point into the key's 128-bit slot (two
-// 64-bit atomic adds, the carry of the low word passed to the high one:
+// fixed-point value at that binary point into the key's 128-bit slot (four
+// 32-bit limbs updated by native shared-memory atomics with exact carries:
 // integer addition, so the order of the adds does not matter) -- the same
 // integer the run reduction forms, hence the same rounded sum.  Last-write
 // mode (positions only): the largest position per key, then its value.  The
@@ -494,15 +494,14 @@ __device__ __noinline__ uint32_t resolve_dense(const Ctx& c, RShared& S, unsigne
   constexpr RLay L = rlay();
   const uint4* const R = reinterpret_cast<const uint4*>(smem + L.R);
   uint32_t* const tag = reinterpret_cast<uint32_t*>(smem + L.skey);  // 1 + largest exponent / 1 + position
-  uint64_t* const tlo = reinterpret_cast<uint64_t*>(smem + L.skey + 4 * kDense);  // low words / values
-  uint64_t* const thi = tlo + kDense;                                              // high words (sum)
+  // sum: four 32-bit limbs per slot (the result's bits later in the first
+  // two); last write: the value per slot
+  uint64_t* const tlo = reinterpret_cast<uint64_t*>(smem + L.skey + 4 * kDense);
+  auto slot_val = [&](uint32_t q) -> uint64_t& { return SUM ? tlo[2 * q] : tlo[q]; };
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const uint32_t span = (uint32_t)D.rg.span;
-  for (uint32_t q = tid; q < span; q += kRT) {
-    tag[q] = 0u;
-    tlo[q] = 0ull;
-    if (SUM) thi[q] = 0ull;
-  }
+  for (uint32_t q = tid; q < span; q += kRT) tag[q] = 0u;
+  for (uint32_t q = tid; q < (SUM ? 2 * span : span); q += kRT) tlo[q] = 0ull;
   __syncthreads();
   bool odd = false;
   for (uint32_t i = tid; i < n; i += kRT) {
@@ -520,17 +519,44 @@ __device__ __noinline__ uint32_t resolve_dense(const Ctx& c, RShared& S, unsigne
   } else {
     __syncthreads();
   }
-  for (uint32_t i = tid; i < n; i += kRT) {
-    const uint4 r = R[i];
-    const uint64_t raw = ((uint64_t)r.w << 32) | r.z;
-    if (SUM) {
-      const int G = max((int)tag[r.x] - 1, 1);
+  if (SUM) {
+    // each write's fixed-point value is added to its slot's four 32-bit limbs
+    // (native shared-memory atomics): its magnitude, limb by limb from the
+    // lowest non-zero one, with the carry (or, for a negative value, the
+    // borrow) that each atomic's old value reveals passed to the next limb.
+    // Every atomic is exact and the carries are counted exactly, so the slot
+    // ends as the two's complement sum of all its writes, whatever the order.
+    uint32_t* const limb = reinterpret_cast<uint32_t*>(tlo);  // slot q: limb[4q .. 4q+3], low first
+    for (uint32_t i = tid; i < n; i += kRT) {
+      const uint4 r = R[i];
+      const uint64_t w = wide<F64>(((uint64_t)r.w << 32) | r.z);
       uint64_t xlo, xhi;
-      fixed_of(wide<F64>(raw), G, xlo, xhi);
-      const unsigned long long old = atomicAdd(reinterpret_cast<unsigned long long*>(&tlo[r.x]), xlo);
-      atomicAdd(reinterpret_cast<unsigned long long*>(&thi[r.x]), xhi + ((uint64_t)old + xlo < xlo ? 1ull : 0ull));
-    } else if (r.y + 1u == tag[r.x]) {
-      tlo[r.x] = raw;
+      fixed_of(w & 0x7FFFFFFFFFFFFFFFull, max((int)tag[r.x] - 1, 1), xlo, xhi);  // the magnitude
+      const bool neg = (w >> 63) != 0;
+      const uint32_t m[4] = {(uint32_t)xlo, (uint32_t)(xlo >> 32), (uint32_t)xhi, (uint32_t)(xhi >> 32)};
+      uint32_t* const L4 = limb + 4 * r.x;
+      uint64_t c = 0;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const uint64_t add = (uint64_t)m[k] + c;  // 0 .. 2^32
+        if (add == 0) continue;                   // (c stays 0)
+        if (add >> 32) {                          // 2^32: the limb is unchanged, carry or borrow 1
+          c = 1;
+          continue;
+        }
+        if (neg) {
+          const uint32_t old = atomicSub(&L4[k], (uint32_t)add);
+          c = old < (uint32_t)add ? 1u : 0u;
+        } else {
+          const uint32_t old = atomicAdd(&L4[k], (uint32_t)add);
+          c = ((uint64_t)old + add) >> 32;
+        }
+      }
+    }
+  } else {
+    for (uint32_t i = tid; i < n; i += kRT) {
+      const uint4 r = R[i];
+      if (r.y + 1u == tag[r.x]) tlo[r.x] = ((uint64_t)r.w << 32) | r.z;
     }
   }
   __syncthreads();
@@ -546,11 +572,11 @@ __device__ __noinline__ uint32_t resolve_dense(const Ctx& c, RShared& S, unsigne
     if (q < s1 && tag[q] != 0u) {
       if (SUM) {
         bool nz;
-        const Acc x{tlo[q], (int64_t)thi[q], 0u};
-        tlo[q] = acc_round(x, max((int)tag[q] - 1, 1), !F64, &nz);
+        const Acc x{tlo[2 * q], (int64_t)tlo[2 * q + 1], 0u};  // (limbs, low first: little-endian words)
+        slot_val(q) = acc_round(x, max((int)tag[q] - 1, 1), !F64, &nz);
         kept = nz;
       } else {
-        kept = keep_zeros || bits_nonzero<F64>(tlo[q]);
+        kept = keep_zeros || bits_nonzero<F64>(slot_val(q));
       }
       if (!kept) tag[q] = 0u;
     }
@@ -575,7 +601,7 @@ __device__ __noinline__ uint32_t resolve_dense(const Ctx& c, RShared& S, unsigne
     if (kept) {
       const uint32_t li = wl + __popc(b & lt);
       dk[li] = q;
-      dv[li] = tlo[q];
+      dv[li] = slot_val(q);
     }
     wl += __popc(b);
   }
