@@ -504,6 +504,56 @@ def run_access(args, world, rank, local_rank):
         torch.distributed.destroy_process_group()
 
 
+def batched_oracle_rate(d, mode, budget_s=20.0):
+    """CPU oracle over the batch, one matrix per thread on every host core
+    (ctypes releases the GIL during the oracle's C++ build): matrices in a
+    seeded order until about budget_s of wall time; writes/s, the matrices
+    and writes done, the threads used."""
+    import concurrent.futures as cf
+
+    import numpy as np
+
+    import oracle
+    tp = np.asarray(d["trip_ptr"], dtype=np.int64)
+    ns = np.asarray(d["n"], dtype=np.int64)
+    order = np.random.default_rng(7).permutation(len(ns))
+    threads = os.cpu_count() or 1
+
+    def one(i):
+        a, b = int(tp[i]), int(tp[i + 1])
+        oracle.assemble_csc(d["rows"][a:b], d["cols"][a:b], d["vals"][a:b], (int(ns[i]), int(ns[i])), mode=mode)
+        return b - a
+
+    done = writes = 0
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+        while done < len(order) and time.perf_counter() - t0 < budget_s:
+            chunk = order[done:done + 4 * threads]
+            writes += sum(ex.map(one, chunk))
+            done += len(chunk)
+    dt = time.perf_counter() - t0
+    return writes / dt, done, writes, threads, dt
+
+
+def diff_oracle_rate(f, mode, k=16):
+    """CPU oracle of the differentiable step (1 thread): assembly, Y = A X, and
+    the backward (dvals and dX = A^T dY); writes/s and the seconds taken."""
+    import numpy as np
+
+    import oracle
+    rng = np.random.default_rng(5)
+    n = f["shape"][0]
+    X = rng.standard_normal((n, k))
+    dY = rng.standard_normal((n, k))
+    t0 = time.perf_counter()
+    cp, ri, v = oracle.assemble_csc(f["rows"], f["cols"], f["vals"], f["shape"], mode=mode)
+    oracle.csc_mm(f["shape"], cp, ri, v, X)
+    oracle.dvals(f["rows"], f["cols"], dY, X)
+    oracle.csc_mm(f["shape"], cp, ri, v, dY, transpose=True)
+    dt = time.perf_counter() - t0
+    return len(f["rows"]) / dt, dt
+
+
 def run_batched_or_diff(args, world, rank, local_rank):
     """The batched workload (one spm_assemble_csc_batched call against the
     same matrices assembled one call each, the latter timed on every 16th
@@ -648,6 +698,19 @@ def run_batched_or_diff(args, world, rank, local_rank):
     }
     if spec["kind"] == "diff":
         line["roofline"] = spmm_roofline
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        if spec["kind"] == "batched":
+            rate, done, wr, thr, dt = batched_oracle_rate(d, spec["mode"])
+            line["cpu_baseline"] = {"value": rate, "unit": "triplets/s", "cores": thr, "host_cores": os.cpu_count(),
+                                    "kind": "oracle",
+                                    "sample": f"{done} of the {B} matrices ({wr} writes) in a seeded order, one "
+                                              f"matrix per thread, std::map build + walk, {dt:.1f} s"}
+        else:
+            rate, dt = diff_oracle_rate(f, spec["mode"])
+            line["cpu_baseline"] = {"value": rate, "unit": "triplets/s", "cores": 1, "host_cores": os.cpu_count(),
+                                    "kind": "oracle",
+                                    "sample": f"the whole workload: std::map assembly, Y = A X, dvals and A^T dY "
+                                              f"(float64), 1 thread, {dt:.1f} s"}
     if alg is not None:
         achieved = alg / (ms / 1000.0) / 1e9
         line["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
