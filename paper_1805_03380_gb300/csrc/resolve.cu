@@ -3,44 +3,46 @@
 // After the partition, the writes of one bucket (an aligned range of the
 // paper's linear index row + col * n_rows, Section 3.3) lie contiguously in
 // the record array as 16-byte records {key within the bucket, stream
-// position, value bits}.  One persistent kernel (two blocks per SM) takes the
-// buckets in order (a ticket, fetched one bucket ahead) and, per bucket:
+// position, value bits}.  One persistent kernel (one 512-thread block per SM)
+// takes the buckets by ticket -- a helper thread fetches the next ticket and
+// descriptor and prefetches that bucket into L2 -- and, per bucket:
 //
-//   load     one bulk copy (cp.async.bulk, completed on an mbarrier) moves the
-//            bucket's records into shared memory; the bucket one round ahead
-//            is prefetched into L2 meanwhile
-//   sort     a counting sort on the top key bits (shared-memory atomics give
-//            each write its rank in its sub-bin), then each thread orders the
-//            few keys of its sub-bins by insertion (a bitonic sort of the whole
-//            bucket when some sub-bin is large); equal keys may end up in any
-//            order, the reduction does not depend on it
+//   load     one bulk copy (cp.async.bulk, completed on an mbarrier, bounded
+//            wait) moves the bucket's records into shared memory
+//   narrow   a bucket whose keys span at most kDense values is reduced in a
+//            key-indexed table with shared-memory atomics, no sort
+//            (resolve_dense)
+//   sort     otherwise a counting sort on the top key bits (shared-memory
+//            atomics give each write its rank in its sub-bin; rows near the
+//            diagonal first get an order-preserving narrower key), then
+//            sub-bins of 2..8 writes are ordered by a sorting network in one
+//            thread's registers and larger ones by warp bitonic networks over
+//            windows of whole sub-bins; equal keys may end up in any order,
+//            the reduction does not depend on it
 //   reduce   the sorted positions are cut into one range per warp at run
 //            boundaries, so that no run of equal keys spans two warps; each
-//            lane reduces the runs in its part of the warp's range
-//            sequentially, and runs that cross lanes are finished with
-//            segmented warp scans (shuffles, no block barrier).
+//            lane reduces the runs in its strip of the warp's range, and runs
+//            that cross lanes are finished with segmented warp scans.
 //              add mode: the exact sum of the run (exact_sum.cuh), its binary
 //              point set by the run's own largest exponent (found in a first
-//              pass); a single write is its own value
+//              pass); a single write is its own value; runs of several writes
+//              are parked and rounded 32 at a time by the whole warp
 //              last-write mode: the write with the largest (seq, position)
 //   zeros    an element whose value compares equal to zero is dropped (after
 //            rounding to the output type), as CSC stores non-zeros only
 //            (Section 3.1)
-//   place    the stored elements are numbered (block scan) and the bucket's
-//            count is published for a decoupled look-back over the buckets of
-//            the same matrix; the elements themselves are written back over
-//            the bucket's records (still in L2), and the block places them in
-//            the CSC arrays at the start of its next bucket, while that
-//            bucket's bulk copy is in flight: by then the buckets before it
-//            have published their counts, so the look-back rarely waits.  The
-//            lines are then discarded from L2, so the round trip costs no HBM
-//            traffic.
+//   out      without the map the stored elements (key, value) are written in
+//            key order over the bucket's records with coalesced stores and
+//            the bucket's count is recorded; k_place, after a scan of the
+//            counts, puts them in the CSC arrays.  With the map the block
+//            takes its output offset from a bounded decoupled look-back and
+//            places its elements and map entries at once.
 //
-// Calls that keep the map (and buckets with more writes than fit in shared
-// memory) place their elements at once instead: a bucket that is too large is
-// resolved in windows of its key range (records gathered from global memory),
-// first to count its elements, then to write them; one key with more writes
-// than a window holds is reduced by a streaming pass.
+// A bucket with more writes than fit in shared memory is resolved in windows
+// of its key range (records gathered from global memory): with the map at
+// once (counted, then written), without it counted here and written by k_big
+// once the offsets are known; one key with more writes than a window holds
+// is reduced by a streaming pass.
 //
 // No kernel traps or waits without a bound: an expired wait is reported as
 // SPM_ERR_TIMEOUT in the device status word and the call stops.
@@ -636,8 +638,52 @@ __device__ __noinline__ uint32_t resolve_tile(const Ctx& c, RShared& S, unsigned
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const bool keep_zeros = !SUM && c.keep_zeros;
 
+  // ---- banded key ranges: when every write's row lies within a band around
+  // the diagonal (row - col in [-md, md], as in FEM and stencil matrices) and
+  // the bucket spans many columns, the sort uses the order-preserving key
+  // (column in the bucket) * W + (row - col + W/2), W = 2^bshift > 2 md + 1,
+  // whose range is far narrower than the bucket's: the sub-bins then separate
+  // the rows of a column instead of holding whole columns.  The stored keys
+  // are mapped back when they are written out (kDefer only).
+  uint32_t bshift = 0;
+  uint64_t span = Rg.span;
+  const uint64_t nr = (uint64_t)D.n_rows;
+  if (!MAP && mode == kDefer && n > 64 && Rg.span > (uint64_t)n * 64) {
+    uint32_t md = 0;
+    for (uint32_t i = tid; i < n; i += kRT) {
+      const uint64_t t = Rg.r0 + R[i].x;
+      const uint64_t co = col_of(Rg, t, nr);
+      const int64_t d = (int64_t)(t - co * nr) - (int64_t)(Rg.col0 + co);
+      const int64_t ad = d < 0 ? -d : d;
+      md = max(md, (uint32_t)(ad < 0x3fffffff ? ad : 0x3fffffff));
+    }
+    md = __reduce_max_sync(kFull, md);
+    if (lane == 0) S.buf[wid] = md;
+    __syncthreads();
+    md = 0;
+#pragma unroll
+    for (int w2 = 0; w2 < kRW; ++w2) md = max(md, S.buf[w2]);
+    const uint64_t ncols = col_of(Rg, Rg.r0 + Rg.span - 1, nr) + 1;
+    const int sh = ceil_log2_u64(2ull * md + 2ull);
+    if ((uint64_t{1} << sh) < nr && (ncols << sh) <= Rg.span / 4 && (ncols << sh) <= (uint64_t{1} << 32)) {
+      bshift = (uint32_t)sh;
+      span = ncols << sh;
+      for (uint32_t i = tid; i < n; i += kRT) {
+        const uint64_t t = Rg.r0 + R[i].x;
+        const uint64_t co = col_of(Rg, t, nr);
+        const int64_t d = (int64_t)(t - co * nr) - (int64_t)(Rg.col0 + co);
+        R[i].x = (uint32_t)((co << sh) | (uint64_t)(d + (int64_t{1} << (sh - 1))));
+      }
+    }
+  }
+  auto unband = [&](uint32_t k) -> uint32_t {
+    if (!bshift) return k;
+    const uint64_t co = k >> bshift;
+    const int64_t d = (int64_t)(k & ((1u << bshift) - 1u)) - (int64_t{1} << (bshift - 1));
+    return (uint32_t)(co * nr + (uint64_t)((int64_t)(Rg.col0 + co) + d) - Rg.r0);
+  };
+
   // ---- counting sort on the top key bits (about one sub-bin per write)
-  const uint64_t span = Rg.span;
   const int sbits = span <= 1 ? 0 : ceil_log2_u64(span);
   const int bbits = min(c.sub_bits, max(4, n <= 1 ? 0 : ceil_log2_u64(n)));
   const int sshift = sbits > bbits ? sbits - bbits : 0;
@@ -686,23 +732,40 @@ __device__ __noinline__ uint32_t resolve_tile(const Ctx& c, RShared& S, unsigned
   // ---- order the keys inside the sub-bins (each holds one key when sshift == 0)
   if (sshift > 0 && n > 1) {
     if (S.maxbin <= 64u) {
-      // sub-bins of 2..8 writes: insertion by one thread; of 9..64: one warp,
-      // a bitonic network over (key, index) in registers
+      // sub-bins of 2..8 writes: one thread, a sorting network in registers;
+      // of 9..64: one warp, a bitonic network over (key, index) in registers
       const uint32_t qa = (uint32_t)(((uint64_t)tid * nbins) / kRT), qb = (uint32_t)(((uint64_t)(tid + 1) * nbins) / kRT);
       for (uint32_t q = qa; q < qb; ++q) {
         const uint32_t a = bins[q], e = bins[q + 1];
-        if (e - a > 8u) continue;
-        for (uint32_t x = a + 1; x < e; ++x) {
-          const uint32_t kv = skey[x];
-          const uint16_t pv = perm[x];
-          uint32_t y = x;
-          while (y > a && skey[y - 1] > kv) {
-            skey[y] = skey[y - 1];
-            perm[y] = perm[y - 1];
-            --y;
+        if (e - a < 2u || e - a > 8u) continue;
+        // 2..8 writes: an 8-input sorting network in registers (19
+        // compare-exchanges; absent inputs are the largest key, ties in any
+        // order: equal keys only need to be adjacent)
+        const uint32_t k = e - a;
+        uint32_t kk[8], pp[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          kk[j] = (uint32_t)j < k ? skey[a + j] : 0xffffffffu;
+          pp[j] = (uint32_t)j < k ? perm[a + j] : 0u;
+        }
+        auto cx = [&](int i, int j) {
+          const bool sw = kk[i] > kk[j];
+          const uint32_t k0 = sw ? kk[j] : kk[i], k1 = sw ? kk[i] : kk[j];
+          const uint32_t p0 = sw ? pp[j] : pp[i], p1 = sw ? pp[i] : pp[j];
+          kk[i] = k0, kk[j] = k1, pp[i] = p0, pp[j] = p1;
+        };
+        cx(0, 2), cx(1, 3), cx(4, 6), cx(5, 7);
+        cx(0, 4), cx(1, 5), cx(2, 6), cx(3, 7);
+        cx(0, 1), cx(2, 3), cx(4, 5), cx(6, 7);
+        cx(2, 4), cx(3, 5);
+        cx(1, 4), cx(3, 6);
+        cx(1, 2), cx(3, 4), cx(5, 6);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          if ((uint32_t)j < k) {
+            skey[a + j] = kk[j];
+            perm[a + j] = (uint16_t)pp[j];
           }
-          skey[y] = kv;
-          perm[y] = pv;
         }
       }
       // A heavy sub-bin is sorted together with the sub-bins after it, up to
@@ -1048,7 +1111,7 @@ numbered:
       const uint32_t p = q0 + lane, p2 = p + 32;
       const uint32_t ix = p < E ? perm[p] : 0u, ix2 = p2 < E ? perm[p2] : 0u;
       const bool kept = (ix & kKept) != 0, kept2 = (ix2 & kKept) != 0;
-      const uint32_t k1 = kept ? skey[p] : 0u, k2 = kept2 ? skey[p2] : 0u;
+      const uint32_t k1 = kept ? unband(skey[p]) : 0u, k2 = kept2 ? unband(skey[p2]) : 0u;
       const uint64_t v1 = kept ? RV[2 * (ix & kIdx) + 1] : 0ull;
       const uint64_t v2 = kept2 ? RV[2 * (ix2 & kIdx) + 1] : 0ull;
       const unsigned b1 = __ballot_sync(kFull, kept), b2 = __ballot_sync(kFull, kept2);

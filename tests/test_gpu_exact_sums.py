@@ -198,3 +198,26 @@ def test_narrow_buckets_last_write_bit_exact():
     want = oracle.assemble_csc(d["rows"], d["cols"], d["vals"], d["shape"], mode="set")
     assert_same_structure(got, want)
     assert got[2].tobytes() == want[2].tobytes()
+
+
+@pytest.mark.parametrize("mode", ["sum", "set"])
+def test_banded_matrix_structure_and_values(mode):
+    # rows within a band around the diagonal (the band-transformed sort keys),
+    # near the first and last columns too, rectangular: structure bit for bit,
+    # sums within the bar, last writes bit for bit
+    rng = np.random.default_rng(31)
+    n_rows, n_cols, m = 300_000, 250_000, 600_000
+    cols = rng.integers(0, n_cols, m)
+    rows = np.clip(cols + rng.integers(-37, 38, m), 0, n_rows - 1)
+    rep = rng.random(m) < 0.3
+    src = rng.integers(0, m, m)
+    rows[rep], cols[rep] = rows[src[rep]], cols[src[rep]]
+    d = dict(rows=rows.astype(np.int32), cols=cols.astype(np.int32), vals=rng.standard_normal(m),
+             shape=(n_rows, n_cols))
+    if mode == "sum":
+        _compare(d, np.float64)
+    else:
+        got = gpu_assemble(d, "set")
+        want = oracle.assemble_csc(d["rows"], d["cols"], d["vals"], d["shape"], mode="set")
+        assert_same_structure(got, want)
+        assert got[2].tobytes() == want[2].tobytes()
