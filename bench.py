@@ -185,7 +185,7 @@ class ClockSampler:
         except Exception:
             self.proc.kill()
             out, _ = self.proc.communicate()
-        self.lines = [ln for ln in out.splitlines() if ln.strip()]
+        self.lines += [ln for ln in out.splitlines() if ln.strip()]  # (several timed regions add up)
 
     def summary(self):
         sm, mx, reasons = [], [], set()
@@ -397,16 +397,24 @@ def run_access(args, world, rank, local_rank):
     sv = np.dtype(spec["dtype"]).itemsize
     stream = torch.cuda.current_stream()
 
+    sampler = ClockSampler(local_rank if "CUDA_VISIBLE_DEVICES" not in os.environ else 0)
+
     def timed(fn, steps):
         for _ in range(args.warmup):
             fn()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         torch.cuda.synchronize()
+        sampler.start()  # clocks sampled during the timed calls only
         for e0, e1 in ev:
             e0.record(stream)
             fn()
             e1.record(stream)
         torch.cuda.synchronize()
+        t_hold = time.perf_counter()  # the same load a moment longer, so that the sampler sees it
+        while time.perf_counter() - t_hold < 0.5:
+            fn()
+            torch.cuda.synchronize()
+        sampler.stop()
         return statistics.mean(e0.elapsed_time(e1) for e0, e1 in ev)
 
     def matrix_from(d):
@@ -499,7 +507,8 @@ def run_access(args, world, rank, local_rank):
                          "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind + " copy bandwidth",
                          "kernel": kernel, "algorithmic_bytes_per_launch": alg, "bytes_formula": formula,
                          "launch_ms_mean": ms},
-            "gpu_launches": launches, "gpu": torch.cuda.get_device_name(dev)}), flush=True)
+            "gpu_launches": launches, "gpu": torch.cuda.get_device_name(dev), "clocks": sampler.summary()}),
+              flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
 
@@ -575,11 +584,14 @@ def run_batched_or_diff(args, world, rank, local_rank):
     # fit in L2: a 512 MB write flushes it before every timed call
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev) if spec["kind"] == "diff" else None
 
+    sampler = ClockSampler(local_rank if "CUDA_VISIBLE_DEVICES" not in os.environ else 0)
+
     def timed(fn, steps):
         for _ in range(args.warmup):
             fn()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         torch.cuda.synchronize()
+        sampler.start()  # clocks sampled during the timed calls only
         for e0, e1 in ev:
             if flush is not None:
                 flush.zero_()
@@ -587,6 +599,11 @@ def run_batched_or_diff(args, world, rank, local_rank):
             fn()
             e1.record(stream)
         torch.cuda.synchronize()
+        t_hold = time.perf_counter()  # the same load a moment longer, so that the sampler sees it
+        while time.perf_counter() - t_hold < 0.5:
+            fn()
+            torch.cuda.synchronize()
+        sampler.stop()
         return statistics.mean(e0.elapsed_time(e1) for e0, e1 in ev)
 
     if spec["kind"] == "batched":
@@ -694,7 +711,7 @@ def run_batched_or_diff(args, world, rank, local_rank):
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if sv == 4 else "f64", "data": "synthetic",
         "config": dict({"workload": args.workload, "description": spec["desc"]}, **extra),
-        "gpu": torch.cuda.get_device_name(dev),
+        "gpu": torch.cuda.get_device_name(dev), "clocks": sampler.summary(),
     }
     if spec["kind"] == "diff":
         line["roofline"] = spmm_roofline
