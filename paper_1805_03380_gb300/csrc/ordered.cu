@@ -76,6 +76,21 @@ __device__ uint64_t reduce_run(const uint64_t* val, int j, int e, bool keep_zero
     keep = F64 ? (bits & 0x7FFFFFFFFFFFFFFFull) != 0 : (bits & 0x7FFFFFFFull) != 0;
     return bits;
   }
+  if (e - j == 2) {
+    // two writes whose exponents lie within the accumulator's window of each
+    // other (or a zero, an infinity, a NaN): the accumulator would hold their
+    // sum exactly, and one IEEE addition rounds that exact sum correctly --
+    // the same bits without the 128-bit path (float32 values: the float64 sum
+    // is exact within 28 binades, then rounded once to float32)
+    const uint64_t wa = o_wide(val[j], F64), wb = o_wide(val[j + 1], F64);
+    const int ea = f64_align_exponent(wa), eb = f64_align_exponent(wb);
+    if (ea <= 0 || eb <= 0 || abs(ea - eb) <= (F64 ? kAlignBits : 28)) {
+      const double sum = __longlong_as_double((long long)wa) + __longlong_as_double((long long)wb);
+      const uint64_t bits = F64 ? (uint64_t)__double_as_longlong(sum) : (uint64_t)__float_as_uint((float)sum);
+      keep = F64 ? (bits & 0x7FFFFFFFFFFFFFFFull) != 0 : (bits & 0x7FFFFFFFull) != 0;
+      return bits;
+    }
+  }
   int emax = 1;
   for (int q = j; q < e; ++q) emax = max(emax, f64_align_exponent(o_wide(val[q], F64)));
   Acc acc = acc_zero();

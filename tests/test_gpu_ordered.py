@@ -71,10 +71,9 @@ def test_same_result_with_and_without_the_single_pass():
             spm.spm_set_tuning(reset=True)
         assert taken0 == 0
         assert_same_structure(got1, got0)
-        if mode == "set":
-            assert_bit_exact(got1[2], got0[2])
-        else:  # sums agree to the last bits the general path keeps
-            np.testing.assert_allclose(got1[2], got0[2], rtol=1e-15, atol=1e-15)
+        # both paths sum each run exactly at the run's own binary point and
+        # round once: the same bits in both modes
+        assert_bit_exact(got1[2], got0[2])
 
 
 def test_streams_out_of_order_take_the_general_path():
@@ -179,3 +178,36 @@ def test_graph_replay_switches_between_the_two_paths():
         got = (A.col_ptr.cpu().numpy(), A.row_idx.cpu().numpy().astype(np.int64), A.vals.cpu().numpy())
         assert_same_structure(got, want)
         np.testing.assert_allclose(got[2], want[2], rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_pairs_across_the_exponent_window_match_the_general_path(dtype):
+    # runs of two writes whose exponents differ by 0..60 binades, with ties
+    # to even and values just above and below them: the single pass (one IEEE
+    # addition inside the window, the accumulator outside it) and the general
+    # path give the same bits
+    import paper_1805_03380_gb300 as spm
+    rng = np.random.default_rng(71)
+    n = 4000
+    big = (1.0 + rng.integers(0, 2**20, n) / 2**20) * np.where(rng.random(n) < 0.5, -1.0, 1.0)
+    shift = rng.integers(0, 61, n)
+    ulp_frac = rng.choice([0.5, 0.5 + 2.0**-30, 0.5 - 2.0**-30, 0.25, 1.0], n)
+    mant_bits = 53 if dtype == np.float64 else 24
+    small = np.ldexp(np.ones(n), -(mant_bits - 1)) * ulp_frac * np.where(shift < 40, 1.0, 0.0)
+    small = np.where(shift < 40, small, np.ldexp(rng.standard_normal(n), -shift.astype(np.int64)))
+    small = small * np.where(rng.random(n) < 0.5, -1.0, 1.0)
+    rows = np.repeat(np.arange(n, dtype=np.int32), 2)
+    cols = np.zeros(2 * n, dtype=np.int32)
+    vals = np.empty(2 * n)
+    vals[0::2], vals[1::2] = big, small
+    d = dict(rows=rows, cols=cols, vals=vals.astype(dtype), shape=(n, 1))
+    got1, taken = _run(d, "sum")
+    assert taken == 1
+    spm.spm_set_tuning(ordered_path=0)
+    try:
+        got0, taken0 = _run(d, "sum")
+    finally:
+        spm.spm_set_tuning(reset=True)
+    assert taken0 == 0
+    assert_same_structure(got1, got0)
+    assert_bit_exact(got1[2], got0[2])
