@@ -61,9 +61,13 @@ typedef enum {
  * bit for bit.  SUM: batch insertion with accumulation, X(r,c) += v (Fig. 2);
  * the exact sum of the writes to one element is rounded once to the output
  * type (round-to-nearest-even), so the result does not depend on the order of
- * the writes (seq has no effect in this mode).  Bits of a value lying more than
- * 58 bits below the largest value of its bucket are dropped (at most 2^-110 of
- * that value per write).  NaN and infinities follow IEEE addition. */
+ * the writes or on how the work is split (seq has no effect in this mode).
+ * The sum is formed in a 128-bit fixed-point integer whose binary point lies
+ * 42 bits below the largest exponent among that element's own writes: the
+ * result is the correctly rounded exact sum whenever the element's writes
+ * span at most 42 binades; bits of a write lying further down are dropped (less
+ * than 2^-94 of the element's largest write per write).  One write is its own
+ * value.  NaN and infinities follow IEEE addition. */
 typedef enum { SPM_MODE_LAST_WRITE = 0, SPM_MODE_SUM = 1 } spm_mode;
 
 /* Value type of the writes and of the CSC values.  SPM_F32 values are
@@ -390,21 +394,22 @@ spm_status spm_triplet_dvals(int64_t m, const int32_t* rows, const int32_t* cols
  * sets them).  A call with NULL restores the defaults.  Changing them changes
  * the workspace size, so query the workspace after setting them.
  *   bucket_target        expected writes per bucket the planner aims for
- *                        (256 .. 114688); a bucket may hold up to twice the
- *                        target, at most 28672, in shared memory -- larger
- *                        buckets take a slower windowed path
- *   sub_bits             log2 of the counting-sort digit used inside a bucket
- *                        (8 .. 11)
+ *                        (256 .. 65536; default 6144); a bucket may hold up
+ *                        to twice the target; at most 8192 writes are
+ *                        resolved in shared memory -- larger buckets take a
+ *                        slower windowed path
+ *   sub_bits             log2 of the largest counting-sort digit used inside
+ *                        a bucket (8 .. 12; default 12)
  *   partition_threads    threads per block of the histogram/scatter kernels
  *                        (256, 512 or 1024)
- *   resolve_threads      threads per block of the per-bucket kernel
- *                        (256, 512 or 1024)
- *   two_pass_min_writes  calls with at least this many writes (and no seq)
- *                        move the writes to their buckets in two passes --
- *                        first to about four groups of buckets per SM, then
- *                        within each group -- which keeps the set of partly
- *                        written cache lines small; the workspace then holds
- *                        4 more bytes per write (>= 0)
+ *   resolve_threads      threads per block of the per-bucket kernel (512: the
+ *                        kernel's shared-memory layout is built for it)
+ *   two_pass_min_writes  calls with at least this many writes move the
+ *                        writes to their buckets in two passes -- first to
+ *                        about four groups of buckets per SM, then within
+ *                        each group -- which keeps the set of partly written
+ *                        cache lines small; the workspace then holds 20 more
+ *                        bytes per write (>= 0; default 2^22)
  *   two_pass_min_fronts  ... and only when the one-pass scatter would write
  *                        to more than this many (partition block, bucket)
  *                        pairs, counted on the device after the histogram;
@@ -416,9 +421,8 @@ spm_status spm_triplet_dvals(int64_t m, const int32_t* rows, const int32_t* cols
  *                        order (the linear indices never decrease); it gives
  *                        up at the first write out of order and the general
  *                        path runs.  0: never tried.  The result is the same
- *                        either way (sums agree except for bits more than 58
- *                        below an element's largest value, which the general
- *                        path aligns per bucket)
+ *                        either way, bit for bit (both sum each run at its
+ *                        own binary point)
  */
 typedef struct {
   int32_t bucket_target;
