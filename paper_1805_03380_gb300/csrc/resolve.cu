@@ -369,14 +369,27 @@ __device__ void emit_range(const Ctx& c, const Desc& D, const Range& R, uint32_t
   const uint64_t jn = col0 + (r0 ? 1u : 0u);                       // first column starting in the range
   const uint64_t je = col0 + col_of(R, r0 + R.span + nr - 1, nr);  // first column starting after it
   uint64_t lastcol = jn - 1;
+  // each iteration's element (and, for lane 0, the element before the warp's
+  // first) is loaded one iteration ahead, so the loads overlap the stores
+  uint32_t nkey = 0, pkey = 0;
+  uint64_t nbits = 0, pbits = 0;
+  {
+    const uint32_t l1 = (tid & ~31u) + lane;
+    if (l1 < nnz) get(l1, nkey, nbits);
+    if (lane == 0 && l1 > 0 && l1 < nnz) get(l1 - 1, pkey, pbits);
+  }
   for (uint32_t li0 = tid & ~31u; li0 < nnz; li0 += blockDim.x) {
     const uint32_t li = li0 + lane;
     const bool have = li < nnz;
+    const uint32_t key = nkey, prevkey = pkey;
+    const uint64_t bits = nbits;
+    {
+      const uint32_t ln = li + blockDim.x;
+      if (ln < nnz) get(ln, nkey, nbits);
+      if (lane == 0 && ln < nnz) get(ln - 1, pkey, pbits);
+    }
     uint64_t col = 0;
     if (have) {
-      uint32_t key;
-      uint64_t bits;
-      get(li, key, bits);
       const uint64_t x = r0 + key;
       const uint64_t cr = col_of(R, x, nr);
       col = col0 + cr;
@@ -384,16 +397,7 @@ __device__ void emit_range(const Ctx& c, const Desc& D, const Range& R, uint32_t
       outp[base + li] = (VT)bits;
     }
     uint64_t pc = __shfl_up_sync(kFull, col, 1);
-    if (have && lane == 0) {
-      if (li == 0) {
-        pc = jn - 1;
-      } else {
-        uint32_t key;
-        uint64_t bits;
-        get(li - 1, key, bits);
-        pc = col0 + col_of(R, r0 + key, nr);
-      }
-    }
+    if (have && lane == 0) pc = li == 0 ? jn - 1 : col0 + col_of(R, r0 + prevkey, nr);
     // offsets of the columns (pc, col]: this element is the first of each
     const uint64_t gap = have ? col - pc : 0;
     if (gap > 0 && gap <= 32)
