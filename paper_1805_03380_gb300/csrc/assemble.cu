@@ -810,6 +810,17 @@ __global__ void k_scan_top(Ctx c, int64_t nblk) {
   }
 }
 
+// The whole scan in one block when the buckets fit one (small calls: two
+// launches fewer than reduce + top + down).
+__global__ void k_scan_one(Ctx c, const uint32_t* __restrict__ in, uint32_t* __restrict__ out) {
+  __shared__ uint32_t buf[32];
+  __shared__ uint32_t tot;
+  const int64_t i = threadIdx.x;
+  const uint32_t v = i < c.nbcap_total && i < (int64_t)c.scal->NB ? in[i] : 0u;
+  const uint32_t off = block_scan_excl<uint32_t>(v, &tot, buf);
+  if (i < c.nbcap_total) out[i] = off;
+}
+
 __global__ void k_scan_down(Ctx c, const uint32_t* __restrict__ in, uint32_t* __restrict__ out) {
   __shared__ uint32_t buf[32];
   __shared__ uint32_t tot;
@@ -1505,6 +1516,17 @@ int resident_grid(K kernel, int sms, int threads, size_t smem) {
   return sms * per_sm;
 }
 
+// Exclusive scan of one count per bucket (in -> out).
+void launch_bucket_scan(const Ctx& ctx, const Layout& L, const uint32_t* in, uint32_t* out, cudaStream_t st) {
+  if (L.scan_blocks == 1) {
+    k_scan_one<<<1, kScanBlock, 0, st>>>(ctx, in, out);
+    return;
+  }
+  k_scan_reduce<<<(unsigned)L.scan_blocks, kScanBlock, 0, st>>>(ctx, in);
+  k_scan_top<<<1, 1024, 0, st>>>(ctx, L.scan_blocks);
+  k_scan_down<<<(unsigned)L.scan_blocks, kScanBlock, 0, st>>>(ctx, in, out);
+}
+
 template <bool BATCHED>
 void launch_partition(const Ctx& ctx, const Layout& L, bool vec, cudaStream_t st, int threads, int sms,
                       int64_t call) {
@@ -1514,9 +1536,7 @@ void launch_partition(const Ctx& ctx, const Layout& L, bool vec, cudaStream_t st
   else k_hist<BATCHED, false><<<C, threads, ps, st>>>(ctx);
   stage_mark(st, call, 2);
   k_colscan<<<(unsigned)((L.nbcap_total + 255) / 256), 256, 0, st>>>(ctx);
-  k_scan_reduce<<<(unsigned)L.scan_blocks, kScanBlock, 0, st>>>(ctx, ctx.bk_count);
-  k_scan_top<<<1, 1024, 0, st>>>(ctx, L.scan_blocks);
-  k_scan_down<<<(unsigned)L.scan_blocks, kScanBlock, 0, st>>>(ctx, ctx.bk_count, ctx.bk_start);
+  launch_bucket_scan(ctx, L, ctx.bk_count, ctx.bk_start, st);
   stage_mark(st, call, 3);
   const bool f64 = ctx.f64 != 0;
   if (ctx.two_pass) {  // (the device picks one of the two paths; the other's blocks return at once)
@@ -1674,19 +1694,18 @@ spm_status run_assembly(int64_t B, const int64_t* h_nr, const int64_t* h_nc, con
   const bool batched = B > 1;
   if (batched) launch_partition<true>(ctx, L, vec, st, tun.partition_threads, ds->sms, call);
   else launch_partition<false>(ctx, L, vec, st, tun.partition_threads, ds->sms, call);
-  launch_resolve(ctx, ds->sms, st);
+  launch_resolve(ctx, ds->sms, L.nbcap_total, st);
   stage_mark(st, call, 5);
   if (!keep_map) {
     // offsets of the buckets' elements, then their placement
-    k_scan_reduce<<<(unsigned)L.scan_blocks, kScanBlock, 0, st>>>(ctx, ctx.bk_nnz);
-    k_scan_top<<<1, 1024, 0, st>>>(ctx, L.scan_blocks);
-    k_scan_down<<<(unsigned)L.scan_blocks, kScanBlock, 0, st>>>(ctx, ctx.bk_nnz, ctx.bk_out);
+    launch_bucket_scan(ctx, L, ctx.bk_nnz, ctx.bk_out, st);
     launch_place(ctx, ds->sms, L.nbcap_total, st);
   }
   stage_mark(st, call, 6);
-  // setup, plan, 2 bucket kernels, 6 partition (with room for two passes: 8), resolve,
-  // and without the map 3 scan kernels and 2 placement kernels
-  g_launches += 11 + (L.S_total > 0 ? 1 : 0) + (L.two_pass ? 2 : 0) + (keep_map ? 0 : 5);
+  // setup, plan, 2 bucket kernels, hist, colscan, scan, scatter (with room for two
+  // passes: 2 more), resolve, and without the map a scan and 2 placement kernels
+  const int scans = L.scan_blocks == 1 ? 1 : 3;
+  g_launches += 8 + scans + (L.S_total > 0 ? 1 : 0) + (L.two_pass ? 2 : 0) + (keep_map ? 0 : 2 + scans);
   if (cudaGetLastError() != cudaSuccess) return SPM_ERR_CUDA;
   return SPM_OK;
 }

@@ -1633,12 +1633,15 @@ void resolve_set_attributes() {
 #undef SPM_ATTR
 }
 
-void launch_resolve(const Ctx& ctx, int sms, cudaStream_t st) {
+void launch_resolve(const Ctx& ctx, int sms, int64_t nbcap, cudaStream_t st) {
   const size_t bytes = rlay().total;
+  const int64_t nb = std::max<int64_t>(nbcap, 1);  // (no more blocks than buckets)
   const bool f64 = ctx.f64 != 0, sum = ctx.sum_mode != 0, seq = ctx.has_seq != 0, map = ctx.keep_map != 0;
 #define SPM_RES(F6, SU, SQ, MP)                                                                              \
   if (f64 == F6 && sum == SU && seq == SQ && map == MP) {                                                   \
-    k_resolve<F6, SU, SQ, MP><<<resident_blocks(k_resolve<F6, SU, SQ, MP>, sms, bytes), kRT, bytes, st>>>(ctx); \
+    k_resolve<F6, SU, SQ, MP>                                                                                \
+        <<<(unsigned)std::min<int64_t>(resident_blocks(k_resolve<F6, SU, SQ, MP>, sms, bytes), nb), kRT, bytes, \
+           st>>>(ctx);                                                                                       \
     return;                                                                                                 \
   }
   SPM_RES_ALL(SPM_RES)
@@ -1653,7 +1656,7 @@ void launch_place(const Ctx& ctx, int sms, int64_t nbcap, cudaStream_t st) {
   else k_place<false><<<blocks, 256, 0, st>>>(ctx);
 #define SPM_BIG(F6, SU, SQ, MP)                             \
   if (!MP && f64 == F6 && sum == SU && seq == SQ) {         \
-    k_big<F6, SU, SQ><<<sms, kRT, bytes, st>>>(ctx);         \
+    k_big<F6, SU, SQ><<<(unsigned)std::min<int64_t>(sms, blocks), kRT, bytes, st>>>(ctx); \
     return;                                                 \
   }
   SPM_RES_ALL(SPM_BIG)

@@ -244,7 +244,7 @@ constexpr uint32_t kFlagKeepZeros = 1u << 30;
 // placement kernels.
 int resolve_capacity(bool map);
 void resolve_set_attributes();
-void launch_resolve(const Ctx& ctx, int sms, cudaStream_t st);
+void launch_resolve(const Ctx& ctx, int sms, int64_t nbcap, cudaStream_t st);
 void launch_place(const Ctx& ctx, int sms, int64_t nbcap, cudaStream_t st);
 
 // Launch counter of the library's kernels (spm_debug_launch_count).
