@@ -98,6 +98,10 @@ __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
+// the same without the arrival (a later copy of the same phase arrives)
+__device__ __forceinline__ void mbar_expect_tx_only(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.expect_tx.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
 // global -> own shared memory, 16-byte aligned addresses and a size that is a
 // multiple of 16
 __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
@@ -256,16 +260,15 @@ struct Desc {
 };
 
 // Bucket b's descriptor (one thread; reads the bucket tables and the matrix).
-__device__ __forceinline__ Desc load_desc(const Ctx& c, uint32_t b) {
+// Bucket b's descriptor from its table entries and its matrix.
+__device__ __forceinline__ Desc make_desc(uint32_t b, uint32_t n, uint32_t start, uint32_t info, uint64_t klo,
+                                          const MatMeta& mm) {
   Desc d;
   d.b = b;
   d.valid = 1;
-  d.n = c.bk_count[b];
-  d.start = c.bk_start[b];
-  const uint32_t info = c.bk_info[b];
-  const uint64_t klo = c.bk_lo[b];
+  d.n = n;
+  d.start = start;
   d.mi = info >> 6;
-  const MatMeta& mm = c.meta[d.mi];
   d.n_rows = mm.n_rows;
   d.n_cols = mm.n_cols;
   d.col_base = mm.col_base;
@@ -275,6 +278,35 @@ __device__ __forceinline__ Desc load_desc(const Ctx& c, uint32_t b) {
   const uint64_t span = mm.K == 0 ? 0 : min(uint64_t{1} << (info & 63), mm.K - klo);
   d.rg = mm.K == 0 ? Range{0, 0, 0, 0, Div32{0, 0, 0}, 0} : make_range((uint64_t)mm.n_rows, klo, span);
   return d;
+}
+
+__device__ __forceinline__ Desc load_desc(const Ctx& c, uint32_t b) {
+  const uint32_t info = c.bk_info[b];
+  return make_desc(b, c.bk_count[b], c.bk_start[b], info, c.bk_lo[b], c.meta[info >> 6]);
+}
+
+// Asynchronous copies of a bucket's table entries into shared memory (the
+// helper thread issues them a bucket ahead and waits only when it builds the
+// descriptor).
+struct DescRaw {
+  uint64_t klo;
+  uint32_t n, start, info, pad;
+};
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit_wait() {
+  asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+__device__ __forceinline__ void raw_fetch(const Ctx& c, uint32_t b, DescRaw* r) {
+  cp_async8(&r->klo, c.bk_lo + b);
+  cp_async4(&r->n, c.bk_count + b);
+  cp_async4(&r->start, c.bk_start + b);
+  cp_async4(&r->info, c.bk_info + b);
+  asm volatile("cp.async.commit_group;" ::: "memory");
 }
 
 struct RShared {
@@ -290,6 +322,9 @@ struct RShared {
   int kmax;
   alignas(16) unsigned char parts[kRW * 32];  // per warp partial of a single key
   uint16_t ring[kRW][64];  // per warp: positions of parked runs waiting to be rounded
+  uint32_t rb, rb_next;    // first record slot of the current / next bucket in the record area
+  uint32_t pre;            // the next bucket's place is set and (part of) its copy in flight
+  uint32_t late_off, late_cnt;  // ... the part of it still to copy once this bucket is done
   uint64_t bar;       // mbarrier of the bulk copy
 };
 
@@ -496,9 +531,9 @@ constexpr uint32_t kDenseNo = ~0u;
 
 template <bool F64, bool SUM>
 __device__ __noinline__ uint32_t resolve_dense(const Ctx& c, RShared& S, unsigned char* smem, uint32_t n,
-                                               const Desc& D) {
+                                               const Desc& D, uint32_t rb) {
   constexpr RLay L = rlay();
-  const uint4* const R = reinterpret_cast<const uint4*>(smem + L.R);
+  const uint4* const R = reinterpret_cast<const uint4*>(smem + L.R) + rb;
   uint32_t* const tag = reinterpret_cast<uint32_t*>(smem + L.skey);  // 1 + largest exponent / 1 + position
   // sum: four 32-bit limbs per slot (the result's bits later in the first
   // two); last write: the value per slot
@@ -630,11 +665,12 @@ enum : int {
 // next barrier ends every read of the shared arrays).
 template <bool F64, bool SUM, bool SEQ, bool MAP, class GetBase>
 __device__ __noinline__ uint32_t resolve_tile(const Ctx& c, RShared& S, unsigned char* smem, uint32_t n, const Desc& D,
-                                 const Range& Rg, int mode, GetBase get_base) {
+                                 const Range& Rg, int mode, GetBase get_base, uint32_t rb = 0) {
   constexpr RLay L = rlay();
-  uint4* const R = reinterpret_cast<uint4*>(smem + L.R);
-  const uint64_t* const RV = reinterpret_cast<const uint64_t*>(smem + L.R);
-  uint64_t* const RVw = reinterpret_cast<uint64_t*>(smem + L.R);
+  // the records: slots [rb, rb + n) of the record area (rb > 0 only without the map)
+  uint4* const R = reinterpret_cast<uint4*>(smem + L.R) + rb;
+  const uint64_t* const RV = reinterpret_cast<const uint64_t*>(R);
+  uint64_t* const RVw = reinterpret_cast<uint64_t*>(R);
   uint32_t* const skey = reinterpret_cast<uint32_t*>(smem + L.skey);
   uint16_t* const perm = reinterpret_cast<uint16_t*>(smem + L.perm);
   uint32_t* const bins = reinterpret_cast<uint32_t*>(smem + L.bins);
@@ -1380,15 +1416,26 @@ __device__ __noinline__ uint32_t resolve_windows(const Ctx& c, RShared& S, unsig
 // while the block waits for the current bucket's bulk copy.
 constexpr int kHelper = kRT - 1;
 
-// Start the bulk copy of bucket D into the record area (thread 0; the
-// previous contents are dead).
+// Start the bulk copy of bucket D into record slots [rb, rb + D.n) of the
+// record area (thread 0; those slots are dead).
 __device__ __forceinline__ void start_bucket(const Ctx& c, RShared& S, unsigned char* smem, const Desc& D,
-                                             uint32_t cap) {
+                                             uint32_t cap, uint32_t rb) {
   if (D.n > 0 && D.n <= cap) {
     fence_proxy_async();
     mbar_expect_tx(&S.bar, D.n * 16u);
-    bulk_load(smem + rlay().R, c.rec + D.start, D.n * 16u, &S.bar);
+    bulk_load(smem + rlay().R + (size_t)16 * rb, c.rec + D.start, D.n * 16u, &S.bar);
   }
+}
+
+// Copy records [off, off + cnt) of bucket D into slots [dst, dst + cnt)
+// (thread 0); `arrive`: this copy completes the barrier's phase, else a later
+// one of the same phase does.
+__device__ __forceinline__ void copy_part(const Ctx& c, RShared& S, unsigned char* smem, const Desc& D, uint32_t off,
+                                          uint32_t cnt, uint32_t dst, bool arrive) {
+  fence_proxy_async();
+  if (arrive) mbar_expect_tx(&S.bar, cnt * 16u);
+  else mbar_expect_tx_only(&S.bar, cnt * 16u);
+  bulk_load(smem + rlay().R + (size_t)16 * dst, c.rec + D.start + off, cnt * 16u, &S.bar);
 }
 
 // Drop the L2 lines that lie entirely inside [a0, a1) (dead data), so that
@@ -1410,40 +1457,67 @@ template <bool F64, bool SUM, bool SEQ, bool MAP>
 __global__ void __launch_bounds__(kRT, 1) k_resolve(Ctx c) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ RShared S;
-  __shared__ Desc nxt;
+  __shared__ Desc nxt;    // the next bucket's descriptor
+  __shared__ DescRaw raw;  // its table entries, fetched asynchronously a bucket earlier
   const int tid = threadIdx.x;
   const uint32_t NB = c.scal->NB;
   const uint32_t cap = MAP ? (uint32_t)kRCapNow : (uint32_t)kRCap;  // writes resolved from shared memory
-  uint32_t next = ~0u;  // (thread kHelper) the ticket after the current bucket's
+  // (thread kHelper) the tickets of the next bucket (its entries in flight)
+  // and of the one after it, and the matrix of the last descriptor it built
+  uint32_t t1 = ~0u, t2 = ~0u;
+  int64_t mi_cached = -1;
+  MatMeta mm_cached;
   if (tid == 0) {
     mbar_init(&S.bar, 1);
     fence_mbar_init();
     S.abort = 0;
+    S.rb = 0;
+    S.pre = 0;
     const uint32_t t = is_aborted(c) ? ~0u : atomicAdd(&c.scal->ticket, 1u);
     S.cur.valid = 0;
     S.cur.b = t;
     if (t < NB) {
       S.cur = load_desc(c, t);
-      start_bucket(c, S, smem, S.cur, cap);
+      start_bucket(c, S, smem, S.cur, cap, 0);
     }
   }
   __syncthreads();
-  if (tid == kHelper && S.cur.valid) next = is_aborted(c) ? ~0u : atomicAdd(&c.scal->ticket, 1u);
+  if (tid == kHelper && S.cur.valid) {
+    t1 = is_aborted(c) ? ~0u : atomicAdd(&c.scal->ticket, 1u);
+    if (t1 < NB) {
+      raw_fetch(c, t1, &raw);
+      t2 = is_aborted(c) ? ~0u : atomicAdd(&c.scal->ticket, 1u);
+    }
+  }
   uint32_t phase = 0;
   bool copying = false;  // a bulk copy has been started and not yet waited for
   while (true) {
     if (!S.cur.valid) break;
     copying = S.cur.n > 0 && S.cur.n <= cap;
     const Desc& D = S.cur;
-    // the next bucket's descriptor, read while this one's copy is in flight
+    // the next bucket's descriptor, built from its table entries (fetched a
+    // bucket earlier) while this bucket's copy is in flight; then the entries
+    // of the bucket after it are fetched and the ticket after that taken,
+    // both waited for only a bucket later
     if (tid == kHelper) {
       nxt.valid = 0;
       nxt.b = ~0u;
-      if (next < NB) {
-        nxt = load_desc(c, next);
-        next = is_aborted(c) ? ~0u : atomicAdd(&c.scal->ticket, 1u);
+      if (t1 < NB) {
+        cp_async_commit_wait();
+        const uint32_t mi = raw.info >> 6;
+        if ((int64_t)mi != mi_cached) {
+          mm_cached = c.meta[mi];
+          mi_cached = mi;
+        }
+        nxt = make_desc(t1, raw.n, raw.start, raw.info, raw.klo, mm_cached);
         // warm L2 with its records, a bucket's time before its bulk copy
         if (nxt.n <= cap) prefetch_l2(c.rec + nxt.start, nxt.n * 16u);
+      }
+      t1 = t2;
+      t2 = ~0u;
+      if (t1 < NB) {
+        raw_fetch(c, t1, &raw);
+        t2 = is_aborted(c) ? ~0u : atomicAdd(&c.scal->ticket, 1u);
       }
     }
     int64_t total = -1;  // set when the bucket is placed here
@@ -1515,13 +1589,32 @@ __global__ void __launch_bounds__(kRT, 1) k_resolve(Ctx c) {
         if (S.abort) break;
         total = S.base + nnz;
       } else {
+        // the next bucket goes to the other end of the record area: the part
+        // of its copy that does not land on this bucket's records starts now,
+        // while this one is resolved, the rest once it is done
+        if (tid == 0 && nxt.valid && nxt.K > 0 && nxt.n > 0 && nxt.n <= cap) {
+          const uint32_t n2 = nxt.n;
+          const bool top = S.rb == 0;  // this bucket at the bottom: the next one at the top
+          const uint32_t r2 = top ? cap - n2 : 0;
+          const uint32_t c0 = S.rb, c1 = S.rb + D.n;  // slots in use
+          const uint32_t ov = top ? (c1 > r2 ? c1 - r2 : 0u) : (n2 > c0 ? n2 - c0 : 0u);  // overlap
+          S.rb_next = r2;
+          S.pre = 1;
+          S.late_cnt = ov;
+          S.late_off = top ? 0u : n2 - ov;
+          if (ov < n2) {  // the early part: after the overlap (top) or before it (bottom)
+            if (top) copy_part(c, S, smem, nxt, ov, n2 - ov, r2 + ov, ov == 0);
+            else copy_part(c, S, smem, nxt, 0, n2 - ov, 0, ov == 0);
+          }
+        }
         // the elements wait over the bucket's records for k_place
+        const uint32_t rb = S.rb;
         uint32_t nnz = kDenseNo;
-        if (!SEQ && D.rg.span <= kDense) nnz = resolve_dense<F64, SUM>(c, S, smem, D.n, D);
+        if (!SEQ && D.rg.span <= kDense) nnz = resolve_dense<F64, SUM>(c, S, smem, D.n, D, rb);
         if (nnz == kDenseNo) {
           nnz = resolve_tile<F64, SUM, SEQ, MAP>(c, S, smem, D.n, D, D.rg, kDefer, [](uint32_t) {
             return int64_t{0};
-          });
+          }, rb);
         }
         if (tid == 0) c.bk_nnz[D.b] = nnz;
         dead0 = res_vals(c, D.start, D.n) + nnz;
@@ -1536,12 +1629,20 @@ __global__ void __launch_bounds__(kRT, 1) k_resolve(Ctx c) {
     __syncthreads();      // the record area and the descriptors are free
     if (tid == 0) {
       S.cur = nxt;
-      if (S.cur.valid) start_bucket(c, S, smem, S.cur, cap);
+      if (S.pre) {
+        S.rb = S.rb_next;  // (part of) its copy is in flight already
+        if (S.late_cnt) copy_part(c, S, smem, S.cur, S.late_off, S.late_cnt, S.rb + S.late_off, true);
+      } else {
+        S.rb = 0;
+        if (S.cur.valid) start_bucket(c, S, smem, S.cur, cap, 0);
+      }
+      S.pre = 0;
     }
     if (dead0) discard_lines(dead0, dead1);
     __syncthreads();
   }
   if (copying) mbar_wait_bounded(&S.bar, phase);  // (a call that stopped early)
+  if (tid == kHelper) asm volatile("cp.async.wait_all;" ::: "memory");  // (no copy outlives the block)
 }
 
 // Calls without the map: every bucket's elements wait over its records, in
