@@ -122,18 +122,27 @@ def measured_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+def _code_only(text):
+    """The source without its comments and blank lines (edits to comments do
+    not change the compiled kernels)."""
+    import re
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    return "\n".join(ln.rstrip() for ln in text.splitlines() if ln.strip())
+
+
 def source_hash():
-    """Hash of the library's sources (every kernel file and header): a
-    committed traffic figure is used only while they are unchanged."""
+    """Hash of the library's code (every kernel file and header, comments
+    left out): a committed traffic figure is used only while it is unchanged."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1805_03380_gb300", "csrc")
     for fn in sorted(os.listdir(csrc)):
         if not fn.endswith((".cu", ".cuh", ".h")):
             continue
-        with open(os.path.join(csrc, fn), "rb") as f:
-            h.update(fn.encode() + f.read())
-    with open(os.path.join(ROOT, "include", "spm.h"), "rb") as f:
-        h.update(b"spm.h" + f.read())
+        with open(os.path.join(csrc, fn), encoding="utf-8") as f:
+            h.update(fn.encode() + _code_only(f.read()).encode())
+    with open(os.path.join(ROOT, "include", "spm.h"), encoding="utf-8") as f:
+        h.update(b"spm.h" + _code_only(f.read()).encode())
     return h.hexdigest()[:16]
 
 

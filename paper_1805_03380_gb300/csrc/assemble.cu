@@ -20,8 +20,11 @@
 //               buckets, when one pass would leave too many partly written
 //               cache lines)
 //   resolve  -> resolve.cu: a persistent kernel loads each bucket into shared
-//               memory, sorts it, resolves repeated writes, drops zeros and
-//               writes the CSC arrays after a decoupled look-back.
+//               memory, sorts it (or reduces it in a key-indexed table when its
+//               key range is narrow), resolves repeated writes, drops zeros and
+//               writes the bucket's stored elements and count; a scan of the
+//               counts and k_place then write the CSC arrays (with the map the
+//               resolve kernel places them itself after a decoupled look-back).
 //
 // No kernel ever traps or spins without a bound: out-of-range indices and
 // expired waits are reported in the device status word.
