@@ -46,3 +46,31 @@ def test_small_search_on_the_gpu(tmp_path):
     assert entry["tuning"] == best["tuning"] and entry["ms"] > 0
     assert at.apply_cached(d["shape"], len(d["rows"]), torch.float64, "sum", path=p) == best["tuning"]
     spm.spm_set_tuning(reset=True)
+
+
+def test_every_candidate_is_a_valid_tuning():
+    # the library accepts every candidate of the search space (host check, no GPU)
+    import paper_1805_03380_gb300 as spm
+    from paper_1805_03380_gb300 import autotune as at
+    t0 = spm.spm_get_tuning()
+    try:
+        for cand in at.default_candidates():
+            spm.spm_set_tuning(reset=True)
+            t = spm.spm_set_tuning(**cand)
+            assert all(t[k] == v for k, v in cand.items())
+    finally:
+        spm.spm_set_tuning(reset=True)
+        spm.spm_set_tuning(**t0)
+
+
+def test_batch_cache_key_follows_the_layout():
+    from paper_1805_03380_gb300 import autotune as at
+    n = np.array([64, 100, 300])
+    tp = np.array([0, 40, 90, 200])
+    k1 = at.batch_cache_key(n, n, tp, torch.float32, "set")
+    assert k1 == at.batch_cache_key(list(n), list(n), list(tp), torch.float32, "set")
+    assert "batch=3" in k1 and "m=200" in k1 and k1.endswith("f32|set|flags=0")
+    # another shape, another split of the same writes, another mode: other keys
+    assert at.batch_cache_key(n + 1, n, tp, torch.float32, "set") != k1
+    assert at.batch_cache_key(n, n, np.array([0, 41, 90, 200]), torch.float32, "set") != k1
+    assert at.batch_cache_key(n, n, tp, torch.float32, "sum") != k1
