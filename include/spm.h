@@ -214,8 +214,9 @@ spm_status spm_assemble_csc_static(int64_t n_rows, int64_t n_cols, int64_t m, co
  * the sync of Section 3.4 after writes made while A was in compressed form.
  *
  * The writes are first resolved among themselves exactly as spm_assemble_csc
- * resolves them (last write by (seq, position), or the correctly rounded sum
- * of the writes to one element); then every element written replaces A's
+ * resolves them (last write by (seq, position), or the sum of the writes to
+ * one element formed as in SUM mode: correctly rounded when they span at
+ * most 42 binades); then every element written replaces A's
  * element in SPM_MODE_LAST_WRITE (a final write of zero removes it) and is
  * added to it in SPM_MODE_SUM (one rounding of A's value + that sum; an
  * element whose result is zero is removed).  A's other elements are kept.
